@@ -1,0 +1,393 @@
+"""Pins for the CPU oracle (no GPU).  Each test ties one oracle function to something other
+than itself: exact rational arithmetic, brute force with Python integers, closed forms,
+invariants of the splitting, or the a priori error bound derived for the method (Sec. 2.2:
+the Ozaki scheme's split into low-precision slices with high-precision accumulation)."""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+U = 2.0 ** -53
+
+
+def frac_matmul(A, B):
+    m, k = A.shape
+    n = B.shape[1]
+    return [[sum(Fraction(float(A[i, l])) * Fraction(float(B[l, j])) for l in range(k)) for j in range(n)]
+            for i in range(m)]
+
+
+# --------------------------------------------------------------------------- double-double
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_dd_matches_exact_rationals(seed):
+    rng = np.random.default_rng(seed)
+    m, k, n = 3, 8, 4
+    A = rng.uniform(-1, 1, (m, k)) * np.exp(rng.normal(0, 8, (m, k)))
+    B = rng.uniform(-1, 1, (k, n)) * np.exp(rng.normal(0, 8, (k, n)))
+    hi, lo = oracle.dgemm_dd(A, B)
+    ex = frac_matmul(A, B)
+    absAB = np.abs(A) @ np.abs(B)
+    for i in range(m):
+        for j in range(n):
+            err = abs(Fraction(hi[i, j]) + Fraction(lo[i, j]) - ex[i][j])
+            assert err <= Fraction(4 * k) * Fraction(U) ** 2 * Fraction(absAB[i, j] * 1.01)
+            assert hi[i, j] == float(Fraction(hi[i, j]) + Fraction(lo[i, j]))  # normalised pair
+
+
+def test_dd_alpha_beta_exact():
+    A = np.array([[1.0 + 2 ** -40, 3.0]])
+    B = np.array([[1.0 - 2 ** -40], [2.0 ** -60]])
+    C0 = np.array([[0.25]])
+    hi, lo = oracle.dgemm_dd(A, B, alpha=3.0, beta=-0.5, C=C0)
+    ex = Fraction(3) * (Fraction(A[0, 0]) * Fraction(B[0, 0]) + Fraction(3.0) * Fraction(B[1, 0])) - Fraction(1, 8)
+    assert abs(Fraction(hi[0, 0]) + Fraction(lo[0, 0]) - ex) <= abs(ex) * Fraction(2) ** -100
+
+
+def test_naive_within_gamma_k():
+    rng = np.random.default_rng(3)
+    m, k, n = 5, 40, 6
+    A = rng.normal(size=(m, k))
+    B = rng.normal(size=(k, n))
+    C = oracle.dgemm_naive(A, B)
+    ex = frac_matmul(A, B)
+    absAB = np.abs(A) @ np.abs(B)
+    gk = k * U / (1 - k * U)
+    for i in range(m):
+        for j in range(n):
+            assert abs(Fraction(C[i, j]) - ex[i][j]) <= Fraction(gk * absAB[i, j] * 1.0001)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_naive_transposes_and_beta(ta, tb):
+    rng = np.random.default_rng(4)
+    m, k, n = 7, 5, 3
+    A = rng.normal(size=(m, k) if ta == "N" else (k, m))
+    B = rng.normal(size=(k, n) if tb == "N" else (n, k))
+    C0 = rng.normal(size=(m, n))
+    opA = A if ta == "N" else A.T
+    opB = B if tb == "N" else B.T
+    C = oracle.dgemm_naive(A, B, ta, tb, alpha=2.0, beta=-1.5, C=C0)
+    np.testing.assert_allclose(C, 2.0 * opA @ opB - 1.5 * C0, rtol=1e-13, atol=1e-13)
+    # beta == 0: NaN in C is never read
+    Cn = np.full((m, n), np.nan)
+    C = oracle.dgemm_naive(A, B, ta, tb, alpha=1.0, beta=0.0, C=Cn)
+    assert np.isfinite(C).all()
+
+
+# --------------------------------------------------------------------------- splitter
+def reconstruct(e, D, s=None):
+    s = D.shape[0] if s is None else s
+    rows, k = D.shape[1], D.shape[2]
+    out = []
+    for i in range(rows):
+        row = []
+        for l in range(k):
+            v = sum(Fraction(int(D[t, i, l])) * Fraction(1, 128 ** (t + 1)) for t in range(s))
+            row.append(v * Fraction(2) ** int(e[i]))
+        out.append(row)
+    return out
+
+
+def test_split_exact_reconstruction_and_digit_bounds():
+    rng = np.random.default_rng(5)
+    # rows spread over many binades, including zeros, powers of two and subnormals
+    X = rng.uniform(-1, 1, (6, 9)) * np.exp2(rng.integers(-40, 40, (6, 9)))
+    X[1, :] = 0.0
+    X[2, 3] = 2.0 ** -1074
+    X[2, 4] = -3 * 2.0 ** -1070
+    X[3, :] = 2.0 ** 300
+    X[4, 0] = -0.0
+    # within a row the spread is < 2^80, so 53 + 80 bits -> 19 digits of 7 bits are exact
+    X[2, :] = np.where(np.abs(X[2, :]) > 0, X[2, :], 1e-300)
+    X[2, :] = X[2, :] * 0 + np.array([1e-300, 3e-301, -7e-302, 2.0 ** -1000, 5e-299, 1e-300, 2e-300, 3e-300, 4e-300])
+    s = 20
+    e, D = oracle.split(X, s)
+    assert D.dtype == np.int8 and np.abs(D.astype(int)).max() <= 127
+    R = reconstruct(e, D)
+    for i in range(X.shape[0]):
+        for l in range(X.shape[1]):
+            assert R[i][l] == Fraction(float(X[i, l])), (i, l)
+    assert e[1] == 0 and not D[:, 1, :].any()          # zero row
+    assert (D[:, 3, :] == np.array([64] + [0] * (s - 1))[:, None]).all()  # 2^300 -> digit 64, rest 0
+    assert e[3] == 301
+
+
+def test_split_sign_coherence_prefix_and_residual():
+    rng = np.random.default_rng(6)
+    X = rng.normal(size=(8, 33)) * np.exp(3 * rng.normal(size=(8, 33)))
+    e8, D8 = oracle.split(X, 8)
+    e3, D3 = oracle.split(X, 3)
+    assert (e8 == e3).all() and (D8[:3] == D3).all()   # prefix property
+    sg = np.sign(X)[None, :, :]
+    assert ((D8 == 0) | (np.sign(D8) == sg)).all()   # digits carry the sign of the entry
+    R3 = reconstruct(e3, D3)
+    for i in range(8):
+        # |a'| in [1/2, 1) for the row max, |a' - sum| < 2^-21, truncation toward zero
+        assert max(abs(Fraction(float(x))) for x in X[i]) / Fraction(2) ** int(e3[i]) >= Fraction(1, 2)
+        for l in range(33):
+            a = Fraction(float(X[i, l]))
+            r = a - R3[i][l]
+            assert abs(r) < Fraction(2) ** (int(e3[i]) - 21)
+            assert r == 0 or (r > 0) == (a > 0)
+
+
+def test_split_closed_form_values():
+    # a' = 1 - 2^-14 has base-128 digits 127, 127, then zeros; 0.75 -> 96 (0.75*128), -0.5 -> -64
+    X = np.array([[1.0 - 2.0 ** -14, 0.75, -0.5, 2.0 ** -7]])
+    e, D = oracle.split(X, 3)
+    assert e[0] == 0
+    assert D[:, 0, 0].tolist() == [127, 127, 0]
+    assert D[:, 0, 1].tolist() == [96, 0, 0]
+    assert D[:, 0, 2].tolist() == [-64, 0, 0]
+    assert D[:, 0, 3].tolist() == [1, 0, 0]
+
+
+def test_split_transposed_and_columns():
+    rng = np.random.default_rng(7)
+    X = rng.normal(size=(5, 4))
+    e1, D1 = oracle.split(X, 4, "N")
+    e2, D2 = oracle.split(np.asfortranarray(X.T), 4, "T")
+    assert (e1 == e2).all() and (D1 == D2).all()
+    f, DB = oracle.split_cols(X, 4)          # columns of X
+    e3, D3 = oracle.split(np.asfortranarray(X.T), 4, "N")
+    assert (f == e3).all() and (DB == D3).all()
+
+
+def test_zsplit_shared_exponent_and_conjugation():
+    rng = np.random.default_rng(8)
+    X = rng.normal(size=(3, 5)) + 1j * rng.normal(size=(3, 5)) * 8
+    e, D = oracle.zsplit(X, 9, "N")
+    for i in range(3):
+        mx = max(max(abs(z.real), abs(z.imag)) for z in X[i])
+        assert e[i] == math.frexp(mx)[1]
+    R = reconstruct(np.repeat(e, 2), D)
+    for i in range(3):
+        for l in range(5):
+            # 9 digits = 63 bits cover 53 bits + the Re/Im exponent gap only approximately:
+            assert abs(R[2 * i][l] - Fraction(X[i, l].real)) < Fraction(2) ** (int(e[i]) - 63)
+            assert abs(R[2 * i + 1][l] - Fraction(X[i, l].imag)) < Fraction(2) ** (int(e[i]) - 63)
+    eC, DC = oracle.zsplit(np.asfortranarray(X.T), 9, "C")   # rows of (X^T)^H = conj(X)
+    assert (eC == e).all()
+    assert (DC[:, 0::2] == D[:, 0::2]).all() and (DC[:, 1::2] == -D[:, 1::2]).all()
+
+
+# --------------------------------------------------------------------------- slice products
+@pytest.mark.parametrize("square", [False, True])
+def test_group_products_brute_force(square):
+    rng = np.random.default_rng(9)
+    s, m, n, k = 4, 3, 5, 7
+    DA = rng.integers(-127, 128, (s, m, k)).astype(np.int8)
+    DB = rng.integers(-127, 128, (s, n, k)).astype(np.int8)
+    G = oracle.group_products(DA, DB, square)
+    for i in range(m):
+        for j in range(n):
+            exp = {}
+            for p in range(1, s + 1):
+                for q in range(1, s + 1):
+                    if not square and p + q > s + 1:
+                        continue
+                    acc = 0
+                    for l in range(k):
+                        acc += int(DA[p - 1, i, l]) * int(DB[q - 1, j, l])
+                    exp[p + q] = exp.get(p + q, 0) + acc
+            for g, v in exp.items():
+                assert G[g - 2, i, j] == v
+    assert G.shape[0] == (2 * s - 1 if square else s)
+
+
+def test_group_products_extremes_no_overflow():
+    s, k = 3, 4096
+    DA = np.full((s, 1, k), 127, np.int8)
+    DB = np.full((s, 1, k), -127, np.int8)
+    G = oracle.group_products(DA, DB)
+    assert G[0, 0, 0] == -127 * 127 * k and G[2, 0, 0] == -3 * 127 * 127 * k
+
+
+# --------------------------------------------------------------------------- emulated GEMM
+def test_emu_integer_inputs_single_slice_is_exact_matmul():
+    rng = np.random.default_rng(10)
+    A = rng.integers(-127, 128, (6, 11)).astype(float)
+    B = rng.integers(-127, 128, (11, 4)).astype(float)
+    A[:, 0] = 127.0  # row max 127 -> e = 7, a' = a/128, one 7-bit digit is exact
+    B[0, :] = -127.0
+    C = oracle.dgemm_emu(A, B, 1)
+    assert (C == A @ B).all()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_emu_exactly_representable_square_set_is_correctly_rounded(seed):
+    # entries with <= 21 significant bits inside a 2^8 window of the row max are exact in
+    # s = 5 digits; with all s^2 pairs T equals the exact product, so C = RN(AB)
+    rng = np.random.default_rng(seed)
+    m, k, n = 4, 6, 5
+    A = rng.integers(-2 ** 20, 2 ** 20, (m, k)) * np.exp2(rng.integers(-8, 0, (m, k))) * 2.0 ** -20
+    B = rng.integers(-2 ** 20, 2 ** 20, (k, n)) * np.exp2(rng.integers(-8, 0, (k, n))) * 2.0 ** -20
+    C = oracle.dgemm_emu(A, B, 5, square=True)
+    ex = frac_matmul(A, B)
+    for i in range(m):
+        for j in range(n):
+            assert C[i, j] == float(ex[i][j])
+
+
+def test_emu_rounding_ties_and_subnormals():
+    # (1 + 2^-52)^2 = 1 + 2^-51 + 2^-104 -> RN gives 1 + 2^-51
+    a = 1.0 + 2.0 ** -52
+    C = oracle.dgemm_emu(np.array([[a]]), np.array([[a]]), 9, square=True)
+    assert C[0, 0] == 1.0 + 2.0 ** -51
+    # 1.5 * 2^-1075 is above half of the smallest subnormal -> rounds to 2^-1074
+    C = oracle.dgemm_emu(np.array([[1.5 * 2.0 ** -537]]), np.array([[2.0 ** -538]]), 2, square=True)
+    assert C[0, 0] == 2.0 ** -1074
+    # exactly half of the smallest subnormal ties to even -> 0
+    C = oracle.dgemm_emu(np.array([[2.0 ** -537]]), np.array([[2.0 ** -538]]), 2, square=True)
+    assert C[0, 0] == 0.0
+    # 3 * 2^-1075 (tie between 1 and 2 ulps of 2^-1074) -> even = 2 * 2^-1074
+    C = oracle.dgemm_emu(np.array([[1.5 * 2.0 ** -537]]), np.array([[2.0 ** -537]]), 2, square=True)
+    assert C[0, 0] == 2.0 ** -1073
+    # overflow -> inf
+    C = oracle.dgemm_emu(np.array([[2.0 ** 600]]), np.array([[2.0 ** 600]]), 2)
+    assert C[0, 0] == np.inf
+
+
+def test_emu_triangle_matches_definition_on_tiny():
+    # brute-force T from the (already pinned) digits with Python integers, then RN
+    rng = np.random.default_rng(11)
+    m, k, n, s = 3, 5, 4, 4
+    A = rng.normal(size=(m, k)) * np.exp(2 * rng.normal(size=(m, k)))
+    B = rng.normal(size=(k, n)) * np.exp(2 * rng.normal(size=(k, n)))
+    e, DA = oracle.split(A, s)
+    f, DB = oracle.split_cols(B, s)
+    C = oracle.dgemm_emu(A, B, s)
+    for i in range(m):
+        for j in range(n):
+            T = Fraction(0)
+            for p in range(1, s + 1):
+                for q in range(1, s + 2 - p):
+                    d = sum(int(DA[p - 1, i, l]) * int(DB[q - 1, j, l]) for l in range(k))
+                    T += Fraction(d) * Fraction(2) ** (int(e[i]) + int(f[j]) - 7 * (p + q))
+            assert C[i, j] == float(T)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6, 7, 8])
+def test_emu_error_within_a_priori_bound(s):
+    rng = np.random.default_rng(100 + s)
+    m, k, n = 24, 70, 20
+    phi = 3.0
+    A = (rng.uniform(size=(m, k)) - 0.5) * np.exp(phi * rng.normal(size=(m, k)))
+    B = (rng.uniform(size=(k, n)) - 0.5) * np.exp(phi * rng.normal(size=(k, n)))
+    C = oracle.dgemm_emu(A, B, s)
+    hi, lo = oracle.dgemm_dd(A, B)
+    bound = oracle.emu_bound(A, B, s) + U * np.abs(C) + 4 * k * U * U * (np.abs(A) @ np.abs(B))
+    assert (np.abs((C - hi) - lo) <= bound).all()
+    # triangle vs square set: the dropped pairs are also inside the bound
+    Cs = oracle.dgemm_emu(A, B, s, square=True)
+    assert (np.abs((Cs - hi) - lo) <= bound).all()
+
+
+def test_emu_error_bound_adversarial_all_max_digits():
+    # a' = 1 - 2^-7s has every digit equal to 127: the residual and the dropped pairs are maximal
+    s, k = 4, 64
+    rng = np.random.default_rng(12)
+    val = 1.0 - 2.0 ** (-7 * s - 2)  # digits 127 x s and a positive residual
+    A = val * rng.choice([-1.0, 1.0], size=(8, k))
+    B = val * rng.choice([-1.0, 1.0], size=(k, 8))
+    C = oracle.dgemm_emu(A, B, s)
+    hi, lo = oracle.dgemm_dd(A, B)
+    bound = oracle.emu_bound(A, B, s) + U * np.abs(C)
+    err = np.abs((C - hi) - lo)
+    assert (err <= bound).all() and err.max() > 0
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_emu_transposes_alpha_beta(ta, tb):
+    rng = np.random.default_rng(13)
+    m, k, n, s = 9, 13, 7, 6
+    A = rng.normal(size=(m, k) if ta == "N" else (k, m))
+    B = rng.normal(size=(k, n) if tb == "N" else (n, k))
+    opA = A if ta == "N" else A.T
+    opB = B if tb == "N" else B.T
+    C0 = rng.normal(size=(m, n))
+    t = oracle.dgemm_emu(np.asfortranarray(opA), np.asfortranarray(opB), s)
+    C = oracle.dgemm_emu(A, B, s, ta, tb, alpha=-0.75, beta=0.5, C=C0)
+    exp = np.array([[math.fma(-0.75, t[i, j], 0.5 * C0[i, j]) for j in range(n)] for i in range(m)]) \
+        if hasattr(math, "fma") else None
+    if exp is not None:
+        assert (C == exp).all()
+    np.testing.assert_allclose(C, -0.75 * opA @ opB + 0.5 * C0, rtol=0, atol=1e-9)
+
+
+def test_emu_trend_error_falls_per_slice():
+    # qualitative trend of Table 1: each added slice cuts the error by tens to hundreds of
+    # times (parity unpinned for the application numbers themselves)
+    rng = np.random.default_rng(14)
+    A = rng.uniform(-1, 1, (32, 64))
+    B = rng.uniform(-1, 1, (64, 32))
+    errs = [oracle.rel_err_vs_dd(oracle.dgemm_emu(A, B, s), A, B) for s in range(2, 8)]
+    for a, b in zip(errs, errs[1:]):
+        assert b < a / 30
+
+
+# --------------------------------------------------------------------------- complex
+def frac_cmatmul(A, B):
+    m, k = A.shape
+    n = B.shape[1]
+    re = [[sum(Fraction(A[i, l].real) * Fraction(B[l, j].real) - Fraction(A[i, l].imag) * Fraction(B[l, j].imag)
+               for l in range(k)) for j in range(n)] for i in range(m)]
+    im = [[sum(Fraction(A[i, l].real) * Fraction(B[l, j].imag) + Fraction(A[i, l].imag) * Fraction(B[l, j].real)
+               for l in range(k)) for j in range(n)] for i in range(m)]
+    return re, im
+
+
+def test_zdd_matches_exact_rationals():
+    rng = np.random.default_rng(15)
+    A = rng.normal(size=(3, 6)) + 1j * rng.normal(size=(3, 6))
+    B = rng.normal(size=(6, 2)) + 1j * rng.normal(size=(6, 2))
+    rh, rl, ih, il = oracle.zgemm_dd(A, B)
+    re, im = frac_cmatmul(A, B)
+    for i in range(3):
+        for j in range(2):
+            assert abs(Fraction(rh[i, j]) + Fraction(rl[i, j]) - re[i][j]) < Fraction(2) ** -95
+            assert abs(Fraction(ih[i, j]) + Fraction(il[i, j]) - im[i][j]) < Fraction(2) ** -95
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "T"), ("N", "C"), ("C", "C")])
+def test_zemu_exact_inputs_correctly_rounded(ta, tb):
+    # parts with <= 14 significant bits inside a 2^6 window of the complex row max are exact
+    # in 3 digits... use s = 4 and the 4 real sub-products: T is exact, so C = RN(AB) per part
+    rng = np.random.default_rng(16)
+    m, k, n = 3, 5, 4
+
+    def mk(shape):
+        re = rng.integers(-2 ** 13, 2 ** 13, shape) * np.exp2(rng.integers(-6, 0, shape)) * 2.0 ** -13
+        im = rng.integers(-2 ** 13, 2 ** 13, shape) * np.exp2(rng.integers(-6, 0, shape)) * 2.0 ** -13
+        return re + 1j * im
+
+    opA, opB = mk((m, k)), mk((k, n))
+    A = opA if ta == "N" else (opA.T if ta == "T" else opA.conj().T)
+    B = opB if tb == "N" else (opB.T if tb == "T" else opB.conj().T)
+    # the triangle set with s digits covers every pair p+q <= s+1; digits here need <= 3 planes,
+    # so s = 5 keeps all nonzero pairs (p, q <= 3 -> p + q <= 6 = s + 1)
+    C = oracle.zgemm_emu(A, B, 5, ta, tb)
+    re, im = frac_cmatmul(opA, opB)
+    for i in range(m):
+        for j in range(n):
+            assert C[i, j].real == float(re[i][j]) and C[i, j].imag == float(im[i][j])
+
+
+def test_zemu_error_bound_and_alpha_beta():
+    rng = np.random.default_rng(17)
+    m, k, n, s = 8, 20, 6, 7
+    A = rng.normal(size=(m, k)) + 1j * rng.normal(size=(m, k))
+    B = rng.normal(size=(k, n)) + 1j * rng.normal(size=(k, n))
+    C = oracle.zgemm_emu(A, B, s)
+    rh, rl, ih, il = oracle.zgemm_dd(A, B)
+    scale = np.abs(A.real) @ np.abs(B.real) + np.abs(A.imag) @ np.abs(B.imag) + \
+        np.abs(A.real) @ np.abs(B.imag) + np.abs(A.imag) @ np.abs(B.real)
+    err = np.maximum(np.abs(C.real - rh - rl), np.abs(C.imag - ih - il)) / scale
+    assert err.max() < 4 * (s + 2) * 2.0 ** (-7 * s) * 4
+    al, be = 0.5 - 2j, 1.5 + 0.25j
+    C0 = rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n))
+    C2 = oracle.zgemm_emu(A, B, s, alpha=al, beta=be, C=C0)
+    np.testing.assert_allclose(C2, al * C + be * C0, rtol=1e-13, atol=1e-13)
