@@ -1,0 +1,144 @@
+/*
+ * ozg.h -- C ABI of the GB300 (sm_103a) library for FP64 / complex128 GEMM emulated with
+ * INT8-range integer slices on the tensor cores, with a tunable slice count.
+ *
+ * Method: the Ozaki scheme on an integer matrix-multiply unit (Sec. 2.2 of "A Pilot Study on
+ * Tunable Precision Emulation via Automatic BLAS Offloading", PEARC'25); the slice count is
+ * the paper's split number, its compute modes "dgemm" (native FP64) and fp64_int8_3 ..
+ * fp64_int8_18 (Sec. 3.1) map to slices = -1 and slices = 3..18.
+ *
+ *   - Row i of op(A) is scaled by 2^-e_i and column j of op(B) by 2^-f_j (e_i, f_j: frexp
+ *     exponents of the row / column maximum), then split by truncation into s signed 7-bit
+ *     digits (|d| <= 127, an INT8 value) per entry.
+ *   - The s(s+1)/2 slice pairs (p, q), p + q <= s + 1, are multiplied exactly as integers and
+ *     summed per group g = p + q.
+ *   - The epilogue forms T_ij = 2^{e_i + f_j - 7(s+1)} sum_g G_g,ij 2^{7(s+1-g)} in FP64 and
+ *     writes C = alpha * T + beta * C.
+ *   - ZGEMM: real and imaginary parts share one exponent per row / column; the four real
+ *     sub-products come from one product of the stacked operands and are combined exactly
+ *     (Re = P_rr - P_ii, Im = P_ri + P_ir) before the FP64 epilogue.
+ *
+ * Conventions (BLAS ?gemm): column-major storage; op(A) is m x k, op(B) is k x n;
+ * trans in {'N','n','T','t'} for DGEMM, plus {'C','c'} for ZGEMM.  Complex matrices are
+ * interleaved complex128 (re, im pairs); leading dimensions count complex elements.
+ *
+ * Memory and ownership: every matrix pointer is a DEVICE pointer (or managed memory) owned by
+ * the caller and never freed by the library.  The context owns its device workspace, which it
+ * grows on demand with cudaMalloc (only between calls, after synchronising its stream).
+ * Calls are asynchronous on the context's stream unless stated otherwise.
+ *
+ * Return codes: 0 on success; -i when argument i is invalid, numbered as in BLAS
+ * (transa = 1, transb = 2, m = 3, n = 4, k = 5, lda = 8, ldb = 10, ldc = 13, slices = 14);
+ * positive values are runtime errors (OZG_ERR_*).  A call that returns an error leaves C
+ * unspecified only for runtime errors; argument errors return before any work is queued.
+ */
+#ifndef OZG_H
+#define OZG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OZG_OK 0
+#define OZG_ERR_CUDA 1         /* a CUDA runtime call failed (see ozg_last_cuda_error) */
+#define OZG_ERR_ALLOC 2        /* device workspace allocation failed */
+#define OZG_ERR_TIMEOUT 3      /* a bounded device-side wait gave up; the kernel returned */
+#define OZG_ERR_UNSUPPORTED 4  /* the request is valid BLAS but outside what this build does */
+#define OZG_ERR_INVALID 5      /* null context or other non-BLAS argument error */
+
+#define OZG_MAX_SLICES 18      /* fp64_int8_18 is the largest mode of Sec. 3.1 */
+#define OZG_NATIVE (-1)        /* slices = -1: native FP64 ("dgemm" mode of Sec. 3.1) */
+
+typedef struct ozg_ctx ozg_ctx;
+
+/* Per-call report.  Fields are filled when the call returns (host-known fields) and after
+ * ozg_sync() (device-computed fields). */
+typedef struct ozg_report {
+  int slices_used;        /* s actually used; -1 when the call ran in native FP64 */
+  int nonfinite;          /* 1 if an input held Inf/NaN and the call was routed to native FP64 */
+  int status;             /* OZG_OK or a positive error code for this call */
+  int reserved;
+} ozg_report;
+
+/* Create a context on the current CUDA device.  workspace_bytes pre-reserves device
+ * workspace (0: grow on first use).  *out receives the context.  Returns 0 or OZG_ERR_*. */
+int ozg_create(ozg_ctx** out, size_t workspace_bytes);
+
+/* Destroy a context: synchronises its stream, frees its workspace.  NULL is accepted. */
+int ozg_destroy(ozg_ctx* ctx);
+
+/* Set the CUDA stream (a cudaStream_t passed as void*) on which the context queues work;
+ * NULL selects the legacy default stream.  The caller keeps ownership of the stream. */
+int ozg_set_stream(ozg_ctx* ctx, void* stream);
+
+/* Block until all work queued by this context has finished; returns the first device-side
+ * status raised since the previous ozg_sync (OZG_ERR_TIMEOUT if a bounded wait expired). */
+int ozg_sync(ozg_ctx* ctx);
+
+/* Human-readable text for a return code (static storage). */
+const char* ozg_strerror(int code);
+
+/* Emulated DGEMM, C = alpha op(A) op(B) + beta C (Sec. 2.2 / 3.1; ?gemm semantics).
+ *   transa, transb: 'N' or 'T' (case-insensitive).  m, n, k >= 0.
+ *   A: device, column-major, lda >= max(1, rows of A); B likewise with ldb; C: m x n, ldc >= max(1, m).
+ *   slices: 1..OZG_MAX_SLICES fixed split number; OZG_NATIVE (-1) runs native FP64.
+ *   beta == 0: C is not read (NaNs in C are ignored).  Quick returns: m == 0 or n == 0, or
+ *   ((alpha == 0 or k == 0) and beta == 1).  alpha == 0 or k == 0 gives C = beta C.
+ *   Inputs holding Inf/NaN are detected on the device and the call is completed by the native
+ *   FP64 kernel (still on the GPU); rep->nonfinite is set after ozg_sync.
+ *   rep may be NULL. */
+int ozg_dgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+              const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+              int64_t ldc, int slices, ozg_report* rep);
+
+/* Emulated ZGEMM (complex128, interleaved), C = alpha op(A) op(B) + beta C; trans in N/T/C.
+ * alpha and beta point to HOST arrays {re, im}.  Other arguments as for ozg_dgemm. */
+int ozg_zgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
+              const double* alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+              const double* beta, double* C, int64_t ldc, int slices, ozg_report* rep);
+
+/* Native FP64 GEMM on the CUDA cores (the "dgemm" mode of Sec. 3.1, and the comparison
+ * kernel of Sec. 4's performance discussion).  Same arguments as ozg_dgemm minus slices. */
+int ozg_native_dgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                     double alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double beta, double* C, int64_t ldc);
+
+/* Native complex128 GEMM (same conventions as ozg_zgemm). */
+int ozg_native_zgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                     const double* alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     const double* beta, double* C, int64_t ldc);
+
+/* ---- inspection entry points (used by the parity tests; same kernels as the GEMM path) ---- */
+
+/* Split the rows of op(X) (rows x k, real FP64, device) into exponents and digit planes, the
+ * first step of Sec. 2.2's scheme.  trans: 'N' (row i of X) or 'T' (column i of X).
+ *   e_out: device int32[rows]; digits_out: device int8[s][rows][k] (k contiguous).
+ * Synchronous (returns after the copy-out kernel finished). */
+int ozg_debug_split(ozg_ctx* ctx, char trans, int64_t rows, int64_t k, const double* X, int64_t ld,
+                    int slices, int32_t* e_out, int8_t* digits_out);
+
+/* Complex variant: op(X) rows x k complex128; trans 'N', 'T' or 'C'.  digits_out is
+ * int8[s][2*rows][k] with Re of row i at 2i and Im at 2i+1; e_out int32[rows]. */
+int ozg_debug_zsplit(ozg_ctx* ctx, char trans, int64_t rows, int64_t k, const double* X, int64_t ld,
+                     int slices, int32_t* e_out, int8_t* digits_out);
+
+/* Exact group products G_g = sum_{p+q=g} D^A_p (D^B_q)^T of the emulated DGEMM (the integer
+ * slice products of Sec. 2.2), computed by the tensor-core kernel and exported as
+ * int64[s][m][n] (row-major, group g = 2..s+1 at index g-2) in device memory G_out.  Requires
+ * (s) * ceil(k / 64) * 64 * 127^2 < 2^31 so that each group is one integer accumulation.
+ * Synchronous. */
+int ozg_debug_group_products(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                             const double* A, int64_t lda, const double* B, int64_t ldb, int slices,
+                             int64_t* G_out);
+
+/* Message of the last failing CUDA runtime call seen by the library in this process. */
+const char* ozg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OZG_H */

@@ -1,0 +1,417 @@
+// C ABI (include/ozg.h): argument checking with BLAS xerbla numbering, quick returns,
+// workspace management and the launch sequence of the emulated GEMM:
+//   split(op(A)) -> split(op(B)) -> fused slice-GEMM + epilogue -> native kernel gated on
+//   the non-finite flag (runs only if an input held Inf/NaN).
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/ozg.h"
+#include "ozg_internal.h"
+
+struct ozg_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  void* ws = nullptr;
+  size_t ws_cap = 0;
+  int* dflags = nullptr;  // [0] status (sticky until ozg_sync), [1] non-finite flag of the last call
+};
+
+namespace {
+
+char g_last_cuda[256] = "no error";
+std::mutex g_err_mu;
+
+int cuda_fail(cudaError_t e) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return OZG_ERR_CUDA;
+}
+#define OZG_CUDA(x)                              \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+char norm_trans(char t) {
+  if (t >= 'a' && t <= 'z') t = (char)(t - 'a' + 'A');
+  return t;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the context workspace.
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  }
+};
+
+int ensure_ws(ozg_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_cap) return OZG_OK;
+  OZG_CUDA(cudaStreamSynchronize(c->stream));
+  if (c->ws) {
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_cap = 0;
+  }
+  size_t want = align_up(bytes + bytes / 8, 1 << 20);
+  cudaError_t e = cudaMalloc(&c->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return OZG_ERR_ALLOC;
+  }
+  c->ws_cap = want;
+  return OZG_OK;
+}
+
+template <typename T>
+T* at(ozg_ctx* c, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(c->ws) + off);
+}
+
+int check_gemm_args(bool cplx, char& ta, char& tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
+                    int64_t ldc) {
+  ta = norm_trans(ta);
+  tb = norm_trans(tb);
+  if (!cplx) {  // BLAS dgemm accepts 'C' as 'T'
+    if (ta == 'C') ta = 'T';
+    if (tb == 'C') tb = 'T';
+  }
+  if (ta != 'N' && ta != 'T' && ta != 'C') return -1;
+  if (tb != 'N' && tb != 'T' && tb != 'C') return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  int64_t nrowa = (ta == 'N') ? m : k, nrowb = (tb == 'N') ? k : n;
+  if (lda < (nrowa > 1 ? nrowa : 1)) return -8;
+  if (ldb < (nrowb > 1 ? nrowb : 1)) return -10;
+  if (ldc < (m > 1 ? m : 1)) return -13;
+  return 0;
+}
+
+// Emulated real or complex GEMM.  alpha/beta: {re, im} (im ignored for real).  When Gdbg is
+// set, exports the int64 group products instead of computing C.
+int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int64_t k, const double* alpha,
+             const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C, int64_t ldc,
+             int s, ozg_report* rep, int64_t* Gdbg) {
+  const int64_t Kp = (int64_t)align_up((size_t)k, 8);
+  const int64_t prA = cplx ? 2 * m : m, prB = cplx ? 2 * n : n;
+  const int BM = ozg::slice_gemm_tile_m(), BN = ozg::slice_gemm_tile_n();
+  const int64_t tiles = ((prA + BM - 1) / BM) * ((prB + BN - 1) / BN);
+  const int grid = (int)(tiles < c->num_sms ? tiles : c->num_sms);
+  Carve cv;
+  size_t oDA = cv.take((size_t)s * prA * Kp * 2), oDB = cv.take((size_t)s * prB * Kp * 2);
+  size_t oE = cv.take(4 * (size_t)m), oF = cv.take(4 * (size_t)n);
+  size_t oMA = cv.take(8 * (size_t)m), oMB = cv.take(8 * (size_t)n);
+  size_t oR = cv.take((size_t)grid * BM * BN * 8);
+  int rc = ensure_ws(c, cv.off);
+  if (rc) return rc;
+  cudaStream_t st = c->stream;
+  int* nonfinite = c->dflags + 1;
+  OZG_CUDA(cudaMemsetAsync(nonfinite, 0, sizeof(int), st));
+
+  ozg::SplitArgs sa;
+  sa.X = A;
+  sa.ld = lda;
+  sa.rows = m;
+  sa.k = k;
+  sa.strided = (ta == 'N');
+  sa.conj = (ta == 'C');
+  sa.cplx = cplx;
+  sa.s = s;
+  sa.Kp = Kp;
+  sa.plane_rows = prA;
+  sa.D = at<__half>(c, oDA);
+  sa.maxbits = at<unsigned long long>(c, oMA);
+  sa.exps = at<int32_t>(c, oE);
+  sa.nonfinite = nonfinite;
+  OZG_CUDA(ozg::launch_split(sa, st));
+  ozg::SplitArgs sb = sa;
+  sb.X = B;
+  sb.ld = ldb;
+  sb.rows = n;
+  sb.strided = (tb != 'N');
+  sb.conj = (tb == 'C');
+  sb.plane_rows = prB;
+  sb.D = at<__half>(c, oDB);
+  sb.maxbits = at<unsigned long long>(c, oMB);
+  sb.exps = at<int32_t>(c, oF);
+  OZG_CUDA(ozg::launch_split(sb, st));
+
+  CUtensorMap tmA, tmB;
+  OZG_CUDA(ozg::make_digit_tmap(&tmA, sa.D, k, prA, Kp, s, BM));
+  OZG_CUDA(ozg::make_digit_tmap(&tmB, sb.D, k, prB, Kp, s, BN));
+  ozg::GemmArgs ga;
+  ga.rows = prA;
+  ga.cols = prB;
+  ga.m = m;
+  ga.n = n;
+  ga.k = k;
+  ga.s = s;
+  ga.cplx = cplx;
+  ga.e = sa.exps;
+  ga.f = sb.exps;
+  ga.C = C;
+  ga.ldc = ldc;
+  ga.alpha[0] = alpha[0];
+  ga.alpha[1] = cplx ? alpha[1] : 0.0;
+  ga.beta[0] = beta[0];
+  ga.beta[1] = cplx ? beta[1] : 0.0;
+  ga.beta_zero = (beta[0] == 0.0 && (!cplx || beta[1] == 0.0));
+  ga.Rws = at<double>(c, oR);
+  ga.Gdbg = Gdbg;
+  ga.status = c->dflags;
+  ga.nonfinite = Gdbg ? nullptr : nonfinite;
+  ga.grid = grid;
+  OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB, ga, st));
+  if (Gdbg) return OZG_OK;
+
+  ozg::NativeArgs na;
+  na.ta = ta;
+  na.tb = tb;
+  na.m = m;
+  na.n = n;
+  na.k = k;
+  na.A = A;
+  na.lda = lda;
+  na.B = B;
+  na.ldb = ldb;
+  na.C = C;
+  na.ldc = ldc;
+  na.alpha[0] = ga.alpha[0];
+  na.alpha[1] = ga.alpha[1];
+  na.beta[0] = ga.beta[0];
+  na.beta[1] = ga.beta[1];
+  na.beta_zero = ga.beta_zero;
+  na.cplx = cplx;
+  na.gate = nonfinite;
+  OZG_CUDA(ozg::launch_native_gemm(na, st));
+  if (rep) {
+    int h = 0;
+    OZG_CUDA(cudaMemcpyAsync(&h, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+    OZG_CUDA(cudaStreamSynchronize(st));
+    rep->nonfinite = h;
+    rep->slices_used = h ? -1 : s;
+  }
+  return OZG_OK;
+}
+
+int gemm_entry(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int64_t k, const double* alpha,
+               const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C,
+               int64_t ldc, int slices, ozg_report* rep, bool native) {
+  // BLAS order: argument errors are reported before anything else (no device work, no context use)
+  int rc = check_gemm_args(cplx, ta, tb, m, n, k, lda, ldb, ldc);
+  if (rc) return rc;
+  if (!native && (slices == 0 || slices < OZG_NATIVE || slices > OZG_MAX_SLICES)) return -14;
+  if (!c) return OZG_ERR_INVALID;
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->slices_used = native ? -1 : slices;
+  }
+  if (m == 0 || n == 0) return OZG_OK;
+  const bool alpha_zero = alpha[0] == 0.0 && (!cplx || alpha[1] == 0.0);
+  const bool beta_one = beta[0] == 1.0 && (!cplx || beta[1] == 0.0);
+  if ((alpha_zero || k == 0) && beta_one) return OZG_OK;
+  cudaSetDevice(c->device);
+  if (alpha_zero || k == 0) {
+    OZG_CUDA(ozg::launch_scale_c(C, m, n, ldc, beta, cplx, c->stream));
+    return OZG_OK;
+  }
+  if (native || slices == OZG_NATIVE) {
+    ozg::NativeArgs na;
+    na.ta = ta;
+    na.tb = tb;
+    na.m = m;
+    na.n = n;
+    na.k = k;
+    na.A = A;
+    na.lda = lda;
+    na.B = B;
+    na.ldb = ldb;
+    na.C = C;
+    na.ldc = ldc;
+    na.alpha[0] = alpha[0];
+    na.alpha[1] = cplx ? alpha[1] : 0.0;
+    na.beta[0] = beta[0];
+    na.beta[1] = cplx ? beta[1] : 0.0;
+    na.beta_zero = beta[0] == 0.0 && (!cplx || beta[1] == 0.0);
+    na.cplx = cplx;
+    OZG_CUDA(ozg::launch_native_gemm(na, c->stream));
+    if (rep) rep->slices_used = -1;
+    return OZG_OK;
+  }
+  return emu_gemm(c, cplx, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, rep, nullptr);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ozg_create(ozg_ctx** out, size_t workspace_bytes) {
+  if (!out) return OZG_ERR_INVALID;
+  *out = nullptr;
+  ozg_ctx* c = new ozg_ctx();
+  OZG_CUDA(cudaGetDevice(&c->device));
+  OZG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  if (cudaMalloc(&c->dflags, 4 * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return OZG_ERR_ALLOC;
+  }
+  OZG_CUDA(cudaMemset(c->dflags, 0, 4 * sizeof(int)));
+  if (workspace_bytes) {
+    int rc = ensure_ws(c, workspace_bytes);
+    if (rc) {
+      cudaFree(c->dflags);
+      delete c;
+      return rc;
+    }
+  }
+  *out = c;
+  return OZG_OK;
+}
+
+int ozg_destroy(ozg_ctx* c) {
+  if (!c) return OZG_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->ws) cudaFree(c->ws);
+  if (c->dflags) cudaFree(c->dflags);
+  delete c;
+  return OZG_OK;
+}
+
+int ozg_set_stream(ozg_ctx* c, void* stream) {
+  if (!c) return OZG_ERR_INVALID;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return OZG_OK;
+}
+
+int ozg_sync(ozg_ctx* c) {
+  if (!c) return OZG_ERR_INVALID;
+  OZG_CUDA(cudaStreamSynchronize(c->stream));
+  int h = 0;
+  OZG_CUDA(cudaMemcpy(&h, c->dflags, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) OZG_CUDA(cudaMemset(c->dflags, 0, sizeof(int)));
+  return h ? (h == 3 ? OZG_ERR_TIMEOUT : OZG_ERR_CUDA) : OZG_OK;
+}
+
+const char* ozg_strerror(int code) {
+  if (code < 0) return "invalid argument (BLAS argument position = -code)";
+  switch (code) {
+    case OZG_OK: return "success";
+    case OZG_ERR_CUDA: return "CUDA runtime error";
+    case OZG_ERR_ALLOC: return "device workspace allocation failed";
+    case OZG_ERR_TIMEOUT: return "a bounded device-side wait expired";
+    case OZG_ERR_UNSUPPORTED: return "unsupported request";
+    case OZG_ERR_INVALID: return "invalid context or argument";
+    default: return "unknown error";
+  }
+}
+
+const char* ozg_last_cuda_error(void) { return g_last_cuda; }
+
+int ozg_dgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+              const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+              int slices, ozg_report* rep) {
+  double al[2] = {alpha, 0.0}, be[2] = {beta, 0.0};
+  return gemm_entry(ctx, false, transa, transb, m, n, k, al, A, lda, B, ldb, be, C, ldc, slices, rep, false);
+}
+
+int ozg_zgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, const double* alpha,
+              const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C,
+              int64_t ldc, int slices, ozg_report* rep) {
+  if (!alpha || !beta) return OZG_ERR_INVALID;
+  return gemm_entry(ctx, true, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, rep, false);
+}
+
+int ozg_native_dgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                     int64_t ldc) {
+  double al[2] = {alpha, 0.0}, be[2] = {beta, 0.0};
+  return gemm_entry(ctx, false, transa, transb, m, n, k, al, A, lda, B, ldb, be, C, ldc, OZG_NATIVE, nullptr, true);
+}
+
+int ozg_native_zgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, const double* alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C,
+                     int64_t ldc) {
+  if (!alpha || !beta) return OZG_ERR_INVALID;
+  return gemm_entry(ctx, true, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, OZG_NATIVE, nullptr,
+                    true);
+}
+
+static int debug_split_impl(ozg_ctx* c, bool cplx, char trans, int64_t rows, int64_t k, const double* X, int64_t ld,
+                            int s, int32_t* e_out, int8_t* digits_out) {
+  if (!c) return OZG_ERR_INVALID;
+  trans = norm_trans(trans);
+  if (!cplx && trans == 'C') trans = 'T';
+  if (trans != 'N' && trans != 'T' && trans != 'C') return -1;
+  if (rows < 0) return -2;
+  if (k <= 0) return -3;
+  int64_t nrow = (trans == 'N') ? rows : k;
+  if (ld < (nrow > 1 ? nrow : 1)) return -5;
+  if (s < 1 || s > OZG_MAX_SLICES) return -6;
+  if (rows == 0) return OZG_OK;
+  cudaSetDevice(c->device);
+  const int64_t Kp = (int64_t)align_up((size_t)k, 8);
+  const int64_t pr = cplx ? 2 * rows : rows;
+  Carve cv;
+  size_t oD = cv.take((size_t)s * pr * Kp * 2), oM = cv.take(8 * (size_t)rows), oE = cv.take(4 * (size_t)rows);
+  int rc = ensure_ws(c, cv.off);
+  if (rc) return rc;
+  ozg::SplitArgs sa;
+  sa.X = X;
+  sa.ld = ld;
+  sa.rows = rows;
+  sa.k = k;
+  sa.strided = (trans == 'N');
+  sa.conj = (trans == 'C');
+  sa.cplx = cplx;
+  sa.s = s;
+  sa.Kp = Kp;
+  sa.plane_rows = pr;
+  sa.D = at<__half>(c, oD);
+  sa.maxbits = at<unsigned long long>(c, oM);
+  sa.exps = at<int32_t>(c, oE);
+  sa.nonfinite = c->dflags + 1;
+  OZG_CUDA(ozg::launch_split(sa, c->stream));
+  OZG_CUDA(ozg::launch_digits_to_i8(sa.D, s, pr, k, Kp, digits_out, c->stream));
+  OZG_CUDA(cudaMemcpyAsync(e_out, sa.exps, 4 * (size_t)rows, cudaMemcpyDeviceToDevice, c->stream));
+  OZG_CUDA(cudaStreamSynchronize(c->stream));
+  return OZG_OK;
+}
+
+int ozg_debug_split(ozg_ctx* ctx, char trans, int64_t rows, int64_t k, const double* X, int64_t ld, int slices,
+                    int32_t* e_out, int8_t* digits_out) {
+  return debug_split_impl(ctx, false, trans, rows, k, X, ld, slices, e_out, digits_out);
+}
+
+int ozg_debug_zsplit(ozg_ctx* ctx, char trans, int64_t rows, int64_t k, const double* X, int64_t ld, int slices,
+                     int32_t* e_out, int8_t* digits_out) {
+  return debug_split_impl(ctx, true, trans, rows, k, X, ld, slices, e_out, digits_out);
+}
+
+int ozg_debug_group_products(ozg_ctx* c, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                             const double* A, int64_t lda, const double* B, int64_t ldb, int slices,
+                             int64_t* G_out) {
+  if (!c) return OZG_ERR_INVALID;
+  int rc = check_gemm_args(false, transa, transb, m, n, k, lda, ldb, m > 0 ? m : 1);
+  if (rc) return rc;
+  if (slices < 1 || slices > OZG_MAX_SLICES) return -14;
+  if (m == 0 || n == 0 || k == 0) return OZG_OK;
+  // one int32 accumulation per group: s * ceil(k/64) k-blocks at most 64 chains of 16 blocks
+  if ((int64_t)slices * ((k + 63) / 64) > 1024) return OZG_ERR_UNSUPPORTED;
+  cudaSetDevice(c->device);
+  double one[2] = {1.0, 0.0}, zero[2] = {0.0, 0.0};
+  rc = emu_gemm(c, false, transa, transb, m, n, k, one, A, lda, B, ldb, zero, nullptr, m, slices, nullptr, G_out);
+  if (rc) return rc;
+  OZG_CUDA(cudaStreamSynchronize(c->stream));
+  return ozg_sync(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,389 @@
+// K2 + K3: the slice products of the Ozaki scheme (Sec. 2.2) on the sm_103a tensor cores,
+// fused with the FP64 scale-and-accumulate epilogue.
+//
+// The INT8-range digits (|d| <= 127) are held in FP16, which represents them exactly, and
+// multiplied by tcgen05.mma kind::f16 with FP32 accumulation in TMEM.  Every product is an
+// integer below 2^14 and an accumulation chain holds at most 1024 products per entry, so every
+// partial sum is an integer below 1024 * 127^2 < 2^24 and the FP32 accumulator is exact: the
+// chain result IS the integer slice product.  (tcgen05.mma kind::i8 does not exist for
+// sm_103a, and the legacy warp-level integer MMA runs ~15x below the FP16 tensor rate.)
+//
+// Per output tile (BM x BN of the (stacked) product) the schedule is group-major:
+//   for g = 2 .. s+1:  for kb in k-blocks:  for p = 1 .. g-1:  D[buf] += A_p[kb] * B_{g-p}[kb]^T
+// cut into chains of SEG_BLOCKS k-blocks.  Each finished chain is drained by the epilogue
+// warps (TMEM -> registers, exact FP32 -> int32) into an int32 group sum G_g while the MMA
+// warp fills the other TMEM buffer.  At the end of group g the epilogue folds G_g into the
+// FP64 value R <- 128 R + G_g (Horner in the group index), kept per CTA in L2-resident
+// scratch; after the last group it writes C = alpha * R 2^{e_i + f_j - 7(s+1)} (+ beta C).
+// Complex (stacked rows 2i = Re, 2i+1 = Im; columns likewise) combines the four real
+// sub-products exactly in int32 before the Horner step: Re = P_rr - P_ii, Im = P_ri + P_ir.
+//
+// Warp roles (384 threads = 3 warpgroups, one CTA per SM, persistent over tiles):
+//   warpgroup 0: warp 0 TMA producer (one lane), warp 1 TMEM allocator + MMA issuer (one lane),
+//                warps 2-3 idle; the group shrinks its registers to 40 (setmaxnreg.dec)
+//   warpgroups 1-2 (warps 4..11): epilogue, grown to 232 registers (setmaxnreg.inc) to hold the
+//                int32 group sums; warp w reads TMEM lanes 32 (w % 4) .. +31 and half
+//                (w - 4) / 4 of the BN columns.
+// Register budget: 384 threads x 168 at launch = 64512 = 128 x 40 + 256 x 232.
+#include "ozg_device.cuh"
+#include "ozg_internal.h"
+
+namespace ozg {
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 128 + EPI_WARPS * 32;
+constexpr int REG_PRODUCER = 40, REG_EPILOGUE = 232;
+static_assert(128 * REG_PRODUCER + EPI_WARPS * 32 * REG_EPILOGUE <= THREADS * 168, "register split");
+constexpr int SEG_BLOCKS = 16;  // 16 * 64 = 1024 products per chain: 1024 * 127^2 = 16516096 < 2^24
+constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t IDESC = umma_idesc_f16_f32(BM, BN);
+constexpr uint32_t TMEM_COLS = 512;  // two BN-column FP32 accumulators
+constexpr int COLS_PER_THREAD = BN / 2;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;
+constexpr int GROUP_M = 8;  // tile raster: GROUP_M row-tiles share a sweep over the column tiles
+
+static_assert(SEG_BLOCKS * BK * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  int per_group = GROUP_M * tiles_n;
+  int grp = t / per_group;
+  int first = grp * GROUP_M;
+  int gsz = min(tiles_m - first, GROUP_M);
+  int r = t % per_group;
+  tm = first + r % gsz;
+  tn = r / gsz;
+}
+
+__device__ __forceinline__ int nseg_of(int g, int KB) { return ((g - 1) * KB + SEG_BLOCKS - 1) / SEG_BLOCKS; }
+
+// x * 2^E with one rounding (the same result as ldexp); fast path when 2^E is a normal double
+__device__ __forceinline__ double scale_pow2(double x, int E) {
+  if (E >= -1022 && E <= 1023) return x * __longlong_as_double((long long)(E + 1023) << 52);
+  return ldexp(x, E);
+}
+
+// Bounded wait used during teardown after an abort (ignores the abort flag).
+__device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > OZG_WAIT_CYCLES) return;
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const GemmArgs P) {
+  if (P.nonfinite != nullptr && *P.nonfinite) return;  // the native FP64 kernel handles this call
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_accf[2], bar_acce[2], bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      mbar_init(&bar_full[i], 1);
+      mbar_init(&bar_empty[i], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_accf[b], 1);
+      mbar_init(&bar_acce[b], EPI_WARPS);
+    }
+    mbar_init(&bar_done, 1);
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_p = &abort_flag;
+
+  const int tiles_m = (int)((P.rows + BM - 1) / BM), tiles_n = (int)((P.cols + BN - 1) / BN);
+  const int ntiles = tiles_m * tiles_n;
+  const int KB = (int)((P.k + BK - 1) / BK);
+  const int s = P.s;
+
+  if (warp < 4) {
+   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_PRODUCER));
+   if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      long long issued = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(t, tiles_m, tiles_n, tm, tn);
+        for (int g = 2; g <= s + 1; ++g)
+          for (int kb = 0; kb < KB; ++kb)
+            for (int p = 1; p < g; ++p) {
+              if (!mbar_wait(&bar_empty[stage], phase ^ 1, abort_p, P.status)) goto producer_done;
+              uint8_t* sA = smem + stage * STAGE_BYTES;
+              mbar_arrive_expect_tx(&bar_full[stage], STAGE_BYTES);
+              tma_load_3d(&tmA, &bar_full[stage], sA, kb * BK, tm * BM, p - 1);
+              tma_load_3d(&tmB, &bar_full[stage], sA + A_BYTES, kb * BK, tn * BN, g - p - 1);
+              ++issued;
+              if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+      }
+    producer_done:
+      if (*abort_p) {
+        // wait (bounded) for the copies still in flight into this CTA's shared memory
+        uint32_t st = stage, ph = phase;
+        for (long long i = 0; i < STAGES && i < issued; ++i) {
+          if (st == 0) {
+            st = STAGES - 1;
+            ph ^= 1;
+          } else {
+            --st;
+          }
+          drain_wait(&bar_full[st], ph);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      uint32_t acc_par = 0;  // bit b: parity of the next use of TMEM buffer b
+      int buf = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int g = 2; g <= s + 1; ++g) {
+          const int nblk = (g - 1) * KB;
+          int b = 0;
+          for (int kb = 0; kb < KB; ++kb)
+            for (int p = 1; p < g; ++p) {
+              if (b % SEG_BLOCKS == 0) {
+                if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, P.status)) goto mma_done;
+                tc_fence_after();
+              }
+              if (!mbar_wait(&bar_full[stage], phase, abort_p, P.status)) goto mma_done;
+              tc_fence_after();
+              {
+                uint8_t* sA = smem + stage * STAGE_BYTES;
+                uint64_t da = umma_desc_sw128(sA), db = umma_desc_sw128(sA + A_BYTES);
+                uint32_t dt = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+                for (int j = 0; j < BK / 16; ++j)
+                  umma_f16(dt, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), IDESC,
+                           (b % SEG_BLOCKS != 0 || j != 0) ? 1u : 0u);
+              }
+              umma_commit(&bar_empty[stage]);
+              if (++stage == STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+              ++b;
+              if (b % SEG_BLOCKS == 0 || b == nblk) {
+                umma_commit(&bar_accf[buf]);
+                acc_par ^= 1u << buf;
+                buf ^= 1;
+              }
+            }
+        }
+      }
+    mma_done:
+      // all MMAs issued by this thread must finish before TMEM is released
+      umma_commit(&bar_done);
+      drain_wait(&bar_done, 0);
+    }
+   }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPILOGUE));
+    const int ew = warp - 4;
+    const int quad = warp & 3;
+    const int chalf = ew >> 2;
+    const int r = quad * 32 + lane;
+    const int push_segs = P.cplx ? 32 : 64;  // int32 group sums stay below 2^31
+    uint32_t acc_par = 0;
+    int buf = 0;
+    double* Rbase = P.Rws + (size_t)blockIdx.x * BM * BN;
+    const bool odd = (lane & 1) != 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, tm, tn);
+      const int64_t grow = (int64_t)tm * BM + r;  // row of the (stacked) product
+      const bool row_ok = grow < P.rows;
+      const int64_t orow = P.cplx ? (grow >> 1) : grow;
+      const int e_row = (row_ok && P.e != nullptr) ? P.e[orow] : 0;
+      const int64_t gcol0 = (int64_t)tn * BN + chalf * COLS_PER_THREAD;
+      for (int g = 2; g <= s + 1; ++g) {
+        int G[COLS_PER_THREAD];
+#pragma unroll
+        for (int c = 0; c < COLS_PER_THREAD; ++c) G[c] = 0;
+        const int nseg = nseg_of(g, KB);
+        bool first_push = true;
+        for (int seg = 0; seg < nseg; ++seg) {
+          if (!mbar_wait(&bar_accf[buf], (acc_par >> buf) & 1, abort_p, P.status)) goto epi_done;
+          tc_fence_after();
+          {
+            const uint32_t taddr =
+                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + chalf * COLS_PER_THREAD);
+#pragma unroll
+            for (int cc = 0; cc < COLS_PER_THREAD / 32; ++cc) {
+              uint32_t v[32];
+              tmem_ld32(taddr + cc * 32, v);
+              tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) G[cc * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_acce[buf]);
+          acc_par ^= 1u << buf;
+          buf ^= 1;
+          const bool group_end = (seg == nseg - 1);
+          if (!(group_end || ((seg + 1) % push_segs) == 0)) continue;
+          const bool final_push = group_end && g == s + 1;
+          // ---- push G into R (or, for inspection, export G) ----
+          // Pushes happen once per group (per 64 chains at most): G moves to a thread-local
+          // array indexed at run time, so the FP64 work below runs in a rolled loop with few
+          // live registers while G itself stays in registers for the frequent drains above.
+          int Gs[COLS_PER_THREAD];
+#pragma unroll
+          for (int c = 0; c < COLS_PER_THREAD; ++c) {
+            Gs[c] = G[c];
+            G[c] = 0;
+          }
+          if (P.Gdbg != nullptr) {
+#pragma unroll 1
+            for (int c = 0; c < COLS_PER_THREAD; ++c) {
+              const int64_t gc = gcol0 + c;
+              if (row_ok && gc < P.cols) P.Gdbg[((int64_t)(g - 2) * P.rows + grow) * P.cols + gc] = Gs[c];
+            }
+          } else if (!P.cplx) {
+            double* Rt = Rbase + (size_t)(chalf * COLS_PER_THREAD) * BM + r;
+            if (!final_push) {
+#pragma unroll 4
+              for (int c = 0; c < COLS_PER_THREAD; ++c) {
+                const double gv = (double)Gs[c];
+                double* Rp = Rt + (size_t)c * BM;
+                *Rp = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+              }
+            } else {
+              const int ebase = e_row - 7 * (s + 1);
+#pragma unroll 4
+              for (int c = 0; c < COLS_PER_THREAD; ++c) {
+                const double gv = (double)Gs[c];
+                const double* Rp = Rt + (size_t)c * BM;
+                const double Rv = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+                const int64_t col = gcol0 + c;
+                if (row_ok && col < P.cols) {
+                  const double tv = scale_pow2(Rv, ebase + __ldg(P.f + col));
+                  double* cp = P.C + orow + col * P.ldc;
+                  *cp = P.beta_zero ? P.alpha[0] * tv : fma(P.alpha[0], tv, P.beta[0] * *cp);
+                }
+              }
+            }
+          } else {
+            double* Rt = Rbase + (size_t)(chalf * COLS_PER_THREAD / 2) * BM + r;
+            const int ebase = e_row - 7 * (s + 1);
+#pragma unroll 2
+            for (int c = 0; c < COLS_PER_THREAD / 2; ++c) {
+              // even lane (Re row) holds (rr, ri), odd lane (Im row) holds (ir, ii) at columns 2c, 2c+1
+              const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * c + 1], 1);
+              const int comb = odd ? (Gs[2 * c] + other) : (Gs[2 * c] - other);
+              double* Rp = Rt + (size_t)c * BM;
+              const double gv = (double)comb;
+              const double Rv = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+              if (!final_push) {
+                *Rp = Rv;
+              } else {
+                const int64_t j = (gcol0 >> 1) + c;
+                const bool ok = row_ok && j < P.n;
+                const double part = ok ? scale_pow2(Rv, ebase + __ldg(P.f + j)) : 0.0;
+                const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
+                const double tr = odd ? partner : part, ti = odd ? part : partner;
+                if (ok) {
+                  double* cp = P.C + 2 * (orow + j * P.ldc);
+                  double re = fma(P.alpha[0], tr, -(P.alpha[1] * ti));
+                  double im = fma(P.alpha[0], ti, P.alpha[1] * tr);
+                  if (!P.beta_zero) {
+                    const double cr = cp[0], ci = cp[1];
+                    re += fma(P.beta[0], cr, -(P.beta[1] * ci));
+                    im += fma(P.beta[0], ci, P.beta[1] * cr);
+                  }
+                  cp[odd ? 1 : 0] = odd ? im : re;
+                }
+              }
+            }
+          }
+          first_push = false;
+        }
+      }
+    }
+  epi_done:;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int slice_gemm_tile_m() { return BM; }
+int slice_gemm_tile_n() { return BN; }
+size_t slice_gemm_smem_bytes() { return SMEM_BYTES; }
+
+cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
+                            int box_rows) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)s};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(rows * Kp * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half*>(D), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& a, cudaStream_t st) {
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  if (a.grid <= 0) return cudaSuccess;
+  slice_gemm_kernel<<<a.grid, THREADS, SMEM_BYTES, st>>>(tmA, tmB, a);
+  return cudaGetLastError();
+}
+
+}  // namespace ozg

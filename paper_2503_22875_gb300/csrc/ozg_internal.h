@@ -1,0 +1,83 @@
+// Internal launch interfaces shared by the library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ozg {
+
+// ---------------------------------------------------------------------------------- split
+// Rows of op(X): element (i, l) at X[i + l*ld] when `strided`, at X[l + i*ld] otherwise
+// (complex: interleaved pairs, same indexing in complex elements; `conj` negates Im).
+struct SplitArgs {
+  const double* X = nullptr;
+  int64_t ld = 0;
+  int64_t rows = 0;   // rows of op(X) (complex rows for cplx)
+  int64_t k = 0;
+  int strided = 0;
+  int conj = 0;
+  int cplx = 0;
+  int s = 0;
+  int64_t Kp = 0;                 // row pitch of the digit planes (elements), multiple of 8, >= k
+  int64_t plane_rows = 0;         // rows per digit plane (rows, or 2*rows for complex)
+  __half* D = nullptr;            // digit planes [s][plane_rows][Kp], fp16 holding integers |d| <= 127
+  unsigned long long* maxbits = nullptr;  // [rows] scratch, zeroed by the launcher
+  int32_t* exps = nullptr;        // [rows] output exponents
+  int* nonfinite = nullptr;       // set to 1 if any entry is Inf/NaN
+};
+cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
+
+// int8 copy of fp16 digit planes (inspection path): out[p][r][l] = D[p][r][l], l < k
+cudaError_t launch_digits_to_i8(const __half* D, int64_t planes, int64_t plane_rows, int64_t k, int64_t Kp,
+                                int8_t* out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------- slice GEMM
+struct GemmArgs {
+  int64_t rows = 0, cols = 0;   // stacked output rows / cols of the real product (complex: 2m, 2n)
+  int64_t m = 0, n = 0;         // output matrix dims (complex: m, n)
+  int64_t k = 0;
+  int s = 0;
+  int cplx = 0;
+  const int32_t* e = nullptr;   // [m] row exponents
+  const int32_t* f = nullptr;   // [n] column exponents
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double alpha[2] = {1, 0}, beta[2] = {0, 0};
+  int beta_zero = 1;
+  double* Rws = nullptr;        // FP64 partial sums, [grid][BN][BM] per CTA
+  int64_t* Gdbg = nullptr;      // inspection: int64 [s][rows][cols] group products (no epilogue)
+  int* status = nullptr;        // device status word (0 ok, 3 timeout)
+  const int* nonfinite = nullptr;  // if non-null and set, the kernel exits (native path takes over)
+  int grid = 0;                 // CTAs to launch (<= tiles); Rws must hold grid tiles
+};
+// Tensor maps over the digit planes: dims {k, rows, s}, box {64, 128 | 256, 1}, fp16, SW128.
+cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
+                            int box_rows);
+cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& a, cudaStream_t st);
+int slice_gemm_tile_m();
+int slice_gemm_tile_n();
+size_t slice_gemm_smem_bytes();
+
+// ---------------------------------------------------------------------------------- native FP64
+struct NativeArgs {
+  char ta = 'N', tb = 'N';
+  int64_t m = 0, n = 0, k = 0;
+  const double* A = nullptr;
+  int64_t lda = 0;
+  const double* B = nullptr;
+  int64_t ldb = 0;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double alpha[2] = {1, 0}, beta[2] = {0, 0};
+  int beta_zero = 1;
+  int cplx = 0;
+  const int* gate = nullptr;  // if non-null, the kernel only runs when *gate != 0
+};
+cudaError_t launch_native_gemm(const NativeArgs& a, cudaStream_t st);
+
+// C = beta * C (beta == 0: zero fill), m x n, complex if cplx
+cudaError_t launch_scale_c(double* C, int64_t m, int64_t n, int64_t ldc, const double* beta, int cplx,
+                           cudaStream_t st);
+
+}  // namespace ozg

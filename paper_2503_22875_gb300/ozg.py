@@ -1,0 +1,174 @@
+"""Thin ctypes binding to the CUDA library libozg.so (include/ozg.h).
+
+Argument marshalling only: every step of the emulated GEMM runs in the library's kernels.
+PyTorch is used for device memory and streams (tensors are passed by ``data_ptr()``).
+There is no CPU fallback: if the library is missing the import of this binding fails.
+
+Matrices follow BLAS conventions (column-major).  A column-major m x n matrix with leading
+dimension m has the same bytes as a row-major torch tensor of shape (n, m); the helpers
+``to_device`` / ``from_device`` convert numpy arrays to and from that layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OzgError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what} failed with code {code}: {strerror(code)}"
+        if code == 1:
+            msg += f" ({last_cuda_error()})"
+        super().__init__(msg)
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("slices_used", ctypes.c_int), ("nonfinite", ctypes.c_int), ("status", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libozg.so (built by ``__graft_entry__.build()`` / ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} is missing (run paper_2503_22875_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    i64, dbl, i32, ch, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_int, ctypes.c_char, ctypes.c_void_p
+    L.ozg_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t]
+    L.ozg_destroy.argtypes = [vp]
+    L.ozg_set_stream.argtypes = [vp, vp]
+    L.ozg_sync.argtypes = [vp]
+    L.ozg_strerror.argtypes = [i32]
+    L.ozg_strerror.restype = ctypes.c_char_p
+    L.ozg_last_cuda_error.restype = ctypes.c_char_p
+    L.ozg_dgemm.argtypes = [vp, ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
+    L.ozg_zgemm.argtypes = [vp, ch, ch, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, i32, vp]
+    L.ozg_native_dgemm.argtypes = [vp, ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64]
+    L.ozg_native_zgemm.argtypes = [vp, ch, ch, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64]
+    L.ozg_debug_split.argtypes = [vp, ch, i64, i64, vp, i64, i32, vp, vp]
+    L.ozg_debug_zsplit.argtypes = [vp, ch, i64, i64, vp, i64, i32, vp, vp]
+    L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().ozg_strerror(int(code)).decode()
+
+
+def last_cuda_error() -> str:
+    return load().ozg_last_cuda_error().decode()
+
+
+def _p(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _c(t: str) -> bytes:
+    return t.encode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != 0:
+        raise OzgError(rc, what)
+    return rc
+
+
+class Context:
+    """An ozg_ctx: owns device workspace and queues work on one CUDA stream."""
+
+    def __init__(self, workspace_bytes: int = 0, stream=None):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.ozg_create(ctypes.byref(h), int(workspace_bytes)), "ozg_create")
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().ozg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None (legacy default)."""
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        _check(load().ozg_set_stream(self._h, ctypes.c_void_p(raw)), "ozg_set_stream")
+
+    def sync(self):
+        _check(load().ozg_sync(self._h), "ozg_sync")
+
+    def dgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, report=False):
+        rep = Report() if report else None
+        rc = load().ozg_dgemm(self._h, _c(transa), _c(transb), m, n, k, float(alpha), _p(A), lda, _p(B), ldb,
+                              float(beta), _p(C), ldc, int(slices), ctypes.byref(rep) if rep else None)
+        _check(rc, "ozg_dgemm")
+        return rep
+
+    def zgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, report=False):
+        rep = Report() if report else None
+        al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+        rc = load().ozg_zgemm(self._h, _c(transa), _c(transb), m, n, k, al, _p(A), lda, _p(B), ldb, be, _p(C), ldc,
+                              int(slices), ctypes.byref(rep) if rep else None)
+        _check(rc, "ozg_zgemm")
+        return rep
+
+    def native_dgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc):
+        _check(load().ozg_native_dgemm(self._h, _c(transa), _c(transb), m, n, k, float(alpha), _p(A), lda, _p(B),
+                                       ldb, float(beta), _p(C), ldc), "ozg_native_dgemm")
+
+    def native_zgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc):
+        al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+        _check(load().ozg_native_zgemm(self._h, _c(transa), _c(transb), m, n, k, al, _p(A), lda, _p(B), ldb, be,
+                                       _p(C), ldc), "ozg_native_zgemm")
+
+    def debug_split(self, trans, rows, k, X, ld, slices, e_out, digits_out, complex_=False):
+        f = load().ozg_debug_zsplit if complex_ else load().ozg_debug_split
+        _check(f(self._h, _c(trans), rows, k, _p(X), ld, int(slices), _p(e_out), _p(digits_out)), "ozg_debug_split")
+
+    def debug_group_products(self, transa, transb, m, n, k, A, lda, B, ldb, slices, G_out):
+        _check(load().ozg_debug_group_products(self._h, _c(transa), _c(transb), m, n, k, _p(A), lda, _p(B), ldb,
+                                               int(slices), _p(G_out)), "ozg_debug_group_products")
+
+
+# ------------------------------------------------------------------- layout helpers (marshalling)
+def to_device(x: np.ndarray, device="cuda"):
+    """numpy (m, n) -> torch tensor holding the column-major bytes of x (shape (n, m))."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.asfortranarray(x).T)).to(device)
+
+
+def from_device(t, m: int, n: int) -> np.ndarray:
+    """Inverse of to_device for an m x n column-major matrix stored in t."""
+    a = t.detach().cpu().numpy().reshape(n, m)
+    return np.asfortranarray(a.T)

@@ -1,0 +1,81 @@
+"""Seeded synthetic inputs shaped like the workloads of the paper's study (Sec. 3.2 / 4).
+
+This module holds no arithmetic of the emulation method: it only draws random matrices, so it
+can feed both the CUDA path and the CPU oracle.  numpy PCG64 generators with fixed seeds.
+
+  uniform_pair          A, B ~ U(-1, 1)                         (small DGEMM, m = n = k = 256)
+  wide_exponent_pair    a = (u - 0.5) exp(phi g), u ~ U(0,1), g ~ N(0,1)   (8192^3 DGEMM sweep)
+  kkr_like_pair         complex n = 113 blocks x 32, block (i,j) ~ CN(0,1) exp(-|r_i - r_j|)
+                        with atom sites r ~ U(cube of unit density) plus (1 + 0.1i) on the
+                        diagonal -- stands in for the MuST "MT u56" ZGEMMs of Sec. 3.2
+  grouped_batch         2048 GEMMs, m, n, k log-uniform in [32, 2048], phi ~ U(0, 4) per call
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def uniform_pair(m: int, n: int, k: int, seed: int = 1):
+    g = rng(seed)
+    A = np.asfortranarray(g.uniform(-1.0, 1.0, size=(m, k)))
+    B = np.asfortranarray(g.uniform(-1.0, 1.0, size=(k, n)))
+    return A, B
+
+
+def wide_exponent(shape, phi: float, g: np.random.Generator) -> np.ndarray:
+    u = g.random(size=shape)
+    z = g.standard_normal(size=shape)
+    return np.asfortranarray((u - 0.5) * np.exp(phi * z))
+
+
+def wide_exponent_pair(m: int, n: int, k: int, phi: float, seed: int = 2):
+    g = rng(seed)
+    return wide_exponent((m, k), phi, g), wide_exponent((k, n), phi, g)
+
+
+def _kkr_matrix(nblk: int, bs: int, g: np.random.Generator, shift: complex) -> np.ndarray:
+    L = nblk ** (1.0 / 3.0)
+    r = g.uniform(0.0, L, size=(nblk, 3))
+    d = np.sqrt(((r[:, None, :] - r[None, :, :]) ** 2).sum(-1))
+    scale = np.exp(-d)  # (nblk, nblk)
+    n = nblk * bs
+    M = (g.standard_normal(size=(n, n)) + 1j * g.standard_normal(size=(n, n))) / np.sqrt(2.0)
+    M *= np.repeat(np.repeat(scale, bs, axis=0), bs, axis=1)
+    M[np.arange(n), np.arange(n)] += shift
+    return np.asfortranarray(M)
+
+
+def kkr_like_pair(nblk: int = 113, bs: int = 32, seed: int = 3, shift: complex = 1.0 + 0.1j):
+    """Two independently seeded KKR-like complex matrices of order nblk * bs."""
+    g = rng(seed)
+    A = _kkr_matrix(nblk, bs, g, shift)
+    B = _kkr_matrix(nblk, bs, g, shift)
+    return A, B
+
+
+@dataclass
+class GemmCall:
+    m: int
+    n: int
+    k: int
+    phi: float
+    seed: int
+
+
+def grouped_batch(count: int = 2048, lo: int = 32, hi: int = 2048, phi_hi: float = 4.0, seed: int = 4):
+    """Shapes and per-call exponent spreads of the grouped batch; matrices via call_matrices()."""
+    g = rng(seed)
+    dims = np.exp(g.uniform(np.log(lo), np.log(hi), size=(count, 3))).round().astype(int)
+    phis = g.uniform(0.0, phi_hi, size=count)
+    seeds = g.integers(0, 2 ** 31 - 1, size=count)
+    return [GemmCall(int(d[0]), int(d[1]), int(d[2]), float(p), int(s)) for d, p, s in zip(dims, phis, seeds)]
+
+
+def call_matrices(c: GemmCall):
+    return wide_exponent_pair(c.m, c.n, c.k, c.phi, seed=c.seed)

@@ -1,0 +1,306 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+  * split exponents and INT8 digits: bit-exact (integer work)
+  * integer group products G_g from the tensor-core kernel: bit-exact
+  * emulated DGEMM / ZGEMM: within a tolerance derived from the FP64 epilogue (Horner over the
+    s groups in FP64, one rounding per step) -- |C_gpu - C_oracle| <= 4 (s + 2) u |alpha| (|A||B|)
+    + 2 u |C| + u |beta| |C0| -- and within the a priori bound of the method against
+    double-double.
+  * native FP64 kernel: within gamma_k of double-double.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_22875_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def ozg():
+    from paper_2503_22875_gb300 import build, ozg
+    build.build()
+    ozg.load()
+    return ozg
+
+
+@pytest.fixture(scope="module")
+def ctx(ozg):
+    c = ozg.Context()
+    yield c
+    c.close()
+
+
+def dev(ozg, x):
+    return ozg.to_device(x)
+
+
+def host(ozg, t, m, n):
+    return ozg.from_device(t, m, n)
+
+
+def wide(shape, phi, seed, zeros=True):
+    g = workloads.rng(seed)
+    X = workloads.wide_exponent(shape, phi, g)
+    if zeros and X.size > 3:
+        X.flat[:: max(7, X.size // 5)] = 0.0
+    return np.asfortranarray(X)
+
+
+# ----------------------------------------------------------------------------- split
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("rows,k,s", [(1, 1, 1), (37, 70, 7), (200, 131, 3), (64, 1000, 12), (5, 9, 18)])
+def test_split_bit_exact(ozg, ctx, trans, rows, k, s):
+    X = wide((rows, k) if trans == "N" else (k, rows), 6.0, rows * 1000 + k)
+    if X.size > 10:
+        X.flat[3] = 2.0 ** -1074
+        X.flat[5] = -3.5e-310
+    dX = dev(ozg, X)
+    e = torch.empty(rows, dtype=torch.int32, device="cuda")
+    d = torch.empty((s, rows, k), dtype=torch.int8, device="cuda")
+    ctx.debug_split(trans, rows, k, dX, X.shape[0], s, e, d)
+    e_o, d_o = oracle.split(X, s, trans)
+    assert np.array_equal(e.cpu().numpy(), e_o)
+    assert np.array_equal(d.cpu().numpy(), d_o)
+
+
+@pytest.mark.parametrize("trans", ["N", "T", "C"])
+def test_zsplit_bit_exact(ozg, ctx, trans):
+    rows, k, s = 45, 77, 9
+    shape = (rows, k) if trans == "N" else (k, rows)
+    X = wide(shape, 3.0, 5) + 1j * wide(shape, 3.0, 6)
+    dX = dev(ozg, X)
+    e = torch.empty(rows, dtype=torch.int32, device="cuda")
+    d = torch.empty((s, 2 * rows, k), dtype=torch.int8, device="cuda")
+    ctx.debug_split(trans, rows, k, dX, X.shape[0], s, e, d, complex_=True)
+    e_o, d_o = oracle.zsplit(X, s, trans)
+    assert np.array_equal(e.cpu().numpy(), e_o)
+    assert np.array_equal(d.cpu().numpy(), d_o)
+
+
+# ----------------------------------------------------------------------------- group products
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("m,n,k,s", [(128, 256, 64, 3), (130, 300, 1100, 4), (7, 5, 3, 7), (257, 513, 200, 8)])
+def test_group_products_bit_exact(ozg, ctx, ta, tb, m, n, k, s):
+    A = wide((m, k) if ta == "N" else (k, m), 2.0, m + 1)
+    B = wide((k, n) if tb == "N" else (n, k), 2.0, n + 2)
+    G = torch.empty((s, m, n), dtype=torch.int64, device="cuda")
+    ctx.debug_group_products(ta, tb, m, n, k, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], s, G)
+    _, DA = oracle.split(A, s, ta)
+    _, DB = oracle.split(B, s, "T" if tb == "N" else "N")
+    G_o = oracle.group_products(DA, DB)
+    assert np.array_equal(G.cpu().numpy(), G_o)
+
+
+def test_group_products_max_digits_chain_boundary(ozg, ctx):
+    # every digit +-127 and k crossing several 1024-product chains: the largest exact FP32 sums
+    s, k = 4, 1000
+    v = 1.0 - 2.0 ** (-7 * s - 3)
+    g = workloads.rng(9)
+    A = np.asfortranarray(v * g.choice([-1.0, 1.0], size=(130, k)))
+    A[:, :] = np.abs(A)  # all positive: chains reach the largest magnitude
+    B = np.asfortranarray(np.full((k, 260), v))
+    G = torch.empty((s, 130, 260), dtype=torch.int64, device="cuda")
+    ctx.debug_group_products("N", "N", 130, 260, k, dev(ozg, A), 130, dev(ozg, B), k, s, G)
+    _, DA = oracle.split(A, s)
+    _, DB = oracle.split_cols(B, s)
+    G_o = oracle.group_products(DA, DB)
+    assert G_o[s - 1].max() == s * k * 127 * 127
+    assert np.array_equal(G.cpu().numpy(), G_o)
+
+
+# ----------------------------------------------------------------------------- emulated DGEMM
+def check_dgemm(C, A, B, s, ta, tb, alpha, beta, C0):
+    E = oracle.dgemm_emu(A, B, s, ta, tb, alpha, beta, C0)
+    AB = oracle.abs_product(A, B, ta, tb)
+    tol = 4 * (s + 2) * U * abs(alpha) * AB + 2 * U * np.abs(E)
+    if C0 is not None and beta != 0:
+        tol = tol + 2 * U * abs(beta) * np.abs(C0)
+    diff = np.abs(C - E)
+    assert (diff <= tol).all(), f"max excess {(diff - tol).max():.3e}"
+    # and the method's own a priori bound against double-double
+    hi, lo = oracle.dgemm_dd(A, B, ta, tb, alpha, beta, C0)
+    bnd = abs(alpha) * (oracle.emu_bound(A, B, s, ta, tb) + (s + 4) * U * AB) + 2 * U * np.abs(hi)
+    if C0 is not None and beta != 0:
+        bnd = bnd + 2 * U * abs(beta) * np.abs(C0)
+    assert (np.abs((C - hi) - lo) <= bnd).all()
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+@pytest.mark.parametrize("m,n,k,s", [(256, 256, 256, 7), (300, 520, 130, 3), (33, 257, 31, 5), (129, 255, 1500, 6),
+                                     (1, 1, 1, 1), (17, 600, 64, 10)])
+def test_dgemm_parity(ozg, ctx, ta, tb, m, n, k, s):
+    A = wide((m, k) if ta == "N" else (k, m), 2.0, 11 * m + k)
+    B = wide((k, n) if tb == "N" else (n, k), 2.0, 13 * n + k)
+    C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    rep = ctx.dgemm(ta, tb, m, n, k, 1.0, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], 0.0, C, m, s,
+                    report=True)
+    assert rep.slices_used == s and rep.nonfinite == 0
+    ctx.sync()
+    check_dgemm(host(ozg, C, m, n), A, B, s, ta, tb, 1.0, 0.0, None)
+
+
+@pytest.mark.parametrize("alpha,beta", [(1.0, 1.0), (-0.5, 0.25), (2.0, -1.0), (3.0, 0.0)])
+def test_dgemm_alpha_beta_and_ldc(ozg, ctx, alpha, beta):
+    m, n, k, s = 150, 270, 90, 7
+    A, B = workloads.uniform_pair(m, n, k, seed=21)
+    ldc = m + 5
+    C0 = np.asfortranarray(workloads.rng(22).uniform(-1, 1, (ldc, n)))
+    dC = dev(ozg, C0)
+    ctx.dgemm("N", "N", m, n, k, alpha, dev(ozg, A), m, dev(ozg, B), k, beta, dC, ldc, s)
+    ctx.sync()
+    Cg = host(ozg, dC, ldc, n)
+    check_dgemm(Cg[:m], A, B, s, "N", "N", alpha, beta, C0[:m])
+    assert np.array_equal(Cg[m:], C0[m:])  # rows between m and ldc untouched
+
+
+def test_dgemm_lda_padding_and_beta_zero_ignores_nan(ozg, ctx):
+    m, n, k, s = 100, 90, 80, 6
+    Af = wide((m + 3, k), 1.0, 31)
+    Bf = wide((k + 2, n), 1.0, 32)
+    C0 = np.full((m, n), np.nan, order="F")
+    dC = dev(ozg, C0)
+    ctx.dgemm("N", "N", m, n, k, 1.0, dev(ozg, Af), m + 3, dev(ozg, Bf), k + 2, 0.0, dC, m, s)
+    ctx.sync()
+    C = host(ozg, dC, m, n)
+    assert np.isfinite(C).all()
+    check_dgemm(C, np.asfortranarray(Af[:m]), np.asfortranarray(Bf[:k]), s, "N", "N", 1.0, 0.0, None)
+
+
+def test_dgemm_quick_returns(ozg, ctx):
+    m, n, k = 40, 30, 20
+    A, B = workloads.uniform_pair(m, n, k, seed=41)
+    C0 = np.asfortranarray(workloads.rng(42).uniform(-1, 1, (m, n)))
+    for alpha, beta, kk, expect in [(0.0, 1.0, k, C0), (1.0, 1.0, 0, C0), (0.0, 2.5, k, 2.5 * C0),
+                                    (1.0, 0.0, 0, np.zeros_like(C0))]:
+        dC = dev(ozg, C0)
+        ctx.dgemm("N", "N", m, n, kk, alpha, dev(ozg, A), m, dev(ozg, B), max(kk, 1), beta, dC, m, 7)
+        ctx.sync()
+        assert np.array_equal(host(ozg, dC, m, n), expect)
+    dC = dev(ozg, C0)
+    ctx.dgemm("N", "N", 0, n, k, 1.0, dev(ozg, A), 1, dev(ozg, B), k, 0.0, dC, 1, 7)  # m == 0: no-op
+    ctx.sync()
+    assert np.array_equal(host(ozg, dC, m, n), C0)
+
+
+def test_nonfinite_routes_to_native(ozg, ctx):
+    m, n, k = 64, 48, 40
+    A, B = workloads.uniform_pair(m, n, k, seed=51)
+    A[3, 7] = np.inf
+    B[2, 5] = np.nan
+    dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    rep = ctx.dgemm("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, dC, m, 7, report=True)
+    assert rep.nonfinite == 1 and rep.slices_used == -1
+    C = host(ozg, dC, m, n)
+    ref = oracle.dgemm_naive(A, B)
+    same = (np.isnan(C) == np.isnan(ref)) & (np.isinf(C) == np.isinf(ref))
+    assert same.all()
+    fin = np.isfinite(ref)
+    np.testing.assert_allclose(C[fin], ref[fin], rtol=1e-13, atol=1e-13)
+
+
+def test_slices_monotone_error(ozg, ctx):
+    m = n = k = 192
+    A, B = workloads.wide_exponent_pair(m, n, k, 2.0, seed=61)
+    dA, dB = dev(ozg, A), dev(ozg, B)
+    errs = []
+    for s in range(3, 10):
+        C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+        ctx.dgemm("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, C, m, s)
+        ctx.sync()
+        errs.append(oracle.rel_err_vs_dd(host(ozg, C, m, n), A, B))
+    for a, b in zip(errs, errs[1:]):
+        assert b <= a / 20 or b < 1e-15
+
+
+# ----------------------------------------------------------------------------- emulated ZGEMM
+def check_zgemm(C, A, B, s, ta, tb, alpha, beta, C0):
+    E = oracle.zgemm_emu(A, B, s, ta, tb, alpha, beta, C0)
+    opA = A if ta == "N" else (A.T if ta == "T" else A.conj().T)
+    opB = B if tb == "N" else (B.T if tb == "T" else B.conj().T)
+    AB = (np.abs(opA.real) + np.abs(opA.imag)) @ (np.abs(opB.real) + np.abs(opB.imag))
+    tol = 8 * (s + 2) * U * abs(alpha) * AB + 4 * U * np.abs(E)
+    if C0 is not None and beta != 0:
+        tol = tol + 4 * U * abs(beta) * np.abs(C0)
+    assert (np.abs(C.real - E.real) <= tol).all()
+    assert (np.abs(C.imag - E.imag) <= tol).all()
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("C", "N"), ("T", "C"), ("N", "T"), ("C", "C")])
+@pytest.mark.parametrize("m,n,k,s", [(64, 128, 96, 7), (77, 150, 333, 4), (3, 5, 2, 9)])
+def test_zgemm_parity(ozg, ctx, ta, tb, m, n, k, s):
+    shA = (m, k) if ta == "N" else (k, m)
+    shB = (k, n) if tb == "N" else (n, k)
+    A = wide(shA, 1.5, m + k) + 1j * wide(shA, 1.5, m + k + 1)
+    B = wide(shB, 1.5, n + k) + 1j * wide(shB, 1.5, n + k + 1)
+    C = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    ctx.zgemm(ta, tb, m, n, k, 1.0, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], 0.0, C, m, s)
+    ctx.sync()
+    check_zgemm(host(ozg, C, m, n), A, B, s, ta, tb, 1.0, 0.0, None)
+
+
+def test_zgemm_alpha_beta(ozg, ctx):
+    m, n, k, s = 90, 70, 50, 8
+    A, B = workloads.kkr_like_pair(nblk=3, bs=32, seed=71)
+    A, B = np.asfortranarray(A[:m, :k]), np.asfortranarray(B[:k, :n])
+    C0 = np.asfortranarray(workloads.rng(72).normal(size=(m, n)) + 1j * workloads.rng(73).normal(size=(m, n)))
+    al, be = 0.5 - 2j, 1.5 + 0.25j
+    dC = dev(ozg, C0)
+    ctx.zgemm("N", "N", m, n, k, al, dev(ozg, A), m, dev(ozg, B), k, be, dC, m, s)
+    ctx.sync()
+    check_zgemm(host(ozg, dC, m, n), A, B, s, "N", "N", al, be, C0)
+
+
+# ----------------------------------------------------------------------------- native FP64
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T"), ("N", "T")])
+def test_native_dgemm(ozg, ctx, ta, tb):
+    m, n, k = 131, 77, 203
+    A = wide((m, k) if ta == "N" else (k, m), 2.0, 81)
+    B = wide((k, n) if tb == "N" else (n, k), 2.0, 82)
+    C0 = np.asfortranarray(workloads.rng(83).normal(size=(m, n)))
+    dC = dev(ozg, C0)
+    ctx.native_dgemm(ta, tb, m, n, k, 1.5, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], -0.5, dC, m)
+    ctx.sync()
+    C = host(ozg, dC, m, n)
+    hi, lo = oracle.dgemm_dd(A, B, ta, tb, 1.5, -0.5, C0)
+    AB = oracle.abs_product(A, B, ta, tb)
+    gk = (k + 2) * U / (1 - (k + 2) * U)
+    assert (np.abs(C - hi - lo) <= gk * (1.5 * AB + 0.5 * np.abs(C0)) + 2 * U * np.abs(hi)).all()
+
+
+def test_native_zgemm_and_slices_minus_one(ozg, ctx):
+    m, n, k = 40, 33, 65
+    A = wide((k, m), 1.0, 91) + 1j * wide((k, m), 1.0, 92)
+    B = wide((k, n), 1.0, 93) + 1j * wide((k, n), 1.0, 94)
+    dC = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    ctx.zgemm("C", "N", m, n, k, 1.0, dev(ozg, A), k, dev(ozg, B), k, 0.0, dC, m, -1)
+    ctx.sync()
+    C = host(ozg, dC, m, n)
+    ref = A.conj().T @ B
+    np.testing.assert_allclose(C, ref, rtol=0, atol=4 * k * U * np.abs(ref).max() + 1e-15)
+
+
+# ----------------------------------------------------------------------------- full size, sampled
+def test_full_size_dgemm_sampled(ozg, ctx):
+    """The 8192^3 wide-exponent DGEMM in the benchmark's launch configuration; sampled rows and
+    columns are checked against the oracle (per-row / per-column scales make the sampled block's
+    emulation identical to the full one's)."""
+    m = n = k = 8192
+    s = 7
+    A, B = workloads.wide_exponent_pair(m, n, k, 0.5, seed=2)
+    dA, dB = dev(ozg, A), dev(ozg, B)
+    dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    ctx.dgemm("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dC, m, s)
+    ctx.sync()
+    g = workloads.rng(99)
+    rows = np.sort(g.choice(m, 24, replace=False))
+    cols = np.sort(g.choice(n, 24, replace=False))
+    rows = np.concatenate([rows, [0, m - 1]])
+    cols = np.concatenate([cols, [0, n - 1]])
+    Cs = dC.cpu().numpy().T[np.ix_(rows, cols)]
+    As = np.asfortranarray(A[rows])
+    Bs = np.asfortranarray(B[:, cols])
+    check_dgemm(Cs, As, Bs, s, "N", "N", 1.0, 0.0, None)
