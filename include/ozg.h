@@ -54,13 +54,15 @@ extern "C" {
 
 typedef struct ozg_ctx ozg_ctx;
 
-/* Per-call report.  Fields are filled when the call returns (host-known fields) and after
- * ozg_sync() (device-computed fields). */
+/* Per-call report.  When a report is requested the call synchronises its stream before
+ * returning, so every field is final on return. */
 typedef struct ozg_report {
   int slices_used;        /* s actually used; -1 when the call ran in native FP64 */
   int nonfinite;          /* 1 if an input held Inf/NaN and the call was routed to native FP64 */
   int status;             /* OZG_OK or a positive error code for this call */
-  int reserved;
+  int samples;            /* entries checked in double-double (0: check disabled) */
+  double est_err;         /* max over the samples of |C - C_dd| / (|alpha||A||B| + |beta||C_old|);
+                             NaN when not checked or routed to native FP64 */
 } ozg_report;
 
 /* Create a context on the current CUDA device.  workspace_bytes pre-reserves device
@@ -78,6 +80,12 @@ int ozg_set_stream(ozg_ctx* ctx, void* stream);
  * status raised since the previous ozg_sync (OZG_ERR_TIMEOUT if a bounded wait expired). */
 int ozg_sync(ozg_ctx* ctx);
 
+/* Sampled error check (the per-result error report): samples > 0 makes every later emulated
+ * call recompute `samples` output entries (the four corners plus hashed positions) in
+ * double-double on the GPU after the GEMM and report the largest componentwise error relative
+ * to |alpha||A||B| + |beta||C_old| in ozg_report.est_err.  0 disables (the default). */
+int ozg_set_check_samples(ozg_ctx* ctx, int samples);
+
 /* Human-readable text for a return code (static storage). */
 const char* ozg_strerror(int code);
 
@@ -88,8 +96,8 @@ const char* ozg_strerror(int code);
  *   beta == 0: C is not read (NaNs in C are ignored).  Quick returns: m == 0 or n == 0, or
  *   ((alpha == 0 or k == 0) and beta == 1).  alpha == 0 or k == 0 gives C = beta C.
  *   Inputs holding Inf/NaN are detected on the device and the call is completed by the native
- *   FP64 kernel (still on the GPU); rep->nonfinite is set after ozg_sync.
- *   rep may be NULL. */
+ *   FP64 kernel (still on the GPU); rep->nonfinite reports it.
+ *   rep may be NULL (asynchronous call); with a report the call returns after its work finished. */
 int ozg_dgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
               int64_t ldc, int slices, ozg_report* rep);
@@ -133,6 +141,22 @@ int ozg_debug_zsplit(ozg_ctx* ctx, char trans, int64_t rows, int64_t k, const do
 int ozg_debug_group_products(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
                              const double* A, int64_t lda, const double* B, int64_t ldb, int slices,
                              int64_t* G_out);
+
+/* ---- per-phase device timing (CUDA events on the context's stream) ---- */
+#define OZG_PHASE_SPLIT 0    /* exponent + digit extraction of both operands */
+#define OZG_PHASE_GEMM 1     /* fused slice-product GEMM + epilogue */
+#define OZG_PHASE_NATIVE 2   /* native FP64 kernel (native mode, or the gated non-finite path) */
+#define OZG_PHASE_CHECK 3    /* sampled double-double error check */
+#define OZG_PHASE_SELECT 4   /* learned slice selector */
+#define OZG_NUM_PHASES 8
+
+/* enable != 0: every later call records a CUDA event pair around each of its phases. */
+int ozg_set_profiling(ozg_ctx* ctx, int enable);
+
+/* Synchronise the context's stream, then return the device milliseconds accumulated per
+ * phase since the previous call (ms[OZG_NUM_PHASES]) and the number of timed launches per
+ * phase (counts[OZG_NUM_PHASES]); either pointer may be NULL.  Resets the accumulators. */
+int ozg_phase_times(ozg_ctx* ctx, double* ms, int64_t* counts);
 
 /* Message of the last failing CUDA runtime call seen by the library in this process. */
 const char* ozg_last_cuda_error(void);

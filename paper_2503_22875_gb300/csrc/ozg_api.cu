@@ -2,9 +2,11 @@
 // workspace management and the launch sequence of the emulated GEMM:
 //   split(op(A)) -> split(op(B)) -> fused slice-GEMM + epilogue -> native kernel gated on
 //   the non-finite flag (runs only if an input held Inf/NaN).
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "../../include/ozg.h"
 #include "ozg_internal.h"
@@ -16,6 +18,19 @@ struct ozg_ctx {
   void* ws = nullptr;
   size_t ws_cap = 0;
   int* dflags = nullptr;  // [0] status (sticky until ozg_sync), [1] non-finite flag of the last call
+  double* dcheck = nullptr;  // [0] max sampled error of the last call, [1..] C_old at the samples
+  int check_samples = 0;
+  uint64_t check_seed = 0x5EED;
+  // per-phase timing
+  bool prof = false;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> pending;
+  std::vector<cudaEvent_t> pool;
+  double acc_ms[OZG_NUM_PHASES] = {};
+  int64_t acc_n[OZG_NUM_PHASES] = {};
 };
 
 namespace {
@@ -70,6 +85,40 @@ int ensure_ws(ozg_ctx* c, size_t bytes) {
   return OZG_OK;
 }
 
+cudaEvent_t pool_get(ozg_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Records an event pair around one phase on the context stream when profiling is on.
+struct PhaseScope {
+  ozg_ctx* c;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(ozg_ctx* c_, int ph) : c(c_), phase(ph) {
+    if (c->prof && (a = pool_get(c)) != nullptr) cudaEventRecord(a, c->stream);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    cudaEvent_t b = pool_get(c);
+    if (!b) {
+      c->pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({phase, a, b});
+  }
+};
+
 template <typename T>
 T* at(ozg_ctx* c, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(c->ws) + off);
@@ -110,12 +159,14 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   size_t oE = cv.take(4 * (size_t)m), oF = cv.take(4 * (size_t)n);
   size_t oMA = cv.take(8 * (size_t)m), oMB = cv.take(8 * (size_t)n);
   size_t oR = cv.take((size_t)grid * BM * BN * 8);
+  size_t oCold = cv.take((size_t)(c->check_samples > 0 ? c->check_samples : 1) * 16);
   int rc = ensure_ws(c, cv.off);
   if (rc) return rc;
   cudaStream_t st = c->stream;
   int* nonfinite = c->dflags + 1;
   OZG_CUDA(cudaMemsetAsync(nonfinite, 0, sizeof(int), st));
 
+  PhaseScope* split_scope = new PhaseScope(c, OZG_PHASE_SPLIT);
   ozg::SplitArgs sa;
   sa.X = A;
   sa.ld = lda;
@@ -131,7 +182,11 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   sa.maxbits = at<unsigned long long>(c, oMA);
   sa.exps = at<int32_t>(c, oE);
   sa.nonfinite = nonfinite;
-  OZG_CUDA(ozg::launch_split(sa, st));
+  {
+    cudaError_t e = ozg::launch_split(sa, st);
+    if (e != cudaSuccess) delete split_scope;
+    OZG_CUDA(e);
+  }
   ozg::SplitArgs sb = sa;
   sb.X = B;
   sb.ld = ldb;
@@ -142,7 +197,11 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   sb.D = at<__half>(c, oDB);
   sb.maxbits = at<unsigned long long>(c, oMB);
   sb.exps = at<int32_t>(c, oF);
-  OZG_CUDA(ozg::launch_split(sb, st));
+  {
+    cudaError_t e = ozg::launch_split(sb, st);
+    delete split_scope;
+    OZG_CUDA(e);
+  }
 
   CUtensorMap tmA, tmB;
   OZG_CUDA(ozg::make_digit_tmap(&tmA, sa.D, k, prA, Kp, s, BM));
@@ -169,7 +228,37 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   ga.status = c->dflags;
   ga.nonfinite = Gdbg ? nullptr : nonfinite;
   ga.grid = grid;
-  OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB, ga, st));
+  ozg::CheckArgs ck;
+  if (c->check_samples > 0 && !Gdbg) {
+    ck.ta = ta;
+    ck.tb = tb;
+    ck.m = m;
+    ck.n = n;
+    ck.k = k;
+    ck.A = A;
+    ck.lda = lda;
+    ck.B = B;
+    ck.ldb = ldb;
+    ck.C = C;
+    ck.ldc = ldc;
+    ck.alpha[0] = ga.alpha[0];
+    ck.alpha[1] = ga.alpha[1];
+    ck.beta[0] = ga.beta[0];
+    ck.beta[1] = ga.beta[1];
+    ck.beta_zero = ga.beta_zero;
+    ck.cplx = cplx;
+    ck.nsamp = c->check_samples;
+    ck.seed = c->check_seed++;
+    ck.cold = at<double>(c, oCold);
+    ck.err_out = c->dcheck;
+    ck.gate = nonfinite;
+    PhaseScope ps(c, OZG_PHASE_CHECK);
+    OZG_CUDA(ozg::launch_check_pre(ck, st));
+  }
+  {
+    PhaseScope ps(c, OZG_PHASE_GEMM);
+    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB, ga, st));
+  }
   if (Gdbg) return OZG_OK;
 
   ozg::NativeArgs na;
@@ -191,13 +280,24 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   na.beta_zero = ga.beta_zero;
   na.cplx = cplx;
   na.gate = nonfinite;
-  OZG_CUDA(ozg::launch_native_gemm(na, st));
+  {
+    PhaseScope ps(c, OZG_PHASE_NATIVE);
+    OZG_CUDA(ozg::launch_native_gemm(na, st));
+  }
+  if (c->check_samples > 0) {
+    PhaseScope ps(c, OZG_PHASE_CHECK);
+    OZG_CUDA(ozg::launch_check_post(ck, st));
+  }
   if (rep) {
     int h = 0;
+    double err = 0.0;
     OZG_CUDA(cudaMemcpyAsync(&h, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (c->check_samples > 0) OZG_CUDA(cudaMemcpyAsync(&err, c->dcheck, sizeof(double), cudaMemcpyDeviceToHost, st));
     OZG_CUDA(cudaStreamSynchronize(st));
     rep->nonfinite = h;
     rep->slices_used = h ? -1 : s;
+    rep->samples = (c->check_samples > 0 && !h) ? c->check_samples : 0;
+    rep->est_err = rep->samples ? err : NAN;
   }
   return OZG_OK;
 }
@@ -213,6 +313,7 @@ int gemm_entry(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, in
   if (rep) {
     std::memset(rep, 0, sizeof(*rep));
     rep->slices_used = native ? -1 : slices;
+    rep->est_err = NAN;
   }
   if (m == 0 || n == 0) return OZG_OK;
   const bool alpha_zero = alpha[0] == 0.0 && (!cplx || alpha[1] == 0.0);
@@ -242,7 +343,10 @@ int gemm_entry(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, in
     na.beta[1] = cplx ? beta[1] : 0.0;
     na.beta_zero = beta[0] == 0.0 && (!cplx || beta[1] == 0.0);
     na.cplx = cplx;
-    OZG_CUDA(ozg::launch_native_gemm(na, c->stream));
+    {
+      PhaseScope ps(c, OZG_PHASE_NATIVE);
+      OZG_CUDA(ozg::launch_native_gemm(na, c->stream));
+    }
     if (rep) rep->slices_used = -1;
     return OZG_OK;
   }
@@ -259,6 +363,11 @@ int ozg_create(ozg_ctx** out, size_t workspace_bytes) {
   ozg_ctx* c = new ozg_ctx();
   OZG_CUDA(cudaGetDevice(&c->device));
   OZG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  if (cudaMalloc(&c->dcheck, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return OZG_ERR_ALLOC;
+  }
   if (cudaMalloc(&c->dflags, 4 * sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -280,9 +389,22 @@ int ozg_create(ozg_ctx** out, size_t workspace_bytes) {
 int ozg_destroy(ozg_ctx* c) {
   if (!c) return OZG_OK;
   cudaStreamSynchronize(c->stream);
+  for (auto& mk : c->pending) {
+    cudaEventDestroy(mk.a);
+    cudaEventDestroy(mk.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
   if (c->ws) cudaFree(c->ws);
   if (c->dflags) cudaFree(c->dflags);
+  if (c->dcheck) cudaFree(c->dcheck);
   delete c;
+  return OZG_OK;
+}
+
+int ozg_set_check_samples(ozg_ctx* c, int samples) {
+  if (!c) return OZG_ERR_INVALID;
+  if (samples < 0 || samples > (1 << 20)) return -2;
+  c->check_samples = samples;
   return OZG_OK;
 }
 
@@ -315,6 +437,36 @@ const char* ozg_strerror(int code) {
 }
 
 const char* ozg_last_cuda_error(void) { return g_last_cuda; }
+
+int ozg_set_profiling(ozg_ctx* c, int enable) {
+  if (!c) return OZG_ERR_INVALID;
+  c->prof = enable != 0;
+  return OZG_OK;
+}
+
+int ozg_phase_times(ozg_ctx* c, double* ms, int64_t* counts) {
+  if (!c) return OZG_ERR_INVALID;
+  OZG_CUDA(cudaStreamSynchronize(c->stream));
+  for (auto& mk : c->pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, mk.a, mk.b) == cudaSuccess) {
+      c->acc_ms[mk.phase] += t;
+      c->acc_n[mk.phase] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(mk.a);
+    c->pool.push_back(mk.b);
+  }
+  c->pending.clear();
+  for (int i = 0; i < OZG_NUM_PHASES; ++i) {
+    if (ms) ms[i] = c->acc_ms[i];
+    if (counts) counts[i] = c->acc_n[i];
+    c->acc_ms[i] = 0.0;
+    c->acc_n[i] = 0;
+  }
+  return OZG_OK;
+}
 
 int ozg_dgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
               const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,

@@ -1,0 +1,161 @@
+// K8: per-call error report.  For S sampled output entries (i, j) the kernel recomputes
+// alpha * sum_l op(A)_il op(B)_lj + beta * C_old in double-double (the "quad using double"
+// arithmetic of Sec. 2.2: TwoProd by fma, TwoSum) and returns
+//   max |C_ij - ref_ij| / (|alpha| (|A||B|)_ij + |beta| |C_old,ij|)
+// -- the componentwise error relative to |A||B|.  One warp per sample; lanes split k.
+// For complex data the four real sub-sums are tracked and both parts are checked.
+#include "ozg_internal.h"
+
+namespace ozg {
+namespace {
+
+struct dd {
+  double hi, lo;
+};
+__device__ __forceinline__ dd two_sum(double a, double b) {
+  double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dd fast_two_sum(double a, double b) {
+  double s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dd dd_add_prod(dd a, double x, double y) {  // a + x*y
+  double p = x * y;
+  double e = fma(x, y, -p);
+  return dd_add(a, {p, e});
+}
+__device__ __forceinline__ dd dd_shfl_xor(dd a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ void sample_ij(const CheckArgs& P, int idx, int64_t& i, int64_t& j) {
+  // the four corners first, then hashed positions
+  if (idx < 4) {
+    i = (idx & 1) ? P.m - 1 : 0;
+    j = (idx & 2) ? P.n - 1 : 0;
+    return;
+  }
+  uint64_t h = splitmix64(P.seed + (uint64_t)idx);
+  i = (int64_t)((h & 0xFFFFFFFFull) % (uint64_t)P.m);
+  j = (int64_t)((h >> 32) % (uint64_t)P.n);
+}
+
+__device__ __forceinline__ double ld_op(const double* X, int64_t ld, char t, int64_t r, int64_t c, int cplx,
+                                        double* im) {
+  if (!cplx) return (t == 'N') ? X[r + c * ld] : X[c + r * ld];
+  const double* p = (t == 'N') ? X + 2 * (r + c * ld) : X + 2 * (c + r * ld);
+  *im = (t == 'C') ? -p[1] : p[1];
+  return p[0];
+}
+
+__global__ void check_pre(CheckArgs P) {
+  if (P.gate != nullptr && *P.gate) return;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= P.nsamp) return;
+  int64_t i, j;
+  sample_ij(P, idx, i, j);
+  if (!P.cplx) {
+    P.cold[2 * idx] = P.C[i + j * P.ldc];
+    P.cold[2 * idx + 1] = 0.0;
+  } else {
+    P.cold[2 * idx] = P.C[2 * (i + j * P.ldc)];
+    P.cold[2 * idx + 1] = P.C[2 * (i + j * P.ldc) + 1];
+  }
+}
+
+__global__ void check_post(CheckArgs P) {
+  if (P.gate != nullptr && *P.gate) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P.nsamp) return;
+  int64_t i, j;
+  sample_ij(P, warp, i, j);
+  dd re = {0, 0}, im = {0, 0};
+  double sabs = 0.0;
+  for (int64_t l = lane; l < P.k; l += 32) {
+    double ai = 0, bi = 0;
+    const double ar = ld_op(P.A, P.lda, P.ta, i, l, P.cplx, &ai);
+    const double br = ld_op(P.B, P.ldb, P.tb, l, j, P.cplx, &bi);
+    re = dd_add_prod(re, ar, br);
+    if (P.cplx) {
+      re = dd_add_prod(re, -ai, bi);
+      im = dd_add_prod(im, ar, bi);
+      im = dd_add_prod(im, ai, br);
+      sabs += (fabs(ar) + fabs(ai)) * (fabs(br) + fabs(bi));
+    } else {
+      sabs += fabs(ar) * fabs(br);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re = dd_add(re, dd_shfl_xor(re, o));
+    im = dd_add(im, dd_shfl_xor(im, o));
+    sabs += __shfl_xor_sync(0xffffffffu, sabs, o);
+  }
+  if (lane != 0) return;
+  const double cr_old = P.beta_zero ? 0.0 : P.cold[2 * warp], ci_old = P.beta_zero ? 0.0 : P.cold[2 * warp + 1];
+  double err;
+  if (!P.cplx) {
+    // ref = alpha * re + beta * c_old, kept to double-double accuracy before the comparison
+    dd ref = {P.alpha[0] * re.hi, fma(P.alpha[0], re.hi, -P.alpha[0] * re.hi) + P.alpha[0] * re.lo};
+    if (!P.beta_zero) ref = dd_add_prod(ref, P.beta[0], cr_old);
+    const double c = P.C[i + j * P.ldc];
+    const double diff = fabs((c - ref.hi) - ref.lo);
+    const double scale = fabs(P.alpha[0]) * sabs + fabs(P.beta[0]) * fabs(cr_old);
+    err = scale > 0 ? diff / scale : (diff > 0 ? INFINITY : 0.0);
+  } else {
+    dd rr = {0, 0}, ri = {0, 0};
+    rr = dd_add_prod(rr, P.alpha[0], re.hi);
+    rr = dd_add_prod(rr, P.alpha[0], re.lo);
+    rr = dd_add_prod(rr, -P.alpha[1], im.hi);
+    rr = dd_add_prod(rr, -P.alpha[1], im.lo);
+    ri = dd_add_prod(ri, P.alpha[0], im.hi);
+    ri = dd_add_prod(ri, P.alpha[0], im.lo);
+    ri = dd_add_prod(ri, P.alpha[1], re.hi);
+    ri = dd_add_prod(ri, P.alpha[1], re.lo);
+    if (!P.beta_zero) {
+      rr = dd_add_prod(rr, P.beta[0], cr_old);
+      rr = dd_add_prod(rr, -P.beta[1], ci_old);
+      ri = dd_add_prod(ri, P.beta[0], ci_old);
+      ri = dd_add_prod(ri, P.beta[1], cr_old);
+    }
+    const double* cp = P.C + 2 * (i + j * P.ldc);
+    const double d = fmax(fabs((cp[0] - rr.hi) - rr.lo), fabs((cp[1] - ri.hi) - ri.lo));
+    const double scale = (fabs(P.alpha[0]) + fabs(P.alpha[1])) * sabs +
+                         (fabs(P.beta[0]) + fabs(P.beta[1])) * (fabs(cr_old) + fabs(ci_old));
+    err = scale > 0 ? d / scale : (d > 0 ? INFINITY : 0.0);
+  }
+  // non-negative doubles order like their bit patterns; NaN (bits above +Inf) wins the max
+  atomicMax(reinterpret_cast<unsigned long long*>(P.err_out), (unsigned long long)__double_as_longlong(err));
+}
+
+}  // namespace
+
+cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st) {
+  if (a.nsamp <= 0 || a.beta_zero) return cudaSuccess;
+  check_pre<<<(a.nsamp + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st) {
+  if (a.nsamp <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.err_out, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int warps_per_block = 4;
+  check_post<<<(a.nsamp + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace ozg

@@ -76,6 +76,28 @@ struct NativeArgs {
 };
 cudaError_t launch_native_gemm(const NativeArgs& a, cudaStream_t st);
 
+// ---------------------------------------------------------------------------------- sampled check
+struct CheckArgs {
+  char ta = 'N', tb = 'N';
+  int64_t m = 0, n = 0, k = 0;
+  const double* A = nullptr;
+  int64_t lda = 0;
+  const double* B = nullptr;
+  int64_t ldb = 0;
+  const double* C = nullptr;
+  int64_t ldc = 0;
+  double alpha[2] = {1, 0}, beta[2] = {0, 0};
+  int beta_zero = 1;
+  int cplx = 0;
+  int nsamp = 0;
+  uint64_t seed = 0;
+  double* cold = nullptr;     // [nsamp][2] C_old at the samples (beta != 0)
+  double* err_out = nullptr;  // max error (device double), reset by launch_check_post
+  const int* gate = nullptr;  // skip when *gate != 0 (call routed to native FP64)
+};
+cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st);
+cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st);
+
 // C = beta * C (beta == 0: zero fill), m x n, complex if cplx
 cudaError_t launch_scale_c(double* C, int64_t m, int64_t n, int64_t ldc, const double* beta, int cplx,
                            cudaStream_t st);

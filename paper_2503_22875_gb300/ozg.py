@@ -31,7 +31,7 @@ class OzgError(RuntimeError):
 
 class Report(ctypes.Structure):
     _fields_ = [("slices_used", ctypes.c_int), ("nonfinite", ctypes.c_int), ("status", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("samples", ctypes.c_int), ("est_err", ctypes.c_double)]
 
 
 def lib_path() -> str:
@@ -61,6 +61,9 @@ def load():
     L.ozg_native_zgemm.argtypes = [vp, ch, ch, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64]
     L.ozg_debug_split.argtypes = [vp, ch, i64, i64, vp, i64, i32, vp, vp]
     L.ozg_debug_zsplit.argtypes = [vp, ch, i64, i64, vp, i64, i32, vp, vp]
+    L.ozg_set_profiling.argtypes = [vp, i32]
+    L.ozg_set_check_samples.argtypes = [vp, i32]
+    L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
     _lib = L
     return L
@@ -125,6 +128,21 @@ class Context:
 
     def sync(self):
         _check(load().ozg_sync(self._h), "ozg_sync")
+
+    PHASES = ("split", "gemm", "native", "check", "select")
+
+    def set_check_samples(self, samples: int):
+        _check(load().ozg_set_check_samples(self._h, int(samples)), "ozg_set_check_samples")
+
+    def set_profiling(self, enable: bool = True):
+        _check(load().ozg_set_profiling(self._h, int(bool(enable))), "ozg_set_profiling")
+
+    def phase_times(self):
+        """{phase: (device ms, launches)} accumulated since the previous call (synchronises)."""
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_int64 * 8)()
+        _check(load().ozg_phase_times(self._h, ms, n), "ozg_phase_times")
+        return {name: (ms[i], n[i]) for i, name in enumerate(self.PHASES)}
 
     def dgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, report=False):
         rep = Report() if report else None

@@ -304,3 +304,45 @@ def test_full_size_dgemm_sampled(ozg, ctx):
     As = np.asfortranarray(A[rows])
     Bs = np.asfortranarray(B[:, cols])
     check_dgemm(Cs, As, Bs, s, "N", "N", 1.0, 0.0, None)
+
+
+# ----------------------------------------------------------------------------- sampled dd check
+@pytest.mark.parametrize("s", [3, 5, 8])
+def test_sampled_check_estimate(ozg, ctx, s):
+    """The GPU double-double check reports the error of sampled entries: never above the true
+    maximum over all entries (oracle), and of the same order (errors are homogeneous here)."""
+    m, n, k = 160, 300, 700
+    A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=101)
+    dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    ctx.set_check_samples(256)
+    try:
+        rep = ctx.dgemm("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, dC, m, s, report=True)
+    finally:
+        ctx.set_check_samples(0)
+    full = oracle.rel_err_vs_dd(host(ozg, dC, m, n), A, B)
+    assert rep.samples == 256
+    assert rep.est_err <= full * (1 + 1e-9) + 1e-300
+    assert rep.est_err >= full / 50
+
+
+def test_sampled_check_beta_and_complex(ozg, ctx):
+    m, n, k, s = 70, 90, 120, 4
+    A = wide((m, k), 1.0, 111) + 1j * wide((m, k), 1.0, 112)
+    B = wide((k, n), 1.0, 113) + 1j * wide((k, n), 1.0, 114)
+    C0 = np.asfortranarray(workloads.rng(115).normal(size=(m, n)) + 1j * workloads.rng(116).normal(size=(m, n)))
+    dC = dev(ozg, C0)
+    ctx.set_check_samples(128)
+    try:
+        rep = ctx.zgemm("N", "N", m, n, k, 0.5 + 1j, dev(ozg, A), m, dev(ozg, B), k, -1.0 + 0.5j, dC, m, s,
+                        report=True)
+        assert rep.samples == 128 and 0 < rep.est_err < 1e-5
+        # real, beta != 0
+        Ar, Br = A.real.copy(order="F"), B.real.copy(order="F")
+        C0r = np.asfortranarray(C0.real)
+        dCr = dev(ozg, C0r)
+        rep = ctx.dgemm("N", "N", m, n, k, 2.0, dev(ozg, Ar), m, dev(ozg, Br), k, 0.5, dCr, m, s, report=True)
+        Cg = host(ozg, dCr, m, n)
+        full = oracle.rel_err_vs_dd(Cg, Ar, Br, alpha=2.0, beta=0.5, C0=C0r)
+        assert 0 < rep.est_err <= full * (1 + 1e-9)
+    finally:
+        ctx.set_check_samples(0)
