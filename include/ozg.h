@@ -142,6 +142,31 @@ int ozg_debug_group_products(ozg_ctx* ctx, char transa, char transb, int64_t m, 
                              const double* A, int64_t lda, const double* B, int64_t ldb, int slices,
                              int64_t* G_out);
 
+/* ---- emulated DGEMM without any device allocation ----
+ * No counterpart in the paper.  For callers that must not call cudaMalloc: code running while
+ * its stream is captured into a CUDA graph (allocation cannot be captured), an interposed
+ * dgemm_ inside a host application that owns all device memory through its own pool or a
+ * fixed budget, and latency-critical paths where cudaMalloc / cudaFree would synchronise the
+ * device.  Same arithmetic, kernels and results as ozg_dgemm (transa, transb in N/T; slices
+ * 1..18 or -1 for native FP64), but no context: the work is queued on `stream` (a cudaStream_t,
+ * NULL = legacy default stream) and all scratch lives in one fixed device array of
+ * OZG_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library's device
+ * code holds until the process exits.
+ *   - The problem must fit the array: about 2 s (m + n) round8(k) + 12 (m + n) bytes plus at
+ *     least one 256 KiB tile of FP64 partial sums (e.g. m = n = k = 1024, s = 8 fits; 2048 does
+ *     not).  Larger problems return OZG_ERR_UNSUPPORTED before any work is queued.
+ *   - The first call on each device resolves the array's device address (cudaGetSymbolAddress,
+ *     with that device current); make that first call before any stream capture begins.
+ *   - Every call reuses the same array; each call clears what must start at zero.  Calls whose
+ *     work overlaps on the GPU (other streams, unordered host threads) race on the array.
+ *   - Asynchronous; device-side wait time-outs are not reported by this entry point (C is then
+ *     unspecified).  Inf/NaN inputs are handled as in ozg_dgemm (native FP64 on the GPU).
+ * Returns 0, a BLAS argument error -i, OZG_ERR_UNSUPPORTED (too large) or OZG_ERR_CUDA. */
+#define OZG_NOALLOC_SCRATCH_BYTES (64u << 20)
+int ozg_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                      int64_t ldc, int slices, void* stream);
+
 /* ---- per-phase device timing (CUDA events on the context's stream) ---- */
 #define OZG_PHASE_SPLIT 0    /* exponent + digit extraction of both operands */
 #define OZG_PHASE_GEMM 1     /* fused slice-product GEMM + epilogue */

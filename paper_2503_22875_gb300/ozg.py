@@ -64,6 +64,7 @@ def load():
     L.ozg_set_profiling.argtypes = [vp, i32]
     L.ozg_set_check_samples.argtypes = [vp, i32]
     L.ozg_phase_times.argtypes = [vp, vp, vp]
+    L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
     _lib = L
     return L
@@ -177,6 +178,14 @@ class Context:
     def debug_group_products(self, transa, transb, m, n, k, A, lda, B, ldb, slices, G_out):
         _check(load().ozg_debug_group_products(self._h, _c(transa), _c(transb), m, n, k, _p(A), lda, _p(B), ldb,
                                                int(slices), _p(G_out)), "ozg_debug_group_products")
+
+
+def dgemm_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, stream=None) -> int:
+    """ozg_dgemm_noalloc: the emulated DGEMM with no device allocation (fixed in-library scratch),
+    for callers that cannot call cudaMalloc.  Returns the library's return code unchanged."""
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    return int(load().ozg_dgemm_noalloc(_c(transa), _c(transb), m, n, k, float(alpha), _p(A), lda, _p(B), ldb,
+                                        float(beta), _p(C), ldc, int(slices), ctypes.c_void_p(raw)))
 
 
 # ------------------------------------------------------------------- layout helpers (marshalling)
