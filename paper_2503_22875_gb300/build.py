@@ -12,6 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libozg.so")
+SHIM_SRC = os.path.join(HERE, "shim", "ozg_blas_shim.cpp")
+SHIM_LIB = os.path.join(BUILD, "libozg_blas.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -32,13 +34,13 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
-        [os.path.join(ROOT, "include", "ozg.h"), __file__]
+        [os.path.join(ROOT, "include", "ozg.h"), os.path.join(ROOT, "include", "ozg_blas.h"), SHIM_SRC, __file__]
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(SHIM_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(SHIM_LIB))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -70,6 +72,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    # the BLAS interposition library, linked against libozg.so (found next to it at run time)
+    tmp = SHIM_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, *ARCH, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", SHIM_SRC, "-o", tmp,
+                        "-L", BUILD, "-lozg", "-Xlinker", "-rpath", "-Xlinker", "$ORIGIN", "-ldl"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"shim build failed:\n{r.stderr}")
+    os.replace(tmp, SHIM_LIB)
     return LIB
 
 

@@ -1,0 +1,241 @@
+// libozg_blas.so: Fortran dgemm_ / zgemm_ that offload a host program's BLAS calls to the GPU
+// emulation (the automatic-offload side of the paper, Sec. 3.1: one preloaded library that
+// intercepts the BLAS call and runs it on the GPU in the mode named by an environment
+// variable).  Data movement is the explicit-copy strategy of Sec. 2.1: host memory -> pinned
+// staging -> device, and back.  See include/ozg_blas.h for the contract.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/ozg.h"
+#include "../../include/ozg_blas.h"
+
+namespace {
+
+typedef void (*gemm_fn)(const char*, const char*, const int*, const int*, const int*, const double*, const double*,
+                        const int*, const double*, const int*, const double*, double*, const int*, size_t, size_t);
+
+std::mutex g_mu;
+ozg_ctx* g_ctx = nullptr;
+cudaStream_t g_stream = nullptr;
+int g_mode = 0;  // 0: not read yet
+long long g_min_mnk = 0;
+void* g_pinned = nullptr;
+size_t g_pinned_cap = 0;
+void* g_dev = nullptr;
+size_t g_dev_cap = 0;
+gemm_fn g_next_d = nullptr, g_next_z = nullptr;
+bool g_resolved = false;
+std::atomic<long long> g_offloaded{0}, g_passed{0};
+
+char upper(char c) { return (c >= 'a' && c <= 'z') ? (char)(c - 'a' + 'A') : c; }
+
+int parse_mode(const char* s) {
+  if (!s) return 0;
+  if (std::strcmp(s, "dgemm") == 0) return OZG_NATIVE;
+  const char* pre = "fp64_int8_";
+  size_t n = std::strlen(pre);
+  if (std::strncmp(s, pre, n) != 0) return 0;
+  const char* p = s + n;
+  if (!*p) return 0;
+  int v = 0;
+  for (; *p; ++p) {
+    if (*p < '0' || *p > '9') return 0;
+    v = v * 10 + (*p - '0');
+    if (v > OZG_MAX_SLICES) return 0;
+  }
+  return (v >= 1) ? v : 0;
+}
+
+void init_locked() {
+  if (g_mode == 0) {
+    const char* e = std::getenv("OZG_COMPUTE_MODE");
+    int m = e ? parse_mode(e) : 7;
+    if (m == 0) {
+      std::fprintf(stderr, "ozg_blas: invalid OZG_COMPUTE_MODE '%s'; using fp64_int8_7\n", e);
+      m = 7;
+    }
+    g_mode = m;
+    const char* t = std::getenv("OZG_OFFLOAD_MIN_MNK");
+    g_min_mnk = t ? std::atoll(t) : 0;
+  }
+  if (!g_resolved) {
+    g_next_d = reinterpret_cast<gemm_fn>(dlsym(RTLD_NEXT, "dgemm_"));
+    g_next_z = reinterpret_cast<gemm_fn>(dlsym(RTLD_NEXT, "zgemm_"));
+    g_resolved = true;
+  }
+}
+
+bool ensure_gpu_locked() {
+  if (g_ctx) return true;
+  if (ozg_create(&g_ctx, 0) != OZG_OK) {
+    g_ctx = nullptr;
+    return false;
+  }
+  if (cudaStreamCreateWithFlags(&g_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    g_stream = nullptr;
+  }
+  ozg_set_stream(g_ctx, g_stream);
+  return true;
+}
+
+bool grow(void** buf, size_t* cap, size_t need, bool pinned) {
+  if (need <= *cap) return true;
+  if (*buf) {
+    if (pinned)
+      cudaFreeHost(*buf);
+    else
+      cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+  }
+  size_t want = need + need / 4;
+  cudaError_t e = pinned ? cudaMallocHost(buf, want) : cudaMalloc(buf, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return false;
+  }
+  *cap = want;
+  return true;
+}
+
+void xerbla(const char* name, int info) {
+  std::fprintf(stderr, " ** On entry to %s parameter number %2d had an illegal value\n", name, info);
+}
+
+// elements spanned by a column-major rows x cols block with leading dimension ld
+size_t span(long long rows, long long cols, long long ld) {
+  if (rows <= 0 || cols <= 0) return 0;
+  return (size_t)((cols - 1) * ld + rows);
+}
+
+// Shared body of dgemm_ / zgemm_ (esz = 8 or 16 bytes per element).
+void gemm_offload(bool cplx, const char* transa, const char* transb, const int* pm, const int* pn, const int* pk,
+                  const double* alpha, const double* A, const int* plda, const double* B, const int* pldb,
+                  const double* beta, double* C, const int* pldc, size_t la, size_t lb) {
+  const char* name = cplx ? "ZGEMM " : "DGEMM ";
+  char ta = upper(*transa), tb = upper(*transb);
+  const int m = *pm, n = *pn, k = *pk, lda = *plda, ldb = *pldb, ldc = *pldc;
+  auto ok_t = [&](char t) { return t == 'N' || t == 'T' || t == 'C'; };
+  int info = 0;
+  int nrowa = (ta == 'N') ? m : k, nrowb = (tb == 'N') ? k : n;
+  if (!ok_t(ta)) info = 1;
+  else if (!ok_t(tb)) info = 2;
+  else if (m < 0) info = 3;
+  else if (n < 0) info = 4;
+  else if (k < 0) info = 5;
+  else if (lda < (nrowa > 1 ? nrowa : 1)) info = 8;
+  else if (ldb < (nrowb > 1 ? nrowb : 1)) info = 10;
+  else if (ldc < (m > 1 ? m : 1)) info = 13;
+  if (info) {
+    xerbla(name, info);
+    return;
+  }
+  const bool alpha_zero = alpha[0] == 0.0 && (!cplx || alpha[1] == 0.0);
+  const bool beta_one = beta[0] == 1.0 && (!cplx || beta[1] == 0.0);
+  const bool beta_zero = beta[0] == 0.0 && (!cplx || beta[1] == 0.0);
+  if (m == 0 || n == 0 || ((alpha_zero || k == 0) && beta_one)) return;
+
+  std::lock_guard<std::mutex> lk(g_mu);
+  init_locked();
+  gemm_fn next = cplx ? g_next_z : g_next_d;
+  if (next && (long long)m * n * k < g_min_mnk) {
+    ++g_passed;
+    next(transa, transb, pm, pn, pk, alpha, A, plda, B, pldb, beta, C, pldc, la, lb);
+    return;
+  }
+  const size_t esz = cplx ? 16 : 8;
+  const size_t sA = span(nrowa, (ta == 'N') ? k : m, lda), sB = span(nrowb, (tb == 'N') ? n : k, ldb);
+  const size_t sC = span(m, n, ldc);
+  const size_t oA = 0, oB = (oA + sA * esz + 255) / 256 * 256, oC = (oB + sB * esz + 255) / 256 * 256;
+  const size_t total = oC + sC * esz;
+  bool gpu = ensure_gpu_locked() && grow(&g_pinned, &g_pinned_cap, total, true) &&
+             grow(&g_dev, &g_dev_cap, total, false);
+  int rc = OZG_ERR_ALLOC;
+  if (gpu) {
+    char* hp = static_cast<char*>(g_pinned);
+    char* dp = static_cast<char*>(g_dev);
+    if (sA) std::memcpy(hp + oA, A, sA * esz);
+    if (sB) std::memcpy(hp + oB, B, sB * esz);
+    const bool need_c = !beta_zero;
+    if (need_c) std::memcpy(hp + oC, C, sC * esz);
+    const size_t up = need_c ? total : oC;
+    cudaError_t e = cudaMemcpyAsync(dp, hp, up, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess) {
+      const double* dA = reinterpret_cast<const double*>(dp + oA);
+      const double* dB = reinterpret_cast<const double*>(dp + oB);
+      double* dC = reinterpret_cast<double*>(dp + oC);
+      // k == 0 or alpha == 0 never reads A / B; give the library valid (unused) pointers
+      rc = cplx ? ozg_zgemm(g_ctx, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, g_mode, nullptr)
+                : ozg_dgemm(g_ctx, ta, tb, m, n, k, alpha[0], dA, lda, dB, ldb, beta[0], dC, ldc, g_mode, nullptr);
+      if (rc == OZG_OK) {
+        e = cudaMemcpyAsync(hp + oC, dC, sC * esz, cudaMemcpyDeviceToHost, g_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
+        if (e == cudaSuccess) rc = ozg_sync(g_ctx);
+        else rc = OZG_ERR_CUDA;
+      }
+    } else {
+      rc = OZG_ERR_CUDA;
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    if (rc == OZG_OK) {
+      for (int j = 0; j < n; ++j)  // rows m .. ldc-1 of each column stay untouched
+        std::memcpy(reinterpret_cast<char*>(C) + (size_t)j * ldc * esz, hp + oC + (size_t)j * ldc * esz,
+                    (size_t)m * esz);
+      ++g_offloaded;
+      return;
+    }
+  }
+  if (next) {
+    std::fprintf(stderr, "ozg_blas: GPU path failed (%s); using the CPU BLAS\n", ozg_strerror(rc));
+    ++g_passed;
+    next(transa, transb, pm, pn, pk, alpha, A, plda, B, pldb, beta, C, pldc, la, lb);
+  } else {
+    std::fprintf(stderr, "ozg_blas: GPU path failed (%s) and no CPU BLAS is loaded; C is unchanged\n",
+                 ozg_strerror(rc));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void dgemm_(const char* transa, const char* transb, const int* m, const int* n, const int* k, const double* alpha,
+            const double* A, const int* lda, const double* B, const int* ldb, const double* beta, double* C,
+            const int* ldc, size_t la, size_t lb) {
+  gemm_offload(false, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, la, lb);
+}
+
+void zgemm_(const char* transa, const char* transb, const int* m, const int* n, const int* k, const double* alpha,
+            const double* A, const int* lda, const double* B, const int* ldb, const double* beta, double* C,
+            const int* ldc, size_t la, size_t lb) {
+  gemm_offload(true, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, la, lb);
+}
+
+int ozg_blas_parse_mode(const char* mode) { return parse_mode(mode); }
+
+int ozg_blas_get_mode(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  init_locked();
+  return g_mode;
+}
+
+int ozg_blas_set_mode(int slices) {
+  if (slices == 0 || slices < OZG_NATIVE || slices > OZG_MAX_SLICES) return -1;
+  std::lock_guard<std::mutex> lk(g_mu);
+  init_locked();
+  g_mode = slices;
+  return 0;
+}
+
+long long ozg_blas_offloaded_calls(void) { return g_offloaded.load(); }
+long long ozg_blas_passed_calls(void) { return g_passed.load(); }
+
+}  // extern "C"

@@ -68,3 +68,19 @@ def test_zgemm_accepts_conjugate_and_checks_args(lib):
 def test_null_context(lib):
     assert lib.ozg_sync(None) == 5
     assert lib.ozg_destroy(None) == 0
+
+
+def test_blas_shim_exports_and_mode_parsing():
+    from paper_2503_22875_gb300 import build
+    build.build()
+    shim = ctypes.CDLL(build.SHIM_LIB)
+    txt = open(os.path.join(ROOT, "include", "ozg_blas.h")).read()
+    names = re.findall(r"^(?:void|int|long long)\s+(\w+)\s*\(", txt, re.M)
+    assert {"dgemm_", "zgemm_", "ozg_blas_parse_mode"} <= set(names)
+    for n in names:
+        assert hasattr(shim, n), n
+    shim.ozg_blas_parse_mode.argtypes = [ctypes.c_char_p]
+    cases = {b"dgemm": -1, b"fp64_int8_3": 3, b"fp64_int8_18": 18, b"fp64_int8_7": 7, b"fp64_int8_19": 0,
+             b"fp64_int8_0": 0, b"fp64_int8_": 0, b"fp64_int8_x": 0, b"int8_7": 0, b"": 0, b"DGEMM": 0}
+    for s, v in cases.items():
+        assert shim.ozg_blas_parse_mode(s) == v, s
