@@ -119,6 +119,50 @@ int ozg_native_zgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t 
                      const double* alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                      const double* beta, double* C, int64_t ldc);
 
+/* ---- grouped (batched) emulated DGEMM ----
+ * Many independent, uneven GEMMs with per-call slice counts in one short launch sequence: a
+ * batched split of every operand, ONE persistent tensor-core launch over the tiles of all calls
+ * (longest-first load balancing across the SMs), a batched native FP64 fallback for calls whose
+ * inputs held Inf/NaN, and a batched sampled error check.  On a non-default context stream the
+ * sequence is captured into a CUDA graph and replayed for as long as the same batch (same
+ * descriptors and slice counts) is submitted again; the matrices' contents may change between
+ * submissions.  Grouping many small GEMMs is the batching addition of the spec design; the
+ * paper has no grouped interface (its offload intercepts one BLAS call at a time, Sec. 3.1). */
+typedef struct ozg_gemm_desc {
+  char transa, transb; /* 'N' or 'T' (case-insensitive; 'C' means 'T') */
+  char reserved[6];    /* set to zero */
+  int64_t m, n, k;
+  double alpha, beta;
+  const double* A; /* device, column-major */
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double* C;
+  int64_t ldc;
+} ozg_gemm_desc;
+
+/* descs: HOST array of count descriptors; slices: HOST array (NULL: all 0), per call 1..18, or
+ * 0 for the context's fallback count (ozg_set_fallback_slices, default 7).  reps: NULL or a HOST
+ * array of count reports (status holds -i for an invalid argument i of that call); with reports
+ * the call returns after the batch finished.  Returns OZG_ERR_INVALID if any descriptor is
+ * invalid (nothing is queued), else 0 or a runtime error. */
+int ozg_dgemm_grouped(ozg_ctx* ctx, int64_t count, const ozg_gemm_desc* descs, const int* slices,
+                      ozg_report* reps);
+
+/* enable != 0 (default): capture grouped calls into CUDA graphs when the context stream is not
+ * the legacy default stream.  Changing it drops the cached graph. */
+int ozg_set_graphs(ozg_ctx* ctx, int enable);
+
+/* Slice count used for calls that request 0 (default 7). */
+int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
+
+/* Tile-shape autotuner: enable != 0 times both tile widths (128 x 256 and 128 x 128 output
+ * tiles) the first time a shape bucket (rounded log2 of m, n, k and the slice count) or a grouped
+ * batch is seen, keeps the faster, and appends single-call choices to cache_path (may be NULL)
+ * as "bucket variant" lines that later contexts read back.  Tuning runs only for calls with
+ * beta == 0, where both widths give bit-identical C; other calls use the padding heuristic. */
+int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
+
 /* ---- inspection entry points (used by the parity tests; same kernels as the GEMM path) ---- */
 
 /* Split the rows of op(X) (rows x k, real FP64, device) into exponents and digit planes, the
@@ -173,6 +217,7 @@ int ozg_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k,
 #define OZG_PHASE_NATIVE 2   /* native FP64 kernel (native mode, or the gated non-finite path) */
 #define OZG_PHASE_CHECK 3    /* sampled double-double error check */
 #define OZG_PHASE_SELECT 4   /* learned slice selector */
+#define OZG_PHASE_GROUPED 5  /* a whole grouped call (graph launch or direct launches) */
 #define OZG_NUM_PHASES 8
 
 /* enable != 0: every later call records a CUDA event pair around each of its phases. */

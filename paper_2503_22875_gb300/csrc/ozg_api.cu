@@ -8,121 +8,10 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/ozg.h"
-#include "ozg_internal.h"
-
-struct ozg_ctx {
-  int device = 0;
-  int num_sms = 0;
-  cudaStream_t stream = nullptr;
-  void* ws = nullptr;
-  size_t ws_cap = 0;
-  int* dflags = nullptr;  // [0] status (sticky until ozg_sync), [1] non-finite flag of the last call
-  double* dcheck = nullptr;  // [0] max sampled error of the last call, [1..] C_old at the samples
-  int check_samples = 0;
-  uint64_t check_seed = 0x5EED;
-  // per-phase timing
-  bool prof = false;
-  struct Mark {
-    int phase;
-    cudaEvent_t a, b;
-  };
-  std::vector<Mark> pending;
-  std::vector<cudaEvent_t> pool;
-  double acc_ms[OZG_NUM_PHASES] = {};
-  int64_t acc_n[OZG_NUM_PHASES] = {};
-};
+#include "ozg_context.h"
 
 namespace {
-
-char g_last_cuda[256] = "no error";
-std::mutex g_err_mu;
-
-int cuda_fail(cudaError_t e) {
-  std::lock_guard<std::mutex> lk(g_err_mu);
-  std::snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
-  return OZG_ERR_CUDA;
-}
-#define OZG_CUDA(x)                              \
-  do {                                           \
-    cudaError_t e_ = (x);                        \
-    if (e_ != cudaSuccess) return cuda_fail(e_); \
-  } while (0)
-
-char norm_trans(char t) {
-  if (t >= 'a' && t <= 'z') t = (char)(t - 'a' + 'A');
-  return t;
-}
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-// Bump allocator over the context workspace.
-struct Carve {
-  size_t off = 0;
-  size_t take(size_t bytes) {
-    size_t o = off;
-    off = align_up(off + bytes, 256);
-    return o;
-  }
-};
-
-int ensure_ws(ozg_ctx* c, size_t bytes) {
-  if (bytes <= c->ws_cap) return OZG_OK;
-  OZG_CUDA(cudaStreamSynchronize(c->stream));
-  if (c->ws) {
-    cudaFree(c->ws);
-    c->ws = nullptr;
-    c->ws_cap = 0;
-  }
-  size_t want = align_up(bytes + bytes / 8, 1 << 20);
-  cudaError_t e = cudaMalloc(&c->ws, want);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    c->ws = nullptr;
-    return OZG_ERR_ALLOC;
-  }
-  c->ws_cap = want;
-  return OZG_OK;
-}
-
-cudaEvent_t pool_get(ozg_ctx* c) {
-  if (!c->pool.empty()) {
-    cudaEvent_t e = c->pool.back();
-    c->pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return e;
-}
-
-// Records an event pair around one phase on the context stream when profiling is on.
-struct PhaseScope {
-  ozg_ctx* c;
-  int phase;
-  cudaEvent_t a = nullptr;
-  PhaseScope(ozg_ctx* c_, int ph) : c(c_), phase(ph) {
-    if (c->prof && (a = pool_get(c)) != nullptr) cudaEventRecord(a, c->stream);
-  }
-  ~PhaseScope() {
-    if (!a) return;
-    cudaEvent_t b = pool_get(c);
-    if (!b) {
-      c->pool.push_back(a);
-      return;
-    }
-    cudaEventRecord(b, c->stream);
-    c->pending.push_back({phase, a, b});
-  }
-};
-
-template <typename T>
-T* at(ozg_ctx* c, size_t off) {
-  return reinterpret_cast<T*>(static_cast<char*>(c->ws) + off);
-}
+using namespace ozg::host;
 
 int check_gemm_args(bool cplx, char& ta, char& tb, int64_t m, int64_t n, int64_t k, int64_t lda, int64_t ldb,
                     int64_t ldc) {
@@ -151,14 +40,18 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
              int s, ozg_report* rep, int64_t* Gdbg) {
   const int64_t Kp = (int64_t)align_up((size_t)k, 8);
   const int64_t prA = cplx ? 2 * m : m, prB = cplx ? 2 * n : n;
-  const int BM = ozg::slice_gemm_tile_m(), BN = ozg::slice_gemm_tile_n();
-  const int64_t tiles = ((prA + BM - 1) / BM) * ((prB + BN - 1) / BN);
-  const int grid = (int)(tiles < c->num_sms ? tiles : c->num_sms);
+  const int BM = ozg::slice_gemm_tile_m();
+  auto grid_of = [&](int variant) {
+    const int BN = ozg::slice_gemm_tile_n_of(variant);
+    const int64_t tiles = ((prA + BM - 1) / BM) * ((prB + BN - 1) / BN);
+    return (int)(tiles < c->num_sms ? tiles : c->num_sms);
+  };
+  const int grid = grid_of(0) > grid_of(1) ? grid_of(0) : grid_of(1);  // R scratch for either width
   Carve cv;
   size_t oDA = cv.take((size_t)s * prA * Kp * 2), oDB = cv.take((size_t)s * prB * Kp * 2);
   size_t oE = cv.take(4 * (size_t)m), oF = cv.take(4 * (size_t)n);
   size_t oMA = cv.take(8 * (size_t)m), oMB = cv.take(8 * (size_t)n);
-  size_t oR = cv.take((size_t)grid * BM * BN * 8);
+  size_t oR = cv.take((size_t)grid * BM * 256 * 8);
   size_t oCold = cv.take((size_t)(c->check_samples > 0 ? c->check_samples : 1) * 16);
   int rc = ensure_ws(c, cv.off);
   if (rc) return rc;
@@ -203,9 +96,11 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     OZG_CUDA(e);
   }
 
-  CUtensorMap tmA, tmB;
+  CUtensorMap tmA, tmB[2];
   OZG_CUDA(ozg::make_digit_tmap(&tmA, sa.D, k, prA, Kp, s, BM));
-  OZG_CUDA(ozg::make_digit_tmap(&tmB, sb.D, k, prB, Kp, s, BN));
+  OZG_CUDA(ozg::make_digit_tmap(&tmB[0], sb.D, k, prB, Kp, s, ozg::slice_gemm_tile_n_of(0)));
+  OZG_CUDA(ozg::make_digit_tmap(&tmB[1], sb.D, k, prB, Kp, s, ozg::slice_gemm_tile_n_of(1)));
+  int variant = choose_variant(c, prA, prB, k, s);
   ozg::GemmArgs ga;
   ga.rows = prA;
   ga.cols = prB;
@@ -227,7 +122,37 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   ga.Gdbg = Gdbg;
   ga.status = c->dflags;
   ga.nonfinite = Gdbg ? nullptr : nonfinite;
-  ga.grid = grid;
+  ga.variant = variant;
+  ga.grid = grid_of(variant);
+  if (c->autotune && !Gdbg && ga.beta_zero) {
+    const uint64_t bucket = shape_bucket(prA, prB, k, s);
+    if (c->tune.find(bucket) == c->tune.end()) {
+      // time both widths on this call (C is write-only here and both give the same bits)
+      float best = 1e30f;
+      for (int v = 0; v < 2; ++v) {
+        ozg::GemmArgs gt = ga;
+        gt.variant = v;
+        gt.grid = grid_of(v);
+        cudaEvent_t e0 = pool_get(c), e1 = pool_get(c);
+        if (!e0 || !e1) return OZG_ERR_CUDA;
+        OZG_CUDA(cudaEventRecord(e0, st));
+        cudaError_t le = ozg::launch_slice_gemm(tmA, tmB[v], gt, st);
+        OZG_CUDA(cudaEventRecord(e1, st));
+        float ms = 1e30f;
+        if (le == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        c->pool.push_back(e0);
+        c->pool.push_back(e1);
+        OZG_CUDA(le);
+        if (ms < best) {
+          best = ms;
+          variant = v;
+        }
+      }
+      tune_store(c, bucket, variant);
+      ga.variant = variant;
+      ga.grid = grid_of(variant);
+    }
+  }
   ozg::CheckArgs ck;
   if (c->check_samples > 0 && !Gdbg) {
     ck.ta = ta;
@@ -257,7 +182,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   }
   {
     PhaseScope ps(c, OZG_PHASE_GEMM);
-    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB, ga, st));
+    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB[ga.variant], ga, st));
   }
   if (Gdbg) return OZG_OK;
 
@@ -363,6 +288,7 @@ int ozg_create(ozg_ctx** out, size_t workspace_bytes) {
   ozg_ctx* c = new ozg_ctx();
   OZG_CUDA(cudaGetDevice(&c->device));
   OZG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  OZG_CUDA(ozg::prepare_kernels());
   if (cudaMalloc(&c->dcheck, sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -436,7 +362,7 @@ const char* ozg_strerror(int code) {
   }
 }
 
-const char* ozg_last_cuda_error(void) { return g_last_cuda; }
+const char* ozg_last_cuda_error(void) { return ozg::host::last_cuda_error_text(); }
 
 int ozg_set_profiling(ozg_ctx* c, int enable) {
   if (!c) return OZG_ERR_INVALID;

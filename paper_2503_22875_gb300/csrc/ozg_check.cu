@@ -61,6 +61,9 @@ __device__ __forceinline__ double ld_op(const double* X, int64_t ld, char t, int
   return p[0];
 }
 
+// One warp per (call, sample); the call's error goes to its own slot of err_out.
+__device__ void check_one(const CheckArgs& P, int sample, int lane, double* err_slot);
+
 __global__ void check_pre(CheckArgs P) {
   if (P.gate != nullptr && *P.gate) return;
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,12 +79,9 @@ __global__ void check_pre(CheckArgs P) {
   }
 }
 
-__global__ void check_post(CheckArgs P) {
-  if (P.gate != nullptr && *P.gate) return;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= P.nsamp) return;
+__device__ void check_one(const CheckArgs& P, int sample, int lane, double* err_slot) {
   int64_t i, j;
-  sample_ij(P, warp, i, j);
+  sample_ij(P, sample, i, j);
   dd re = {0, 0}, im = {0, 0};
   double sabs = 0.0;
   for (int64_t l = lane; l < P.k; l += 32) {
@@ -105,7 +105,7 @@ __global__ void check_post(CheckArgs P) {
     sabs += __shfl_xor_sync(0xffffffffu, sabs, o);
   }
   if (lane != 0) return;
-  const double cr_old = P.beta_zero ? 0.0 : P.cold[2 * warp], ci_old = P.beta_zero ? 0.0 : P.cold[2 * warp + 1];
+  const double cr_old = P.beta_zero ? 0.0 : P.cold[2 * sample], ci_old = P.beta_zero ? 0.0 : P.cold[2 * sample + 1];
   double err;
   if (!P.cplx) {
     // ref = alpha * re + beta * c_old, kept to double-double accuracy before the comparison
@@ -138,7 +138,36 @@ __global__ void check_post(CheckArgs P) {
     err = scale > 0 ? d / scale : (d > 0 ? INFINITY : 0.0);
   }
   // non-negative doubles order like their bit patterns; NaN (bits above +Inf) wins the max
-  atomicMax(reinterpret_cast<unsigned long long*>(P.err_out), (unsigned long long)__double_as_longlong(err));
+  atomicMax(reinterpret_cast<unsigned long long*>(err_slot), (unsigned long long)__double_as_longlong(err));
+}
+
+__global__ void check_post(CheckArgs P) {
+  if (P.gate != nullptr && *P.gate) return;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= P.nsamp) return;
+  check_one(P, warp, lane, P.err_out);
+}
+
+// batched: calls[c] with nsamp samples each; warp w -> call w / nsamp, sample w % nsamp
+__global__ void check_pre_batched(const CheckArgs* calls, int ncalls, int nsamp) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)ncalls * nsamp) return;
+  const CheckArgs P = calls[idx / nsamp];
+  const int smp = (int)(idx % nsamp);
+  if (P.beta_zero || (P.gate != nullptr && *P.gate)) return;
+  int64_t i, j;
+  sample_ij(P, smp, i, j);
+  P.cold[2 * smp] = P.C[i + j * P.ldc];
+  P.cold[2 * smp + 1] = 0.0;
+}
+
+__global__ void check_post_batched(const CheckArgs* calls, int ncalls, int nsamp) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (int64_t)ncalls * nsamp) return;
+  const CheckArgs P = calls[warp / nsamp];
+  if (P.gate != nullptr && *P.gate) return;
+  check_one(P, (int)(warp % nsamp), lane, P.err_out);
 }
 
 }  // namespace
@@ -146,6 +175,23 @@ __global__ void check_post(CheckArgs P) {
 cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st) {
   if (a.nsamp <= 0 || a.beta_zero) return cudaSuccess;
   check_pre<<<(a.nsamp + 127) / 128, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_batched_pre(const CheckArgs* calls_dev, int ncalls, int nsamp, cudaStream_t st) {
+  const int64_t total = (int64_t)ncalls * nsamp;
+  if (total <= 0) return cudaSuccess;
+  check_pre_batched<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(calls_dev, ncalls, nsamp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, int nsamp, double* errs_dev,
+                                      cudaStream_t st) {
+  const int64_t total = (int64_t)ncalls * nsamp;
+  if (total <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(errs_dev, 0, sizeof(double) * ncalls, st);
+  if (e != cudaSuccess) return e;
+  check_post_batched<<<(unsigned)((total + 3) / 4), 128, 0, st>>>(calls_dev, ncalls, nsamp);
   return cudaGetLastError();
 }
 

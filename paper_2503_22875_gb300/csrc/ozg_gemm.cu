@@ -25,26 +25,50 @@
 //                int32 group sums; warp w reads TMEM lanes 32 (w % 4) .. +31 and half
 //                (w - 4) / 4 of the BN columns.
 // Register budget: 384 threads x 168 at launch = 64512 = 128 x 40 + 256 x 232.
+//
+// Two tile widths (BN = 256 or 128; the autotuner picks per shape) and two work sources: one
+// GEMM (tiles rastered in GROUP_M row bands), or a grouped list of tiles drawn from many GEMMs,
+// each with its own tensor maps, slice count and epilogue parameters (one persistent launch
+// for a whole batch of uneven problems).
 #include "ozg_device.cuh"
 #include "ozg_internal.h"
 
 namespace ozg {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 128 + EPI_WARPS * 32;
 constexpr int REG_PRODUCER = 40, REG_EPILOGUE = 232;
 static_assert(128 * REG_PRODUCER + EPI_WARPS * 32 * REG_EPILOGUE <= THREADS * 168, "register split");
 constexpr int SEG_BLOCKS = 16;  // 16 * 64 = 1024 products per chain: 1024 * 127^2 = 16516096 < 2^24
-constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t IDESC = umma_idesc_f16_f32(BM, BN);
-constexpr uint32_t TMEM_COLS = 512;  // two BN-column FP32 accumulators
-constexpr int COLS_PER_THREAD = BN / 2;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024;
-constexpr int GROUP_M = 8;  // tile raster: GROUP_M row-tiles share a sweep over the column tiles
-
+constexpr int GROUP_M = 8;      // tile raster: GROUP_M row-tiles share a sweep over the column tiles
 static_assert(SEG_BLOCKS * BK * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
+
+template <int BN_>
+struct Cfg {
+  static constexpr int BN = BN_;
+  static constexpr int STAGES = BN_ == 256 ? 4 : 6;
+  static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN_ * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr uint32_t IDESC = umma_idesc_f16_f32(BM, BN_);
+  static constexpr uint32_t TMEM_COLS = 2 * BN_;  // two BN-column FP32 accumulators
+  static constexpr int CPT = BN_ / 2;             // columns per epilogue thread
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+};
+
+// Everything one output tile needs, from either work source.
+struct TileJob {
+  const CUtensorMap* tmA;
+  const CUtensorMap* tmB;
+  int tm, tn, KB, s, cplx, skip;
+  int64_t rows, cols, n;  // stacked product rows / cols, output columns (complex: n)
+  const int32_t* e;
+  const int32_t* f;
+  double* C;
+  int64_t ldc;
+  double a0, a1, b0, b1;
+  int beta_zero;
+};
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
   int per_group = GROUP_M * tiles_n;
@@ -54,6 +78,62 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   int r = t % per_group;
   tm = first + r % gsz;
   tn = r / gsz;
+}
+
+template <int BN_, bool GROUPED>
+__device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* P,
+                                           const GroupArgs* G) {
+  TileJob j;
+  if (!GROUPED) {
+    const int tiles_m = (int)((P->rows + BM - 1) / BM), tiles_n = (int)((P->cols + BN_ - 1) / BN_);
+    tile_coords(t, tiles_m, tiles_n, j.tm, j.tn);
+    j.tmA = tmA;
+    j.tmB = tmB;
+    j.KB = (int)((P->k + BK - 1) / BK);
+    j.s = P->s;
+    j.cplx = P->cplx;
+    j.skip = 0;
+    j.rows = P->rows;
+    j.cols = P->cols;
+    j.n = P->n;
+    j.e = P->e;
+    j.f = P->f;
+    j.C = P->C;
+    j.ldc = P->ldc;
+    j.a0 = P->alpha[0];
+    j.a1 = P->alpha[1];
+    j.b0 = P->beta[0];
+    j.b1 = P->beta[1];
+    j.beta_zero = P->beta_zero;
+  } else {
+    const GroupTile gt = G->tiles[t];
+    if (gt.call < 0) {  // padding slot of the load-balanced tile list
+      j.skip = 1;
+      return j;
+    }
+    const GroupCall* c = G->calls + gt.call;
+    j.tm = gt.tm;
+    j.tn = gt.tn;
+    j.tmA = &c->tmA;
+    j.tmB = &c->tmB;
+    j.KB = (int)((c->k + BK - 1) / BK);
+    j.s = c->s;
+    j.cplx = c->cplx;
+    j.skip = (c->nonfinite != nullptr && *c->nonfinite) ? 1 : 0;
+    j.rows = c->rows;
+    j.cols = c->cols;
+    j.n = c->n;
+    j.e = c->e;
+    j.f = c->f;
+    j.C = c->C;
+    j.ldc = c->ldc;
+    j.a0 = c->alpha[0];
+    j.a1 = c->alpha[1];
+    j.b0 = c->beta[0];
+    j.b1 = c->beta[1];
+    j.beta_zero = c->beta_zero;
+  }
+  return j;
 }
 
 __device__ __forceinline__ int nseg_of(int g, int KB) { return ((g - 1) * KB + SEG_BLOCKS - 1) / SEG_BLOCKS; }
@@ -72,16 +152,21 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
-    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      const GemmArgs P) {
-  if (P.nonfinite != nullptr && *P.nonfinite) return;  // the native FP64 kernel handles this call
-
+template <int BN_, bool GROUPED>
+__device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtensorMap* tmB0, const GemmArgs* P,
+                                          const GroupArgs* G) {
+  using K = Cfg<BN_>;
+  constexpr int BN = BN_, STAGES = K::STAGES, CPT = K::CPT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_accf[2], bar_acce[2], bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
+
+  int* status = GROUPED ? G->status : P->status;
+  double* Rws = GROUPED ? G->Rws : P->Rws;
+  int64_t* Gdbg = GROUPED ? nullptr : P->Gdbg;
+  const int ntiles = GROUPED ? G->ntiles : (int)(((P->rows + BM - 1) / BM) * ((P->cols + BN - 1) / BN));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -97,109 +182,112 @@ __global__ void __launch_bounds__(THREADS, 1)
     abort_flag = 0;
     mbar_fence_init();
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
+  if (!GROUPED && warp == 0 && lane == 0) {
+    tma_prefetch_desc(tmA0);
+    tma_prefetch_desc(tmB0);
   }
-  if (warp == 1) tmem_alloc(&tmem_slot, TMEM_COLS);
+  if (warp == 1) tmem_alloc(&tmem_slot, K::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   volatile int* abort_p = &abort_flag;
 
-  const int tiles_m = (int)((P.rows + BM - 1) / BM), tiles_n = (int)((P.cols + BN - 1) / BN);
-  const int ntiles = tiles_m * tiles_n;
-  const int KB = (int)((P.k + BK - 1) / BK);
-  const int s = P.s;
-
   if (warp < 4) {
-   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_PRODUCER));
-   if (warp == 0) {
-    // ------------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      uint32_t stage = 0, phase = 0;
-      long long issued = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        int tm, tn;
-        tile_coords(t, tiles_m, tiles_n, tm, tn);
-        for (int g = 2; g <= s + 1; ++g)
-          for (int kb = 0; kb < KB; ++kb)
-            for (int p = 1; p < g; ++p) {
-              if (!mbar_wait(&bar_empty[stage], phase ^ 1, abort_p, P.status)) goto producer_done;
-              uint8_t* sA = smem + stage * STAGE_BYTES;
-              mbar_arrive_expect_tx(&bar_full[stage], STAGE_BYTES);
-              tma_load_3d(&tmA, &bar_full[stage], sA, kb * BK, tm * BM, p - 1);
-              tma_load_3d(&tmB, &bar_full[stage], sA + A_BYTES, kb * BK, tn * BN, g - p - 1);
-              ++issued;
-              if (++stage == STAGES) {
-                stage = 0;
-                phase ^= 1;
-              }
-            }
-      }
-    producer_done:
-      if (*abort_p) {
-        // wait (bounded) for the copies still in flight into this CTA's shared memory
-        uint32_t st = stage, ph = phase;
-        for (long long i = 0; i < STAGES && i < issued; ++i) {
-          if (st == 0) {
-            st = STAGES - 1;
-            ph ^= 1;
-          } else {
-            --st;
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_PRODUCER));
+    if (warp == 0) {
+      // ---------------------------------------------------------------- TMA producer
+      if (lane == 0) {
+        uint32_t stage = 0, phase = 0;
+        long long issued = 0;
+        const CUtensorMap* last_map = nullptr;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+          const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
+          if (j.skip) continue;
+          if (GROUPED && j.tmA != last_map) {
+            tensormap_acquire(j.tmA);
+            tensormap_acquire(j.tmB);
+            last_map = j.tmA;
           }
-          drain_wait(&bar_full[st], ph);
+          for (int g = 2; g <= j.s + 1; ++g)
+            for (int kb = 0; kb < j.KB; ++kb)
+              for (int p = 1; p < g; ++p) {
+                if (!mbar_wait(&bar_empty[stage], phase ^ 1, abort_p, status)) goto producer_done;
+                uint8_t* sA = smem + stage * K::STAGE_BYTES;
+                mbar_arrive_expect_tx(&bar_full[stage], K::STAGE_BYTES);
+                tma_load_3d(j.tmA, &bar_full[stage], sA, kb * BK, j.tm * BM, p - 1);
+                tma_load_3d(j.tmB, &bar_full[stage], sA + K::A_BYTES, kb * BK, j.tn * BN, g - p - 1);
+                ++issued;
+                if (++stage == STAGES) {
+                  stage = 0;
+                  phase ^= 1;
+                }
+              }
         }
-      }
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      uint32_t stage = 0, phase = 0;
-      uint32_t acc_par = 0;  // bit b: parity of the next use of TMEM buffer b
-      int buf = 0;
-      for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        for (int g = 2; g <= s + 1; ++g) {
-          const int nblk = (g - 1) * KB;
-          int b = 0;
-          for (int kb = 0; kb < KB; ++kb)
-            for (int p = 1; p < g; ++p) {
-              if (b % SEG_BLOCKS == 0) {
-                if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, P.status)) goto mma_done;
-                tc_fence_after();
-              }
-              if (!mbar_wait(&bar_full[stage], phase, abort_p, P.status)) goto mma_done;
-              tc_fence_after();
-              {
-                uint8_t* sA = smem + stage * STAGE_BYTES;
-                uint64_t da = umma_desc_sw128(sA), db = umma_desc_sw128(sA + A_BYTES);
-                uint32_t dt = tmem + (uint32_t)(buf * BN);
-#pragma unroll
-                for (int j = 0; j < BK / 16; ++j)
-                  umma_f16(dt, da + (uint64_t)(2 * j), db + (uint64_t)(2 * j), IDESC,
-                           (b % SEG_BLOCKS != 0 || j != 0) ? 1u : 0u);
-              }
-              umma_commit(&bar_empty[stage]);
-              if (++stage == STAGES) {
-                stage = 0;
-                phase ^= 1;
-              }
-              ++b;
-              if (b % SEG_BLOCKS == 0 || b == nblk) {
-                umma_commit(&bar_accf[buf]);
-                acc_par ^= 1u << buf;
-                buf ^= 1;
-              }
+      producer_done:
+        if (*abort_p) {
+          // wait (bounded) for the copies still in flight into this CTA's shared memory
+          uint32_t st = stage, ph = phase;
+          for (long long i = 0; i < STAGES && i < issued; ++i) {
+            if (st == 0) {
+              st = STAGES - 1;
+              ph ^= 1;
+            } else {
+              --st;
             }
+            drain_wait(&bar_full[st], ph);
+          }
         }
       }
-    mma_done:
-      // all MMAs issued by this thread must finish before TMEM is released
-      umma_commit(&bar_done);
-      drain_wait(&bar_done, 0);
+    } else if (warp == 1) {
+      // ---------------------------------------------------------------- MMA issuer
+      if (lane == 0) {
+        uint32_t stage = 0, phase = 0;
+        uint32_t acc_par = 0;  // bit b: parity of the next use of TMEM buffer b
+        int buf = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+          const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
+          if (j.skip) continue;
+          for (int g = 2; g <= j.s + 1; ++g) {
+            const int nblk = (g - 1) * j.KB;
+            int b = 0;
+            for (int kb = 0; kb < j.KB; ++kb)
+              for (int p = 1; p < g; ++p) {
+                if (b % SEG_BLOCKS == 0) {
+                  if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, status)) goto mma_done;
+                  tc_fence_after();
+                }
+                if (!mbar_wait(&bar_full[stage], phase, abort_p, status)) goto mma_done;
+                tc_fence_after();
+                {
+                  uint8_t* sA = smem + stage * K::STAGE_BYTES;
+                  uint64_t da = umma_desc_sw128(sA), db = umma_desc_sw128(sA + K::A_BYTES);
+                  uint32_t dt = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+                  for (int q = 0; q < BK / 16; ++q)
+                    umma_f16(dt, da + (uint64_t)(2 * q), db + (uint64_t)(2 * q), K::IDESC,
+                             (b % SEG_BLOCKS != 0 || q != 0) ? 1u : 0u);
+                }
+                umma_commit(&bar_empty[stage]);
+                if (++stage == STAGES) {
+                  stage = 0;
+                  phase ^= 1;
+                }
+                ++b;
+                if (b % SEG_BLOCKS == 0 || b == nblk) {
+                  umma_commit(&bar_accf[buf]);
+                  acc_par ^= 1u << buf;
+                  buf ^= 1;
+                }
+              }
+          }
+        }
+      mma_done:
+        // all MMAs issued by this thread must finish before TMEM is released
+        umma_commit(&bar_done);
+        drain_wait(&bar_done, 0);
+      }
     }
-   }
   } else {
     // ------------------------------------------------------------------ epilogue
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPILOGUE));
@@ -207,38 +295,38 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int quad = warp & 3;
     const int chalf = ew >> 2;
     const int r = quad * 32 + lane;
-    const int push_segs = P.cplx ? 32 : 64;  // int32 group sums stay below 2^31
     uint32_t acc_par = 0;
     int buf = 0;
-    double* Rbase = P.Rws + (size_t)blockIdx.x * BM * BN;
+    double* Rbase = Rws + (size_t)blockIdx.x * BM * BN;
     const bool odd = (lane & 1) != 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, tm, tn);
-      const int64_t grow = (int64_t)tm * BM + r;  // row of the (stacked) product
-      const bool row_ok = grow < P.rows;
-      const int64_t orow = P.cplx ? (grow >> 1) : grow;
-      const int e_row = (row_ok && P.e != nullptr) ? P.e[orow] : 0;
-      const int64_t gcol0 = (int64_t)tn * BN + chalf * COLS_PER_THREAD;
+      const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
+      if (j.skip) continue;
+      const int s = j.s;
+      const int push_segs = j.cplx ? 32 : 64;  // int32 group sums stay below 2^31
+      const int64_t grow = (int64_t)j.tm * BM + r;  // row of the (stacked) product
+      const bool row_ok = grow < j.rows;
+      const int64_t orow = j.cplx ? (grow >> 1) : grow;
+      const int e_row = (row_ok && j.e != nullptr) ? j.e[orow] : 0;
+      const int64_t gcol0 = (int64_t)j.tn * BN + chalf * CPT;
       for (int g = 2; g <= s + 1; ++g) {
-        int G[COLS_PER_THREAD];
+        int Gr[CPT];
 #pragma unroll
-        for (int c = 0; c < COLS_PER_THREAD; ++c) G[c] = 0;
-        const int nseg = nseg_of(g, KB);
+        for (int c = 0; c < CPT; ++c) Gr[c] = 0;
+        const int nseg = nseg_of(g, j.KB);
         bool first_push = true;
         for (int seg = 0; seg < nseg; ++seg) {
-          if (!mbar_wait(&bar_accf[buf], (acc_par >> buf) & 1, abort_p, P.status)) goto epi_done;
+          if (!mbar_wait(&bar_accf[buf], (acc_par >> buf) & 1, abort_p, status)) goto epi_done;
           tc_fence_after();
           {
-            const uint32_t taddr =
-                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + chalf * COLS_PER_THREAD);
+            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BN + chalf * CPT);
 #pragma unroll
-            for (int cc = 0; cc < COLS_PER_THREAD / 32; ++cc) {
+            for (int cc = 0; cc < CPT / 32; ++cc) {
               uint32_t v[32];
               tmem_ld32(taddr + cc * 32, v);
               tmem_ld_wait();
 #pragma unroll
-              for (int i = 0; i < 32; ++i) G[cc * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
+              for (int i = 0; i < 32; ++i) Gr[cc * 32 + i] += __float2int_rn(__uint_as_float(v[i]));
             }
           }
           tc_fence_before();
@@ -249,27 +337,27 @@ __global__ void __launch_bounds__(THREADS, 1)
           const bool group_end = (seg == nseg - 1);
           if (!(group_end || ((seg + 1) % push_segs) == 0)) continue;
           const bool final_push = group_end && g == s + 1;
-          // ---- push G into R (or, for inspection, export G) ----
-          // Pushes happen once per group (per 64 chains at most): G moves to a thread-local
-          // array indexed at run time, so the FP64 work below runs in a rolled loop with few
-          // live registers while G itself stays in registers for the frequent drains above.
-          int Gs[COLS_PER_THREAD];
+          // ---- push the group sums into R (or, for inspection, export them) ----
+          // Pushes happen once per group (per 64 chains at most): the sums move to a
+          // thread-local array indexed at run time, so the FP64 work below runs in a rolled
+          // loop with few live registers while Gr stays in registers for the drains above.
+          int Gs[CPT];
 #pragma unroll
-          for (int c = 0; c < COLS_PER_THREAD; ++c) {
-            Gs[c] = G[c];
-            G[c] = 0;
+          for (int c = 0; c < CPT; ++c) {
+            Gs[c] = Gr[c];
+            Gr[c] = 0;
           }
-          if (P.Gdbg != nullptr) {
+          if (Gdbg != nullptr) {
 #pragma unroll 1
-            for (int c = 0; c < COLS_PER_THREAD; ++c) {
+            for (int c = 0; c < CPT; ++c) {
               const int64_t gc = gcol0 + c;
-              if (row_ok && gc < P.cols) P.Gdbg[((int64_t)(g - 2) * P.rows + grow) * P.cols + gc] = Gs[c];
+              if (row_ok && gc < j.cols) Gdbg[((int64_t)(g - 2) * j.rows + grow) * j.cols + gc] = Gs[c];
             }
-          } else if (!P.cplx) {
-            double* Rt = Rbase + (size_t)(chalf * COLS_PER_THREAD) * BM + r;
+          } else if (!j.cplx) {
+            double* Rt = Rbase + (size_t)(chalf * CPT) * BM + r;
             if (!final_push) {
 #pragma unroll 4
-              for (int c = 0; c < COLS_PER_THREAD; ++c) {
+              for (int c = 0; c < CPT; ++c) {
                 const double gv = (double)Gs[c];
                 double* Rp = Rt + (size_t)c * BM;
                 *Rp = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
@@ -277,23 +365,23 @@ __global__ void __launch_bounds__(THREADS, 1)
             } else {
               const int ebase = e_row - 7 * (s + 1);
 #pragma unroll 4
-              for (int c = 0; c < COLS_PER_THREAD; ++c) {
+              for (int c = 0; c < CPT; ++c) {
                 const double gv = (double)Gs[c];
                 const double* Rp = Rt + (size_t)c * BM;
                 const double Rv = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
                 const int64_t col = gcol0 + c;
-                if (row_ok && col < P.cols) {
-                  const double tv = scale_pow2(Rv, ebase + __ldg(P.f + col));
-                  double* cp = P.C + orow + col * P.ldc;
-                  *cp = P.beta_zero ? P.alpha[0] * tv : fma(P.alpha[0], tv, P.beta[0] * *cp);
+                if (row_ok && col < j.cols) {
+                  const double tv = scale_pow2(Rv, ebase + __ldg(j.f + col));
+                  double* cp = j.C + orow + col * j.ldc;
+                  *cp = j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp);
                 }
               }
             }
           } else {
-            double* Rt = Rbase + (size_t)(chalf * COLS_PER_THREAD / 2) * BM + r;
+            double* Rt = Rbase + (size_t)(chalf * CPT / 2) * BM + r;
             const int ebase = e_row - 7 * (s + 1);
 #pragma unroll 2
-            for (int c = 0; c < COLS_PER_THREAD / 2; ++c) {
+            for (int c = 0; c < CPT / 2; ++c) {
               // even lane (Re row) holds (rr, ri), odd lane (Im row) holds (ir, ii) at columns 2c, 2c+1
               const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * c + 1], 1);
               const int comb = odd ? (Gs[2 * c] + other) : (Gs[2 * c] - other);
@@ -303,19 +391,19 @@ __global__ void __launch_bounds__(THREADS, 1)
               if (!final_push) {
                 *Rp = Rv;
               } else {
-                const int64_t j = (gcol0 >> 1) + c;
-                const bool ok = row_ok && j < P.n;
-                const double part = ok ? scale_pow2(Rv, ebase + __ldg(P.f + j)) : 0.0;
+                const int64_t jc = (gcol0 >> 1) + c;
+                const bool ok = row_ok && jc < j.n;
+                const double part = ok ? scale_pow2(Rv, ebase + __ldg(j.f + jc)) : 0.0;
                 const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
                 const double tr = odd ? partner : part, ti = odd ? part : partner;
                 if (ok) {
-                  double* cp = P.C + 2 * (orow + j * P.ldc);
-                  double re = fma(P.alpha[0], tr, -(P.alpha[1] * ti));
-                  double im = fma(P.alpha[0], ti, P.alpha[1] * tr);
-                  if (!P.beta_zero) {
+                  double* cp = j.C + 2 * (orow + jc * j.ldc);
+                  double re = fma(j.a0, tr, -(j.a1 * ti));
+                  double im = fma(j.a0, ti, j.a1 * tr);
+                  if (!j.beta_zero) {
                     const double cr = cp[0], ci = cp[1];
-                    re += fma(P.beta[0], cr, -(P.beta[1] * ci));
-                    im += fma(P.beta[0], ci, P.beta[1] * cr);
+                    re += fma(j.b0, cr, -(j.b1 * ci));
+                    im += fma(j.b0, ci, j.b1 * cr);
                   }
                   cp[odd ? 1 : 0] = odd ? im : re;
                 }
@@ -333,8 +421,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc(tmem, K::TMEM_COLS);
   }
+}
+
+template <int BN_>
+__global__ void __launch_bounds__(THREADS, 1)
+    slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const GemmArgs P) {
+  if (P.nonfinite != nullptr && *P.nonfinite) return;  // the native FP64 kernel handles this call
+  gemm_body<BN_, false>(&tmA, &tmB, &P, nullptr);
+}
+
+template <int BN_>
+__global__ void __launch_bounds__(THREADS, 1) slice_gemm_grouped_kernel(const GroupArgs G) {
+  gemm_body<BN_, true>(nullptr, nullptr, nullptr, &G);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -354,11 +455,20 @@ EncodeTiledFn get_encode_fn() {
   return fn;
 }
 
+template <typename Kern>
+cudaError_t set_smem_once(Kern k, size_t bytes, bool& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 }  // namespace
 
 int slice_gemm_tile_m() { return BM; }
-int slice_gemm_tile_n() { return BN; }
-size_t slice_gemm_smem_bytes() { return SMEM_BYTES; }
+int slice_gemm_tile_n() { return 256; }
+int slice_gemm_tile_n_of(int variant) { return variant == 1 ? 128 : 256; }
+size_t slice_gemm_smem_bytes() { return Cfg<256>::SMEM; }
 
 cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
                             int box_rows) {
@@ -374,15 +484,42 @@ cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t prepare_kernels() {
+  static bool d0 = false, d1 = false, d2 = false, d3 = false;
+  cudaError_t e;
+  if ((e = set_smem_once(slice_gemm_kernel<256>, Cfg<256>::SMEM, d0)) != cudaSuccess) return e;
+  if ((e = set_smem_once(slice_gemm_kernel<128>, Cfg<128>::SMEM, d1)) != cudaSuccess) return e;
+  if ((e = set_smem_once(slice_gemm_grouped_kernel<256>, Cfg<256>::SMEM, d2)) != cudaSuccess) return e;
+  return set_smem_once(slice_gemm_grouped_kernel<128>, Cfg<128>::SMEM, d3);
+}
+
 cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& a, cudaStream_t st) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(slice_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
   if (a.grid <= 0) return cudaSuccess;
-  slice_gemm_kernel<<<a.grid, THREADS, SMEM_BYTES, st>>>(tmA, tmB, a);
+  cudaError_t e;
+  if (a.variant == 1) {
+    static bool done = false;
+    if ((e = set_smem_once(slice_gemm_kernel<128>, Cfg<128>::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_kernel<128><<<a.grid, THREADS, Cfg<128>::SMEM, st>>>(tmA, tmB, a);
+  } else {
+    static bool done = false;
+    if ((e = set_smem_once(slice_gemm_kernel<256>, Cfg<256>::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_kernel<256><<<a.grid, THREADS, Cfg<256>::SMEM, st>>>(tmA, tmB, a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st) {
+  if (grid <= 0 || g.ntiles <= 0) return cudaSuccess;
+  cudaError_t e;
+  if (variant == 1) {
+    static bool done = false;
+    if ((e = set_smem_once(slice_gemm_grouped_kernel<128>, Cfg<128>::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_grouped_kernel<128><<<grid, THREADS, Cfg<128>::SMEM, st>>>(g);
+  } else {
+    static bool done = false;
+    if ((e = set_smem_once(slice_gemm_grouped_kernel<256>, Cfg<256>::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_grouped_kernel<256><<<grid, THREADS, Cfg<256>::SMEM, st>>>(g);
+  }
   return cudaGetLastError();
 }
 

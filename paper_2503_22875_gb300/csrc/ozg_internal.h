@@ -50,7 +50,36 @@ struct GemmArgs {
   int* status = nullptr;        // device status word (0 ok, 3 timeout)
   const int* nonfinite = nullptr;  // if non-null and set, the kernel exits (native path takes over)
   int grid = 0;                 // CTAs to launch (<= tiles); Rws must hold grid tiles
+  int variant = 0;              // tile width: 0 -> BN = 256, 1 -> BN = 128
 };
+
+// Grouped (batched) GEMM: one persistent launch over the tiles of many independent problems.
+struct GroupCall {
+  CUtensorMap tmA, tmB;         // digit planes of this call (64-byte aligned inside the struct)
+  int64_t rows = 0, cols = 0, m = 0, n = 0, k = 0;
+  int s = 0, cplx = 0, beta_zero = 1, pad = 0;
+  const int32_t* e = nullptr;
+  const int32_t* f = nullptr;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  double alpha[2] = {1, 0}, beta[2] = {0, 0};
+  const int* nonfinite = nullptr;  // this call's Inf/NaN flag (its tiles are skipped when set)
+};
+struct GroupTile {
+  int call;  // < 0: empty slot (load-balancing padding)
+  int tm, tn, pad;
+};
+struct GroupArgs {
+  const GroupTile* tiles = nullptr;  // CTA b processes tiles b, b + grid, b + 2 grid, ...
+  int ntiles = 0;
+  const GroupCall* calls = nullptr;
+  int* status = nullptr;
+  double* Rws = nullptr;
+};
+cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st);
+// set the kernels' dynamic shared-memory limits (once per process, before any stream capture)
+cudaError_t prepare_kernels();
+int slice_gemm_tile_n_of(int variant);
 // Tensor maps over the digit planes: dims {k, rows, s}, box {64, 128 | 256, 1}, fp16, SW128.
 cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
                             int box_rows);
@@ -97,6 +126,19 @@ struct CheckArgs {
 };
 cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st);
 cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st);
+// batched: ncalls x nsamp samples; CheckArgs::err_out of call c must point at errs_dev[c]
+cudaError_t launch_check_batched_pre(const CheckArgs* calls_dev, int ncalls, int nsamp, cudaStream_t st);
+cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, int nsamp, double* errs_dev,
+                                      cudaStream_t st);
+
+// ---------------------------------------------------------------------------------- batched
+// prefix arrays: njobs + 1 entries, prefix[0] = 0, prefix[njobs] = units
+cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int64_t* rowmax_prefix_dev, int64_t rowmax_units,
+                                 const int64_t* digit_prefix_dev, int64_t digit_units, int njobs, cudaStream_t st);
+// native FP64 for the real calls whose *flags_dev[c] != 0 (list, prefix, total: device scratch
+// of ncalls, ncalls + 1 and 2 entries)
+cudaError_t launch_native_batched(const NativeArgs* calls_dev, int ncalls, const int* const* flags_dev, int* list_dev,
+                                  int64_t* prefix_dev, int64_t* total_dev, int grid, cudaStream_t st);
 
 // C = beta * C (beta == 0: zero fill), m x n, complex if cplx
 cudaError_t launch_scale_c(double* C, int64_t m, int64_t n, int64_t ldc, const double* beta, int cplx,

@@ -29,6 +29,15 @@ class OzgError(RuntimeError):
         super().__init__(msg)
 
 
+class GemmDesc(ctypes.Structure):
+    """ozg_gemm_desc of include/ozg.h."""
+    _fields_ = [("transa", ctypes.c_char), ("transb", ctypes.c_char), ("reserved", ctypes.c_char * 6),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
 class Report(ctypes.Structure):
     _fields_ = [("slices_used", ctypes.c_int), ("nonfinite", ctypes.c_int), ("status", ctypes.c_int),
                 ("samples", ctypes.c_int), ("est_err", ctypes.c_double)]
@@ -65,6 +74,10 @@ def load():
     L.ozg_set_check_samples.argtypes = [vp, i32]
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
+    L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_set_graphs.argtypes = [vp, i32]
+    L.ozg_set_fallback_slices.argtypes = [vp, i32]
+    L.ozg_set_autotune.argtypes = [vp, i32, ctypes.c_char_p]
     L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
     _lib = L
     return L
@@ -130,7 +143,7 @@ class Context:
     def sync(self):
         _check(load().ozg_sync(self._h), "ozg_sync")
 
-    PHASES = ("split", "gemm", "native", "check", "select")
+    PHASES = ("split", "gemm", "native", "check", "select", "grouped")
 
     def set_check_samples(self, samples: int):
         _check(load().ozg_set_check_samples(self._h, int(samples)), "ozg_set_check_samples")
@@ -160,6 +173,32 @@ class Context:
                               int(slices), ctypes.byref(rep) if rep else None)
         _check(rc, "ozg_zgemm")
         return rep
+
+    def dgemm_grouped(self, calls, slices=None, report=False):
+        """calls: sequence of (transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc) with
+        device tensors or raw pointers; slices: per-call slice counts (0: fallback).  Returns the
+        list of Report when report=True."""
+        n = len(calls)
+        arr = (GemmDesc * n)()
+        for i, c in enumerate(calls):
+            ta, tb, m, nn, k, al, A, lda, B, ldb, be, C, ldc = c
+            arr[i] = GemmDesc(ta.encode(), tb.encode(), b"", m, nn, k, float(al), float(be), _p(A), lda, _p(B), ldb,
+                              _p(C), ldc)
+        sl = (ctypes.c_int * n)(*([0] * n if slices is None else [int(x) for x in slices]))
+        reps = (Report * n)() if report else None
+        rc = load().ozg_dgemm_grouped(self._h, n, arr, sl, reps)
+        _check(rc, "ozg_dgemm_grouped")
+        return list(reps) if report else None
+
+    def set_graphs(self, enable: bool):
+        _check(load().ozg_set_graphs(self._h, int(bool(enable))), "ozg_set_graphs")
+
+    def set_fallback_slices(self, s: int):
+        _check(load().ozg_set_fallback_slices(self._h, int(s)), "ozg_set_fallback_slices")
+
+    def set_autotune(self, enable: bool, cache_path: str | None = None):
+        _check(load().ozg_set_autotune(self._h, int(bool(enable)), cache_path.encode() if cache_path else None),
+               "ozg_set_autotune")
 
     def native_dgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc):
         _check(load().ozg_native_dgemm(self._h, _c(transa), _c(transb), m, n, k, float(alpha), _p(A), lda, _p(B),

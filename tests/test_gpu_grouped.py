@@ -1,0 +1,144 @@
+"""Grouped emulated DGEMM (one persistent launch over many uneven GEMMs, CUDA-graph replay,
+tile-width autotuner) against the oracle, call by call."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_22875_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def ozg():
+    from paper_2503_22875_gb300 import build, ozg
+    build.build()
+    ozg.load()
+    return ozg
+
+
+def make_batch(ozg, count, seed, max_dim=600, beta_zero=False):
+    g = workloads.rng(seed)
+    batch = []
+    for i in range(count):
+        m, n, k = (int(x) for x in np.exp(g.uniform(0, np.log(max_dim), 3)).round())
+        ta, tb = g.choice(["N", "T"]), g.choice(["N", "T"])
+        s = int(g.integers(3, 10))
+        alpha = float(g.choice([1.0, -0.5, 2.0]))
+        beta = 0.0 if beta_zero else float(g.choice([0.0, 1.0, 0.25]))
+        A = workloads.wide_exponent((m, k) if ta == "N" else (k, m), float(g.uniform(0, 3)), g)
+        B = workloads.wide_exponent((k, n) if tb == "N" else (n, k), float(g.uniform(0, 3)), g)
+        C0 = np.asfortranarray(g.uniform(-1, 1, (m, n)))
+        batch.append(dict(ta=ta, tb=tb, m=m, n=n, k=k, s=s, alpha=alpha, beta=beta, A=A, B=B, C0=C0,
+                          dA=ozg.to_device(A), dB=ozg.to_device(B), dC=ozg.to_device(C0)))
+    return batch
+
+
+def calls_of(batch):
+    return [(b["ta"], b["tb"], b["m"], b["n"], b["k"], b["alpha"], b["dA"], b["A"].shape[0], b["dB"],
+             b["B"].shape[0], b["beta"], b["dC"], b["m"]) for b in batch]
+
+
+def check_batch(ozg, batch):
+    for b in batch:
+        C = ozg.from_device(b["dC"], b["m"], b["n"])
+        E = oracle.dgemm_emu(b["A"], b["B"], b["s"], b["ta"], b["tb"], b["alpha"], b["beta"], b["C0"])
+        AB = oracle.abs_product(b["A"], b["B"], b["ta"], b["tb"])
+        tol = 4 * (b["s"] + 2) * U * abs(b["alpha"]) * AB + 2 * U * np.abs(E) + 2 * U * abs(b["beta"]) * np.abs(b["C0"])
+        assert (np.abs(C - E) <= tol).all(), (b["m"], b["n"], b["k"], b["s"])
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_grouped_matches_oracle_and_replays(ozg, graphs):
+    st = torch.cuda.Stream()
+    ctx = ozg.Context(stream=st)
+    ctx.set_graphs(graphs)
+    ctx.set_check_samples(16)
+    batch = make_batch(ozg, 40, seed=300)
+    with torch.cuda.stream(st):
+        reps = ctx.dgemm_grouped(calls_of(batch), [b["s"] for b in batch], report=True)
+    assert all(r.status == 0 and r.slices_used == b["s"] and r.nonfinite == 0 for r, b in zip(reps, batch))
+    assert all(0 <= r.est_err < 1e-3 for r in reps)
+    check_batch(ozg, batch)
+    # replay (graph) with new contents in the same buffers
+    g = workloads.rng(301)
+    for b in batch:
+        b["A"] = np.asfortranarray(b["A"] * g.uniform(0.5, 2.0))
+        b["dA"].copy_(ozg.to_device(b["A"]))
+        b["C0"] = np.asfortranarray(g.uniform(-1, 1, (b["m"], b["n"])))
+        b["dC"].copy_(ozg.to_device(b["C0"]))
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        ctx.dgemm_grouped(calls_of(batch), [b["s"] for b in batch])
+    ctx.sync()
+    check_batch(ozg, batch)
+    ctx.close()
+
+
+def test_grouped_autotune_bit_identical_and_nonfinite(ozg, tmp_path):
+    st = torch.cuda.Stream()
+    batch = make_batch(ozg, 24, seed=310, beta_zero=True)
+    batch[5]["A"][0, 0] = np.nan
+    batch[5]["dA"].copy_(ozg.to_device(batch[5]["A"]))
+    outs = []
+    for tune in (False, True):
+        ctx = ozg.Context(stream=st)
+        ctx.set_autotune(tune, str(tmp_path / "tune.txt"))
+        for b in batch:
+            b["dC"].zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            reps = ctx.dgemm_grouped(calls_of(batch), [b["s"] for b in batch], report=True)
+        assert reps[5].nonfinite == 1 and reps[5].slices_used == -1
+        outs.append([b["dC"].clone() for b in batch])
+        ctx.close()
+    for x, y in zip(*outs):
+        assert torch.equal(torch.nan_to_num(x, nan=7.0), torch.nan_to_num(y, nan=7.0))
+    b = batch[5]
+    C = ozg.from_device(b["dC"], b["m"], b["n"])
+    ref = oracle.dgemm_naive(b["A"], b["B"], b["ta"], b["tb"], b["alpha"])
+    assert np.array_equal(np.isnan(C), np.isnan(ref))
+    others = [x for i, x in enumerate(batch) if i != 5]
+    check_batch(ozg, others)
+
+
+def test_grouped_edge_calls_and_invalid(ozg):
+    ctx = ozg.Context()
+    A, B = workloads.uniform_pair(20, 10, 30, seed=320)
+    dA, dB = ozg.to_device(A), ozg.to_device(B)
+    C0 = np.asfortranarray(workloads.rng(321).uniform(-1, 1, (20, 10)))
+    dC1, dC2, dC3 = ozg.to_device(C0), ozg.to_device(C0), ozg.to_device(C0)
+    calls = [("N", "N", 20, 10, 30, 1.0, dA, 20, dB, 30, 0.0, dC1, 20),
+             ("N", "N", 20, 10, 0, 1.0, dA, 20, dB, 30, 2.0, dC2, 20),    # k == 0: C = beta C
+             ("N", "N", 20, 10, 30, 0.0, dA, 20, dB, 30, 0.5, dC3, 20)]   # alpha == 0
+    ctx.dgemm_grouped(calls, [7, 7, 7])
+    ctx.sync()
+    E = oracle.dgemm_emu(A, B, 7)
+    assert (np.abs(ozg.from_device(dC1, 20, 10) - E) <= 4 * 9 * U * (np.abs(A) @ np.abs(B)) + 2 * U * np.abs(E)).all()
+    assert np.array_equal(ozg.from_device(dC2, 20, 10), 2.0 * C0)
+    assert np.array_equal(ozg.from_device(dC3, 20, 10), 0.5 * C0)
+    bad = [("N", "N", 20, 10, 30, 1.0, dA, 19, dB, 30, 0.0, dC1, 20)]
+    with pytest.raises(ozg.OzgError):
+        ctx.dgemm_grouped(bad, [7])
+    ctx.close()
+
+
+def test_single_call_autotune_cache_and_bits(ozg, tmp_path):
+    m, n, k, s = 300, 200, 500, 6
+    A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=330)
+    dA, dB = ozg.to_device(A), ozg.to_device(B)
+    res = []
+    path = tmp_path / "single.txt"
+    for tune in (False, True, True):
+        ctx = ozg.Context()
+        ctx.set_autotune(tune, str(path))
+        dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+        ctx.dgemm("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dC, m, s)
+        ctx.sync()
+        res.append(dC.clone())
+        ctx.close()
+    assert torch.equal(res[0], res[1]) and torch.equal(res[1], res[2])
+    lines = path.read_text().split()
+    assert len(lines) == 2 and lines[1] in ("0", "1")  # one bucket tuned once, then read back
