@@ -65,6 +65,13 @@ def _load():
             lib.orc_zgemm_emu.argtypes = [c_char, c_char, c_i64, c_i64, c_i64, vp, vp, c_i64, vp, c_i64,
                                           vp, vp, c_i64, c_int]
             lib.orc_emu_bound.argtypes = [c_char, c_char, c_i64, c_i64, c_i64, vp, c_i64, vp, c_i64, c_int, vp]
+            lib.orc_mlp_loss_grad.argtypes = [vp, vp, vp, c_int, vp]
+            lib.orc_mlp_loss_grad.restype = c_dbl
+            lib.orc_mlp_select.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_float, c_int, c_int, vp, c_int, vp]
+            lib.orc_mlp_select.restype = c_int
+            lib.orc_features.argtypes = [c_char, c_char, c_i64, c_i64, c_i64, vp, c_i64, vp, c_i64, c_dbl, vp]
+            lib.orc_bf16_round.argtypes = [ctypes.c_float]
+            lib.orc_bf16_round.restype = ctypes.c_float
             lib.orc_set_threads.argtypes = [c_int]
             lib.orc_get_threads.restype = c_int
             _lib = lib
@@ -240,3 +247,46 @@ def rel_err_vs_dd(C, A, B, transa="N", transb="N", alpha=1.0, beta=0.0, C0=None)
     with np.errstate(invalid="ignore", divide="ignore"):
         r = np.where(scale > 0, diff / np.where(scale > 0, scale, 1.0), np.where(diff > 0, np.inf, 0.0))
     return float(r.max()) if r.size else 0.0
+
+
+# ----------------------------------------------------------------------------- selector
+SEL_PARAMS = 6475
+
+
+def mlp_loss_grad(theta, X, y):
+    """O-mlp: mean cross-entropy and its FP64 gradient (BF16-rounded weights in the forward pass,
+    straight-through gradient).  theta: float32[6475]; X: float32[B, 24]; y: int32[B]."""
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    g = np.zeros(SEL_PARAMS)
+    loss = _load().orc_mlp_loss_grad(_ptr(theta), _ptr(X), _ptr(y), int(len(y)), _ptr(g))
+    return loss, g
+
+
+def bf16_round(x: float) -> float:
+    return float(_load().orc_bf16_round(float(x)))
+
+
+def mlp_select(model: dict, feat, s_cap: int):
+    """FP32 emulation of the GPU inference and decision.  model: mean, inv_std (float32[24]),
+    W1, W2, W3 (uint16 BF16 bits), b1, b2, b3 (float32), thr, s_lo, fallback."""
+    f = np.ascontiguousarray(feat, dtype=np.float32)
+    arrs = [np.ascontiguousarray(model[k], dtype=dt) for k, dt in
+            (("mean", np.float32), ("inv_std", np.float32), ("W1", np.uint16), ("b1", np.float32),
+             ("W2", np.uint16), ("b2", np.float32), ("W3", np.uint16), ("b3", np.float32))]
+    probs = np.zeros(11, dtype=np.float32)
+    s = _load().orc_mlp_select(*[_ptr(a) for a in arrs], float(model["thr"]), int(model["s_lo"]),
+                               int(model["fallback"]), _ptr(f), int(s_cap), _ptr(probs))
+    return s, probs
+
+
+def features(A, B, target, transa="N", transb="N"):
+    """The selector's 24 features of op(A) op(B) from their definition (float32[24])."""
+    A, B = _fortran(A, np.float64), _fortran(B, np.float64)
+    m, k = _op_shape(transa, A)
+    _, n = _op_shape(transb, B)
+    out = np.zeros(24, dtype=np.float32)
+    _load().orc_features(_b(transa), _b(transb), m, n, k, _ptr(A), max(A.shape[0], 1), _ptr(B), max(B.shape[0], 1),
+                         float(target), _ptr(out))
+    return out

@@ -487,3 +487,188 @@ ORC_EXPORT void orc_emu_bound(char ta, char tb, int64_t m, int64_t n, int64_t k,
     }
   free(e); free(f);
 }
+
+/* ===================================================================== selector (adaptive s)
+ * The adaptive split number the paper proposes (Sec. 4), as restated for this project: an MLP
+ * 24 -> 64 -> 64 -> 11 over per-GEMM features predicts the minimal sufficient slice count.
+ * theta = [W1 (64x24), b1 (64), W2 (64x64), b2 (64), W3 (11x64), b3 (11)], row-major [out][in].
+ */
+#define SEL_IN 24
+#define SEL_H 64
+#define SEL_OUT 11
+#define O_W1 0
+#define O_B1 (O_W1 + SEL_H * SEL_IN)
+#define O_W2 (O_B1 + SEL_H)
+#define O_B2 (O_W2 + SEL_H * SEL_H)
+#define O_W3 (O_B2 + SEL_H)
+#define O_B3 (O_W3 + SEL_OUT * SEL_H)
+#define SEL_PARAMS (O_B3 + SEL_OUT)
+
+/* BF16 rounding of a float: keep the top 16 bits of the IEEE single, rounding the dropped 16
+ * bits to nearest with ties to even (finite inputs). */
+static float bf16_round(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  u &= 0xFFFF0000u;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+ORC_EXPORT float orc_bf16_round(float x) { return bf16_round(x); }
+
+/* Mean cross-entropy of the MLP on a batch and its gradient, in FP64, with the weights rounded
+ * to BF16 in the forward pass and the gradient passed straight through that rounding.
+ * X: [B][24] normalised features (float); y: [B] classes 0..10; grad: [SEL_PARAMS] or NULL. */
+ORC_EXPORT double orc_mlp_loss_grad(const float* theta, const float* X, const int* y, int B, double* grad) {
+  double W1[SEL_H * SEL_IN], W2[SEL_H * SEL_H], W3[SEL_OUT * SEL_H];
+  for (int i = 0; i < SEL_H * SEL_IN; ++i) W1[i] = bf16_round(theta[O_W1 + i]);
+  for (int i = 0; i < SEL_H * SEL_H; ++i) W2[i] = bf16_round(theta[O_W2 + i]);
+  for (int i = 0; i < SEL_OUT * SEL_H; ++i) W3[i] = bf16_round(theta[O_W3 + i]);
+  if (grad) memset(grad, 0, sizeof(double) * SEL_PARAMS);
+  double loss = 0.0;
+  for (int b = 0; b < B; ++b) {
+    const float* x = X + (size_t)b * SEL_IN;
+    double h1[SEL_H], h2[SEL_H], z[SEL_OUT], p[SEL_OUT];
+    for (int o = 0; o < SEL_H; ++o) {
+      double a = theta[O_B1 + o];
+      for (int j = 0; j < SEL_IN; ++j) a += W1[o * SEL_IN + j] * (double)x[j];
+      h1[o] = a > 0 ? a : 0;
+    }
+    for (int o = 0; o < SEL_H; ++o) {
+      double a = theta[O_B2 + o];
+      for (int j = 0; j < SEL_H; ++j) a += W2[o * SEL_H + j] * h1[j];
+      h2[o] = a > 0 ? a : 0;
+    }
+    double zm = -INFINITY;
+    for (int o = 0; o < SEL_OUT; ++o) {
+      double a = theta[O_B3 + o];
+      for (int j = 0; j < SEL_H; ++j) a += W3[o * SEL_H + j] * h2[j];
+      z[o] = a;
+      if (a > zm) zm = a;
+    }
+    double se = 0;
+    for (int o = 0; o < SEL_OUT; ++o) se += exp(z[o] - zm);
+    for (int o = 0; o < SEL_OUT; ++o) p[o] = exp(z[o] - zm) / se;
+    loss += (log(se) + zm - z[y[b]]) / B;
+    if (!grad) continue;
+    double dz[SEL_OUT], dh2[SEL_H], dh1[SEL_H];
+    for (int o = 0; o < SEL_OUT; ++o) dz[o] = (p[o] - (o == y[b] ? 1.0 : 0.0)) / B;
+    for (int o = 0; o < SEL_OUT; ++o) {
+      grad[O_B3 + o] += dz[o];
+      for (int j = 0; j < SEL_H; ++j) grad[O_W3 + o * SEL_H + j] += dz[o] * h2[j];
+    }
+    for (int j = 0; j < SEL_H; ++j) {
+      double a = 0;
+      for (int o = 0; o < SEL_OUT; ++o) a += W3[o * SEL_H + j] * dz[o];
+      dh2[j] = h2[j] > 0 ? a : 0;
+    }
+    for (int o = 0; o < SEL_H; ++o) {
+      grad[O_B2 + o] += dh2[o];
+      for (int j = 0; j < SEL_H; ++j) grad[O_W2 + o * SEL_H + j] += dh2[o] * h1[j];
+    }
+    for (int j = 0; j < SEL_H; ++j) {
+      double a = 0;
+      for (int o = 0; o < SEL_H; ++o) a += W2[o * SEL_H + j] * dh2[o];
+      dh1[j] = h1[j] > 0 ? a : 0;
+    }
+    for (int o = 0; o < SEL_H; ++o) {
+      grad[O_B1 + o] += dh1[o];
+      for (int j = 0; j < SEL_IN; ++j) grad[O_W1 + o * SEL_IN + j] += dh1[o] * x[j];
+    }
+  }
+  return loss;
+}
+
+/* Inference as the GPU performs it, emulated in FP32 on the CPU: weights are BF16 bit patterns
+ * (row-major [out][in]), biases FP32; each dot product is a chain of fmaf in ascending input
+ * order starting from the bias; softmax with expf; the decision is the smallest class whose
+ * cumulative probability reaches thr (else `fallback`), as s = s_lo + class, capped to s_cap.
+ * feat: raw features [24]; probs_out: [11] or NULL.  Returns s. */
+static float bf16_to_f(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+ORC_EXPORT int orc_mlp_select(const float* mean, const float* inv_std, const uint16_t* W1, const float* b1,
+                              const uint16_t* W2, const float* b2, const uint16_t* W3, const float* b3, float thr,
+                              int s_lo, int fallback, const float* feat, int s_cap, float* probs_out) {
+  float x[SEL_IN], h1[SEL_H], h2[SEL_H], z[SEL_OUT];
+  for (int j = 0; j < SEL_IN; ++j) x[j] = (feat[j] - mean[j]) * inv_std[j];
+  for (int o = 0; o < SEL_H; ++o) {
+    float a = b1[o];
+    for (int j = 0; j < SEL_IN; ++j) a = fmaf(bf16_to_f(W1[o * SEL_IN + j]), x[j], a);
+    h1[o] = a > 0.f ? a : 0.f;
+  }
+  for (int o = 0; o < SEL_H; ++o) {
+    float a = b2[o];
+    for (int j = 0; j < SEL_H; ++j) a = fmaf(bf16_to_f(W2[o * SEL_H + j]), h1[j], a);
+    h2[o] = a > 0.f ? a : 0.f;
+  }
+  float zm = -INFINITY;
+  for (int o = 0; o < SEL_OUT; ++o) {
+    float a = b3[o];
+    for (int j = 0; j < SEL_H; ++j) a = fmaf(bf16_to_f(W3[o * SEL_H + j]), h2[j], a);
+    z[o] = a;
+    if (a > zm) zm = a;
+  }
+  float ez[SEL_OUT], sum = 0.f;
+  for (int o = 0; o < SEL_OUT; ++o) {
+    ez[o] = expf(z[o] - zm);
+    sum += ez[o];
+  }
+  float cum = 0.f;
+  int chosen = -1;
+  for (int o = 0; o < SEL_OUT; ++o) {
+    const float p = ez[o] / sum;
+    if (probs_out) probs_out[o] = p;
+    cum += p;
+    if (chosen < 0 && cum >= thr) chosen = o;
+  }
+  int s = chosen < 0 ? fallback : s_lo + chosen;
+  if (s < 1) s = 1;
+  if (s > s_cap) s = s_cap;
+  return s;
+}
+
+/* The selector's features of one GEMM from their definition: log2 m, log2 n, log2 k; for the
+ * rows of op(A) the fractions of entries whose exponent gap e_i - E(a) (E: frexp exponent) falls
+ * in [0,4), [4,8), ..., [32,36), and the fraction that is >= 36 or zero; the same for the
+ * columns of op(B); log10(target).  out: [24] floats. */
+ORC_EXPORT void orc_features(char ta, char tb, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                             const double* B, int64_t ldb, double target, float* out) {
+  double hist[2][10];
+  memset(hist, 0, sizeof(hist));
+  for (int side = 0; side < 2; ++side) {
+    const int64_t rows = side ? n : m;
+    for (int64_t i = 0; i < rows; ++i) {
+      double amax = 0;
+      for (int64_t l = 0; l < k; ++l) {
+        double v = side ? op_r(tb, B, ldb, l, i) : op_r(ta, A, lda, i, l);
+        if (fabs(v) > amax) amax = fabs(v);
+      }
+      int e = 0;
+      if (amax != 0) frexp(amax, &e);
+      for (int64_t l = 0; l < k; ++l) {
+        double v = side ? op_r(tb, B, ldb, l, i) : op_r(ta, A, lda, i, l);
+        int bin = 9;
+        if (v != 0) {
+          int ev;
+          frexp(v, &ev);
+          int gap = e - ev;
+          bin = gap < 36 ? (gap < 0 ? 0 : gap / 4) : 9;
+        }
+        hist[side][bin] += 1;
+      }
+    }
+  }
+  out[0] = log2f((float)m);
+  out[1] = log2f((float)n);
+  out[2] = log2f((float)k);
+  for (int b = 0; b < 10; ++b) {
+    out[3 + b] = (float)(hist[0][b] / ((double)m * (double)k));
+    out[13 + b] = (float)(hist[1][b] / ((double)n * (double)k));
+  }
+  out[23] = (float)log10(target);
+}

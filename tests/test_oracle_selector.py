@@ -1,0 +1,103 @@
+"""Pins for the oracle's selector functions (no GPU): BF16 rounding, the MLP loss and its
+gradient, the FP32 inference emulation and decision rule, and the feature definition."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+P = oracle.SEL_PARAMS
+O_W1, O_B1 = 0, 64 * 24
+O_W2, O_B2 = O_B1 + 64, O_B1 + 64 + 64 * 64
+O_W3, O_B3 = O_B2 + 64, O_B2 + 64 + 11 * 64
+
+
+def test_bf16_rounding_closed_forms():
+    assert oracle.bf16_round(1.0) == 1.0
+    assert oracle.bf16_round(1.0 + 2 ** -8) == 1.0                 # tie -> even (mantissa ...0)
+    assert oracle.bf16_round(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6   # tie -> even (rounds up)
+    assert oracle.bf16_round(1.0 + 2 ** -8 + 2 ** -20) == 1.0 + 2 ** -7
+    assert oracle.bf16_round(-3.0) == -3.0
+    assert oracle.bf16_round(2.0 ** -130) == 2.0 ** -130           # subnormal float, 8 leading bits
+
+
+def test_mlp_zero_network_closed_form():
+    theta = np.zeros(P, np.float32)
+    X = np.random.default_rng(0).normal(size=(5, 24)).astype(np.float32)
+    y = np.array([0, 3, 10, 3, 7], np.int32)
+    loss, g = oracle.mlp_loss_grad(theta, X, y)
+    assert abs(loss - math.log(11)) < 1e-14
+    # d loss / d b3 = mean(p - onehot) with p uniform
+    exp_b3 = np.full(11, 1 / 11.0)
+    for c in y:
+        exp_b3[c] -= 1.0 / len(y)
+    np.testing.assert_allclose(g[O_B3:O_B3 + 11], exp_b3, atol=1e-15)
+    assert not g[:O_B3].any()  # zero weights and ReLU(0) = 0 block every other gradient
+
+
+def _params(seed, scale=0.3):
+    r = np.random.default_rng(seed)
+    th = r.normal(0, scale, P).astype(np.float32)
+    # weights exactly representable in BF16 so that +-1 BF16 ulp steps are exact perturbations
+    for lo, hi in ((O_W1, O_B1), (O_W2, O_B2), (O_W3, O_B3)):
+        th[lo:hi] = np.array([oracle.bf16_round(float(v)) for v in th[lo:hi]], np.float32)
+    return th
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_mlp_gradient_finite_differences(seed):
+    r = np.random.default_rng(100 + seed)
+    th = _params(seed)
+    X = r.normal(size=(6, 24)).astype(np.float32)
+    y = r.integers(0, 11, 6).astype(np.int32)
+    _, g = oracle.mlp_loss_grad(th, X, y)
+    # biases: smooth central differences
+    for idx in list(range(O_B1, O_B1 + 5)) + list(range(O_B2, O_B2 + 5)) + list(range(O_B3, O_B3 + 11)):
+        h = 1e-3
+        tp, tm = th.copy(), th.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        fd = (oracle.mlp_loss_grad(tp, X, y)[0] - oracle.mlp_loss_grad(tm, X, y)[0]) / (tp[idx] - tm[idx])
+        assert abs(fd - g[idx]) <= 2e-3 * max(1.0, abs(g[idx])), idx
+    # weights: +- one BF16 ulp (exact in the rounded forward pass); checks every layer's indexing
+    for idx in (O_W1 + 3 * 24 + 5, O_W1 + 40 * 24 + 23, O_W2 + 7 * 64 + 50, O_W2 + 63 * 64 + 1,
+                O_W3 + 2 * 64 + 9, O_W3 + 10 * 64 + 63):
+        w = float(th[idx])
+        ulp = 2.0 ** (math.frexp(w)[1] - 8) if w != 0 else 2.0 ** -20
+        tp, tm = th.copy(), th.copy()
+        tp[idx] = w + ulp
+        tm[idx] = w - ulp
+        assert oracle.bf16_round(float(tp[idx])) == tp[idx] and oracle.bf16_round(float(tm[idx])) == tm[idx]
+        fd = (oracle.mlp_loss_grad(tp, X, y)[0] - oracle.mlp_loss_grad(tm, X, y)[0]) / (2 * ulp)
+        assert abs(fd - g[idx]) <= 0.05 * abs(g[idx]) + 1e-4, (idx, fd, g[idx])
+
+
+def test_mlp_select_closed_form_decision():
+    # zero weights: the output probabilities are softmax(b3) -> decision from cumulative sums
+    p = np.array([0.05, 0.10, 0.30, 0.40, 0.10, 0.05, 0, 0, 0, 0, 0], np.float64)
+    b3 = np.log(np.maximum(p, 1e-30)).astype(np.float32)
+    model = dict(mean=np.zeros(24, np.float32), inv_std=np.ones(24, np.float32),
+                 W1=np.zeros(64 * 24, np.uint16), b1=np.zeros(64, np.float32),
+                 W2=np.zeros(64 * 64, np.uint16), b2=np.zeros(64, np.float32),
+                 W3=np.zeros(11 * 64, np.uint16), b3=b3, thr=0.8, s_lo=2, fallback=9)
+    s, probs = oracle.mlp_select(model, np.zeros(24, np.float32), 12)
+    np.testing.assert_allclose(probs, p, atol=1e-6)
+    assert s == 2 + 3          # cumulative 0.05, 0.15, 0.45, 0.85 >= 0.8 at class 3
+    model["thr"] = 0.99
+    assert oracle.mlp_select(model, np.zeros(24, np.float32), 12)[0] == 2 + 5
+    assert oracle.mlp_select(model, np.zeros(24, np.float32), 6)[0] == 6  # capped
+
+
+def test_features_closed_forms():
+    A = np.array([[1.0, 2.0 ** -5, 2.0 ** -40, 0.0],
+                  [3.0, 3.0, 3.0, 3.0]])
+    B = np.ones((4, 3))
+    f = oracle.features(A, B, 1e-10)
+    assert f[0] == 1.0 and f[1] == math.log2(3) and f[2] == 2.0
+    # row 0: gaps 0, 5, 40, zero -> bins 0, 1, 9, 9 ; row 1: all gap 0 -> bin 0
+    np.testing.assert_array_equal(f[3:13], np.array([5, 1, 0, 0, 0, 0, 0, 0, 0, 2], np.float32) / 8)
+    np.testing.assert_array_equal(f[13:23], np.array([1, 0, 0, 0, 0, 0, 0, 0, 0, 0], np.float32))
+    assert abs(f[23] + 10) < 1e-6
+    g = oracle.features(np.asfortranarray(A.T), B, 1e-14, transa="T")
+    np.testing.assert_array_equal(f[:23], g[:23])
