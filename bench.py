@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--size", type=int, default=M)
     ap.add_argument("--slices", type=int, default=0, help="0: smallest s meeting 1e-12 on the sampled check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grouped", action="store_true", help="skip the grouped-batch comparison")
+    ap.add_argument("--grouped-count", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -186,6 +188,53 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------ grouped batch
+def grouped_section(ozg, torch, count, steps):
+    """2048 uneven GEMMs (m, n, k log-uniform in [32, 2048], phi ~ U(0, 4)) at fixed s = 7:
+    one ozg_dgemm call at a time vs one grouped, graph-replayed ozg_dgemm_grouped call."""
+    from paper_2503_22875_gb300 import workloads
+    batch = workloads.grouped_batch_device(count)
+    st = torch.cuda.Stream()
+    Cs = [torch.empty((n, m), dtype=torch.float64, device="cuda") for m, n, k, _, _, _ in batch]
+    calls = [("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m) for (m, n, k, _, A, B), C in zip(batch, Cs)]
+    flops = sum(2.0 * m * n * k for m, n, k, _, _, _ in batch)
+    s = [7] * count
+    ctx = ozg.Context(stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one_at_a_time():
+        for c in calls:
+            ctx.dgemm(*c, 7)
+
+    def grouped():
+        ctx.dgemm_grouped(calls, s)
+
+    out = {}
+    for name, fn in (("one_at_a_time_s7", one_at_a_time), ("grouped_graph_s7", grouped)):
+        with torch.cuda.stream(st):
+            fn()  # warm-up (and graph capture for the grouped call)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(steps):
+                fn()
+            e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+    ctx.set_check_samples(16)
+    with torch.cuda.stream(st):
+        reps = ctx.dgemm_grouped(calls, s, report=True)
+    errs = [r.est_err for r in reps]
+    out["calls"] = count
+    out["fp64_equiv_flops"] = flops
+    out["max_err_sampled_dd_s7"] = max(errs)
+    out["frac_calls_le_1e-12_s7"] = sum(e <= TARGET_ERR for e in errs) / count
+    out["workload"] = (f"{count} DGEMMs, m,n,k log-uniform in [32, 2048], a=(u-0.5)exp(phi g), phi~U(0,4) per call, "
+                       f"beta=0; generated on the GPU (seeded torch generator)")
+    ctx.close()
+    return out
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -299,6 +348,10 @@ def run_gpu(args):
     tn1.synchronize()
     native_tflops = flops / (tn0.elapsed_time(tn1) / 1e3) / 1e12
 
+    grouped = None
+    if not args.no_grouped:
+        grouped = grouped_section(ozg, torch, args.grouped_count, max(1, min(args.steps, 5)))
+
     peaks, peak_src = measured_peaks()
     gemm_ms, gemm_n = phases["gemm"]
     split_ms, split_n = phases["split"]
@@ -331,6 +384,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": {"value": flops * world / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n},
+        "grouped_batch": grouped,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

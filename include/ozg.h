@@ -63,6 +63,9 @@ typedef struct ozg_report {
   int samples;            /* entries checked in double-double (0: check disabled) */
   double est_err;         /* max over the samples of |C - C_dd| / (|alpha||A||B| + |beta||C_old|);
                              NaN when not checked or routed to native FP64 */
+  int selected;           /* slice count the learned selector chose (0: the count was fixed) */
+  int repaired;           /* 1: the check rejected the selected count and the call was re-run at
+                             the fallback count (slices_used then holds the fallback) */
 } ozg_report;
 
 /* Create a context on the current CUDA device.  workspace_bytes pre-reserves device
@@ -86,13 +89,51 @@ int ozg_sync(ozg_ctx* ctx);
  * to |alpha||A||B| + |beta||C_old| in ozg_report.est_err.  0 disables (the default). */
 int ozg_set_check_samples(ozg_ctx* ctx, int samples);
 
+/* ---- learned slice selector (slices = 0: automatic) ----
+ * The paper proposes adjusting the split number to the accuracy each computation needs
+ * (Sec. 4).  With a model loaded, a call with slices = 0 computes per-GEMM features on the GPU
+ * (log2 m, n, k; 10-bin histograms of the within-row / within-column exponent gaps of op(A) and
+ * op(B); log10 of the target error), evaluates a 24-64-64-11 MLP (BF16 weights, FP32
+ * accumulation) on the GPU and uses the smallest s in 2..12 whose cumulative predicted
+ * probability reaches the model's threshold -- all on the device, no host round trip.  The
+ * sampled double-double check is always on for such calls (>= 64 samples); if its estimate
+ * exceeds the target the call is recomputed at the fallback count (ozg_set_fallback_slices),
+ * again on the device.  Without a model, slices = 0 means the fallback count. */
+
+/* Load a selector model file (format in the library's selector source).  Returns 0 or
+ * OZG_ERR_INVALID (unreadable or malformed file). */
+int ozg_load_selector(ozg_ctx* ctx, const char* path);
+
+/* Target componentwise error for automatic slice counts (default 1e-12). */
+int ozg_set_target_error(ozg_ctx* ctx, double target);
+
+/* Selector features of one GEMM, computed by the same kernels as the automatic path:
+ * feat_out (device float[24]); prob_out (device float[11] or NULL) and s_out (device int or
+ * NULL) receive the loaded model's class probabilities and decision (left untouched without a
+ * model).  Synchronous. */
+int ozg_selector_features(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
+                          const double* A, int64_t lda, const double* B, int64_t ldb, float* feat_out,
+                          float* prob_out, int* s_out);
+
+/* On-GPU training of the selector's MLP (FP32 master parameters; BF16-rounded weights in the
+ * forward pass, straight-through gradients; mean cross-entropy).  Parameters are the HOST array
+ * theta[OZG_SELECTOR_PARAMS] = W1[64x24], b1[64], W2[64x64], b2[64], W3[11x64], b3[11]
+ * (row-major [out][in]).  X: DEVICE float[B][24] normalised features, y: DEVICE int[B] class
+ * indices 0..10.  Each call is synchronous. */
+#define OZG_SELECTOR_PARAMS 6475
+int ozg_selector_set_params(ozg_ctx* ctx, const float* theta);     /* also resets Adam state */
+int ozg_selector_get_params(ozg_ctx* ctx, float* theta);
+int ozg_selector_grads(ozg_ctx* ctx, const float* X, const int* y, int B, float* grad, float* loss);
+int ozg_selector_train_step(ozg_ctx* ctx, const float* X, const int* y, int B, float lr, float* loss);
+
 /* Human-readable text for a return code (static storage). */
 const char* ozg_strerror(int code);
 
 /* Emulated DGEMM, C = alpha op(A) op(B) + beta C (Sec. 2.2 / 3.1; ?gemm semantics).
  *   transa, transb: 'N' or 'T' (case-insensitive).  m, n, k >= 0.
  *   A: device, column-major, lda >= max(1, rows of A); B likewise with ldb; C: m x n, ldc >= max(1, m).
- *   slices: 1..OZG_MAX_SLICES fixed split number; OZG_NATIVE (-1) runs native FP64.
+ *   slices: 1..OZG_MAX_SLICES fixed split number; OZG_NATIVE (-1) runs native FP64; 0 lets the
+ *   learned selector choose (see below; the fallback count when no model is loaded).
  *   beta == 0: C is not read (NaNs in C are ignored).  Quick returns: m == 0 or n == 0, or
  *   ((alpha == 0 or k == 0) and beta == 1).  alpha == 0 or k == 0 gives C = beta C.
  *   Inputs holding Inf/NaN are detected on the device and the call is completed by the native

@@ -2,6 +2,7 @@
 // workspace management and the launch sequence of the emulated GEMM:
 //   split(op(A)) -> split(op(B)) -> fused slice-GEMM + epilogue -> native kernel gated on
 //   the non-finite flag (runs only if an input held Inf/NaN).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +39,15 @@ int check_gemm_args(bool cplx, char& ta, char& tb, int64_t m, int64_t n, int64_t
 int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int64_t k, const double* alpha,
              const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C, int64_t ldc,
              int s, ozg_report* rep, int64_t* Gdbg) {
+  // automatic slice count: the selector chooses s on the device; digit planes are written for
+  // its largest class (by the prefix property the GEMM uses the first s), the sampled check is
+  // always on, and a failed check re-runs the call at the fallback count
+  const bool autos = (s == 0) && c->sel_s_hi > 0 && !Gdbg;
+  if (s == 0 && !autos) s = c->fallback_slices;
+  const int s_fb = c->fallback_slices;
+  if (autos) s = std::max(c->sel_s_hi, s_fb);
+  const int nsamp = autos ? std::max(c->check_samples, 64) : c->check_samples;
+  const bool beta_zero0 = (beta[0] == 0.0 && (!cplx || beta[1] == 0.0));
   const int64_t Kp = (int64_t)align_up((size_t)k, 8);
   const int64_t prA = cplx ? 2 * m : m, prB = cplx ? 2 * n : n;
   const int BM = ozg::slice_gemm_tile_m();
@@ -52,7 +62,9 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   size_t oE = cv.take(4 * (size_t)m), oF = cv.take(4 * (size_t)n);
   size_t oMA = cv.take(8 * (size_t)m), oMB = cv.take(8 * (size_t)n);
   size_t oR = cv.take((size_t)grid * BM * 256 * 8);
-  size_t oCold = cv.take((size_t)(c->check_samples > 0 ? c->check_samples : 1) * 16);
+  size_t oCold = cv.take((size_t)(nsamp > 0 ? nsamp : 1) * 16);
+  size_t oHist = cv.take(2 * 10 * 8), oSd = cv.take(4 * sizeof(int)), oErr2 = cv.take(sizeof(double));
+  size_t oSaved = cv.take((autos && !beta_zero0) ? (size_t)m * n * (cplx ? 16 : 8) : 8);
   int rc = ensure_ws(c, cv.off);
   if (rc) return rc;
   cudaStream_t st = c->stream;
@@ -95,6 +107,18 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     delete split_scope;
     OZG_CUDA(e);
   }
+  int* s_dev = at<int>(c, oSd);  // [0] chosen s, [1] 1 unless the check forced a re-run
+  if (autos) {
+    PhaseScope ps(c, OZG_PHASE_SELECT);
+    unsigned long long* hist = at<unsigned long long>(c, oHist);
+    OZG_CUDA(cudaMemsetAsync(hist, 0, 2 * 10 * 8, st));
+    ozg::SplitArgs ha = sa, hb = sb;
+    ha.hist = hist;
+    hb.hist = hist + 10;
+    OZG_CUDA(ozg::launch_gap_hist_pair(ha, hb, st));
+    OZG_CUDA(ozg::launch_select_single(c->dsel, hist, hist + 10, m, n, k, (float)std::log10(c->target), s, s_dev,
+                                       nullptr, nullptr, st));
+  }
 
   CUtensorMap tmA, tmB[2];
   OZG_CUDA(ozg::make_digit_tmap(&tmA, sa.D, k, prA, Kp, s, BM));
@@ -124,7 +148,8 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   ga.nonfinite = Gdbg ? nullptr : nonfinite;
   ga.variant = variant;
   ga.grid = grid_of(variant);
-  if (c->autotune && !Gdbg && ga.beta_zero) {
+  ga.s_dev = autos ? s_dev : nullptr;
+  if (c->autotune && !Gdbg && ga.beta_zero && !autos) {
     const uint64_t bucket = shape_bucket(prA, prB, k, s);
     if (c->tune.find(bucket) == c->tune.end()) {
       // time both widths on this call (C is write-only here and both give the same bits)
@@ -154,7 +179,10 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     }
   }
   ozg::CheckArgs ck;
-  if (c->check_samples > 0 && !Gdbg) {
+  if (autos && !beta_zero0)
+    OZG_CUDA(cudaMemcpy2DAsync(at<double>(c, oSaved), (size_t)m * (cplx ? 16 : 8), C, (size_t)ldc * (cplx ? 16 : 8),
+                               (size_t)m * (cplx ? 16 : 8), (size_t)n, cudaMemcpyDeviceToDevice, st));
+  if (nsamp > 0 && !Gdbg) {
     ck.ta = ta;
     ck.tb = tb;
     ck.m = m;
@@ -172,7 +200,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     ck.beta[1] = ga.beta[1];
     ck.beta_zero = ga.beta_zero;
     ck.cplx = cplx;
-    ck.nsamp = c->check_samples;
+    ck.nsamp = nsamp;
     ck.seed = c->check_seed++;
     ck.cold = at<double>(c, oCold);
     ck.err_out = c->dcheck;
@@ -209,20 +237,40 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     PhaseScope ps(c, OZG_PHASE_NATIVE);
     OZG_CUDA(ozg::launch_native_gemm(na, st));
   }
-  if (c->check_samples > 0) {
+  if (nsamp > 0) {
     PhaseScope ps(c, OZG_PHASE_CHECK);
     OZG_CUDA(ozg::launch_check_post(ck, st));
   }
+  const int s_rep = std::min(s_fb, s);
+  if (autos) {  // judged by the check: re-run at the fallback count when the error is too large
+    OZG_CUDA(ozg::launch_repair_prep(c->dcheck, c->target, s_dev + 1, at<double>(c, oSaved), C, m, n, ldc,
+                                     cplx ? 2 : 1, beta_zero0 ? 0 : 1, st));
+    ozg::GemmArgs g2 = ga;
+    g2.s = s_rep;
+    g2.s_dev = nullptr;
+    g2.nonfinite = s_dev + 1;  // the kernel exits unless the repair is needed
+    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB[g2.variant], g2, st));
+    ozg::CheckArgs ck2 = ck;
+    ck2.err_out = at<double>(c, oErr2);
+    ck2.gate = s_dev + 1;
+    OZG_CUDA(ozg::launch_check_post(ck2, st));
+  }
   if (rep) {
-    int h = 0;
-    double err = 0.0;
+    int h = 0, sd[2] = {s, 1};
+    double err = 0.0, err2 = 0.0;
     OZG_CUDA(cudaMemcpyAsync(&h, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (c->check_samples > 0) OZG_CUDA(cudaMemcpyAsync(&err, c->dcheck, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (nsamp > 0) OZG_CUDA(cudaMemcpyAsync(&err, c->dcheck, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (autos) {
+      OZG_CUDA(cudaMemcpyAsync(sd, s_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(&err2, at<double>(c, oErr2), sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     OZG_CUDA(cudaStreamSynchronize(st));
     rep->nonfinite = h;
-    rep->slices_used = h ? -1 : s;
-    rep->samples = (c->check_samples > 0 && !h) ? c->check_samples : 0;
-    rep->est_err = rep->samples ? err : NAN;
+    rep->slices_used = h ? -1 : (autos ? (sd[1] ? sd[0] : s_rep) : s);
+    rep->samples = (nsamp > 0 && !h) ? nsamp : 0;
+    rep->est_err = rep->samples ? ((autos && !sd[1]) ? err2 : err) : NAN;
+    rep->selected = autos ? sd[0] : 0;
+    rep->repaired = (autos && !h && !sd[1]) ? 1 : 0;
   }
   return OZG_OK;
 }
@@ -233,7 +281,7 @@ int gemm_entry(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, in
   // BLAS order: argument errors are reported before anything else (no device work, no context use)
   int rc = check_gemm_args(cplx, ta, tb, m, n, k, lda, ldb, ldc);
   if (rc) return rc;
-  if (!native && (slices == 0 || slices < OZG_NATIVE || slices > OZG_MAX_SLICES)) return -14;
+  if (!native && (slices < OZG_NATIVE || slices > OZG_MAX_SLICES)) return -14;
   if (!c) return OZG_ERR_INVALID;
   if (rep) {
     std::memset(rep, 0, sizeof(*rep));
@@ -323,6 +371,10 @@ int ozg_destroy(ozg_ctx* c) {
   if (c->ws) cudaFree(c->ws);
   if (c->dflags) cudaFree(c->dflags);
   if (c->dcheck) cudaFree(c->dcheck);
+  if (c->dsel) cudaFree(c->dsel);
+  if (c->train) cudaFree(c->train);
+  c->plan.reset();
+  if (c->gws) cudaFree(c->gws);
   delete c;
   return OZG_OK;
 }

@@ -247,7 +247,44 @@ __global__ void __launch_bounds__(256) native_batched(const NativeArgs* calls, c
   }
 }
 
+__global__ void repair_prep_batched(const RepairJob* jobs, int njobs, double target) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= njobs) return;
+  const RepairJob J = jobs[i];
+  const double e = J.err ? *J.err : 0.0;
+  const bool bad = J.auto_mode && !(J.nonfinite && *J.nonfinite) && !(e <= target);
+  *J.skip2 = bad ? 0 : 1;
+}
+
+// unit = 256 elements of one automatic, beta != 0 call
+__global__ void save_restore_batched(const RepairJob* jobs, const int64_t* prefix, int njobs, int restore) {
+  const int64_t unit = blockIdx.x;
+  const int jb = find_job(prefix, njobs, unit);
+  const RepairJob J = jobs[jb];
+  if (restore && *J.skip2) return;
+  const int64_t e = (unit - prefix[jb]) * 256 + threadIdx.x;
+  if (e >= J.m * J.n) return;
+  const int64_t i = e % J.m, j = e / J.m;
+  if (restore)
+    J.C[i + j * J.ldc] = J.saved[e];
+  else
+    J.saved[e] = J.C[i + j * J.ldc];
+}
+
 }  // namespace
+
+cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  repair_prep_batched<<<(njobs + 127) / 128, 128, 0, st>>>(jobs_dev, njobs, target);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_save_restore_batched(const RepairJob* jobs_dev, const int64_t* prefix_dev, int64_t units,
+                                        int njobs, int restore, cudaStream_t st) {
+  if (units <= 0 || njobs <= 0) return cudaSuccess;
+  save_restore_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, prefix_dev, njobs, restore);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int64_t* rowmax_prefix_dev, int64_t rowmax_units,
                                  const int64_t* digit_prefix_dev, int64_t digit_units, int njobs, cudaStream_t st) {

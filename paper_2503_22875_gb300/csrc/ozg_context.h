@@ -53,6 +53,12 @@ struct ozg_ctx {
   std::string tune_path;
   std::unordered_map<uint64_t, int> tune;
   bool tune_loaded = false;
+  // learned slice selector
+  ozg::SelectorDev* dsel = nullptr;  // device copy of the loaded model
+  int sel_s_hi = 0;                  // largest class of the loaded model (0: no model)
+  double target = 1e-12;             // requested error for automatic slice counts
+  float* train = nullptr;            // [theta | grad | m1 | m2 | loss] for on-GPU training
+  int adam_step = 0;
 };
 
 namespace ozg {

@@ -90,7 +90,7 @@ __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const 
     j.tmA = tmA;
     j.tmB = tmB;
     j.KB = (int)((P->k + BK - 1) / BK);
-    j.s = P->s;
+    j.s = P->s_dev != nullptr ? *P->s_dev : P->s;
     j.cplx = P->cplx;
     j.skip = 0;
     j.rows = P->rows;

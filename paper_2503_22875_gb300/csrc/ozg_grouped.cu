@@ -7,6 +7,7 @@
 // longest-first to the least-loaded CTA; the persistent kernel's CTA b then walks slots
 // b, b + grid, ... of the interleaved list (empty slots are skipped).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <queue>
 #include <vector>
@@ -25,6 +26,12 @@ struct GroupPlan {
   size_t oJobs = 0, oRmPre = 0, oDgPre = 0, oCalls = 0, oTiles = 0, oNative = 0, oFlagPtrs = 0;
   size_t oNList = 0, oNPre = 0, oNTot = 0, oChecks = 0, oErrs = 0, oCold = 0, oR = 0;
   std::vector<int> s_used;
+  // automatic (selector) calls
+  int any_auto = 0, s_fb = 0;
+  int64_t save_units = 0;
+  size_t oHist = 0, hist_bytes = 0, oSel = 0, oSused = 0, oRep = 0, oSavePre = 0, oSaved = 0;
+  size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0;
+  std::vector<char> autom;
 };
 
 void destroy_plan(GroupPlan* p) {
@@ -84,6 +91,14 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
   OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int64_t>(c, P.oRmPre), P.rowmax_units,
                                 gat<int64_t>(c, P.oDgPre), P.digit_units, P.njobs, st));
+  if (P.any_auto) {
+    OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
+    OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int64_t>(c, P.oDgPre), P.digit_units, P.njobs,
+                                     st));
+    OZG_CUDA(launch_select_batched(c->dsel, gat<SelectJob>(c, P.oSel), P.ncalls, (float)std::log10(c->target), st));
+    OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
+                                         P.ncalls, 0, st));
+  }
   if (P.nsamp > 0) OZG_CUDA(launch_check_batched_pre(gat<CheckArgs>(c, P.oChecks), P.ncalls, P.nsamp, st));
   GroupArgs g;
   g.tiles = gat<GroupTile>(c, P.oTiles);
@@ -97,6 +112,16 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
                                  2 * c->num_sms, st));
   if (P.nsamp > 0)
     OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, P.oChecks), P.ncalls, P.nsamp, gat<double>(c, P.oErrs), st));
+  if (P.any_auto) {  // the check judges the selector: re-run rejected calls at the fallback count
+    OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, P.oRep), P.ncalls, c->target, st));
+    OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
+                                         P.ncalls, 1, st));
+    GroupArgs g2 = g;
+    g2.calls = gat<GroupCall>(c, P.oCalls2);
+    OZG_CUDA(launch_slice_gemm_grouped(g2, P.variant, P.grid, st));
+    OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, P.oChecks2), P.ncalls, P.nsamp, gat<double>(c, P.oErrs2),
+                                       st));
+  }
   return OZG_OK;
 }
 
@@ -119,8 +144,19 @@ int check_desc(const ozg_gemm_desc& d, char& ta, char& tb) {
 
 // Build (upload) the plan's tables for `variant` into the grouped workspace.
 int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vector<int>& s,
-               const std::vector<char>& TA, const std::vector<char>& TB, int variant, GroupPlan* P) {
-  const int nsamp = c->check_samples;
+               const std::vector<char>& TA, const std::vector<char>& TB, const std::vector<char>& autom, int variant,
+               GroupPlan* P) {
+  // s[i]: slice count of fixed calls; for automatic calls the fallback count (a cost estimate
+  // and the re-run count), while their digit planes are written for the selector's top class
+  int any_auto = 0;
+  for (int64_t i = 0; i < count; ++i) any_auto |= autom[i];
+  const int s_hi = std::max(c->sel_s_hi, c->fallback_slices);
+  std::vector<int> planes(count);
+  for (int64_t i = 0; i < count; ++i) planes[i] = autom[i] ? s_hi : s[i];
+  const int nsamp = any_auto ? std::max(c->check_samples, 64) : c->check_samples;
+  P->any_auto = any_auto;
+  P->autom = autom;
+  P->s_fb = c->fallback_slices;
   P->ncalls = (int)count;
   P->nsamp = nsamp;
   P->variant = variant;
@@ -147,8 +183,8 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     const int64_t Kp = (d[i].k + 7) / 8 * 8;
     oEA[i] = cv.take(4 * (size_t)d[i].m);
     oEB[i] = cv.take(4 * (size_t)d[i].n);
-    oDA[i] = cv.take((size_t)s[i] * d[i].m * Kp * 2);
-    oDB[i] = cv.take((size_t)s[i] * d[i].n * Kp * 2);
+    oDA[i] = cv.take((size_t)planes[i] * d[i].m * Kp * 2);
+    oDB[i] = cv.take((size_t)planes[i] * d[i].n * Kp * 2);
   }
   P->njobs = (int)(2 * count);
   P->oJobs = cv.take(sizeof(SplitArgs) * 2 * count);
@@ -165,6 +201,26 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->oErrs = cv.take(sizeof(double) * count);
   P->oCold = cv.take(sizeof(double) * 2 * (size_t)std::max(nsamp, 1) * count);
   P->oR = cv.take((size_t)P->grid * 128 * 256 * 8);
+  std::vector<int64_t> sp(count + 1, 0);
+  std::vector<size_t> oSv(count, 0);
+  if (any_auto) {
+    P->oHist = cv.take(sizeof(unsigned long long) * 20 * count);
+    P->hist_bytes = sizeof(unsigned long long) * 20 * count;
+    P->oSel = cv.take(sizeof(SelectJob) * count);
+    P->oSused = cv.take(sizeof(int) * count);
+    P->oRep = cv.take(sizeof(RepairJob) * count);
+    P->oSavePre = cv.take(sizeof(int64_t) * (count + 1));
+    P->oCalls2 = cv.take(sizeof(GroupCall) * count + 64);
+    P->oChecks2 = cv.take(sizeof(CheckArgs) * count);
+    P->oErrs2 = cv.take(sizeof(double) * count);
+    P->oSkip2 = cv.take(sizeof(int) * count);
+    for (int64_t i = 0; i < count; ++i) {
+      const bool sv = autom[i] && d[i].beta != 0.0;
+      sp[i + 1] = sp[i] + (sv ? (d[i].m * d[i].n + 255) / 256 : 0);
+      if (sv) oSv[i] = cv.take(sizeof(double) * d[i].m * d[i].n);
+    }
+    P->save_units = sp[count];
+  }
   int rc = ensure_gws(c, cv.off);
   if (rc) return rc;
   P->epoch = c->gws_epoch;
@@ -184,13 +240,14 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     a.rows = d[i].m;
     a.k = d[i].k;
     a.strided = (TA[i] == 'N');
-    a.s = s[i];
+    a.s = planes[i];
     a.Kp = Kp;
     a.plane_rows = d[i].m;
     a.D = gat<__half>(c, oDA[i]);
     a.maxbits = gat<unsigned long long>(c, oMA[i]);
     a.exps = gat<int32_t>(c, oEA[i]);
     a.nonfinite = flags + i;
+    a.hist = autom[i] ? gat<unsigned long long>(c, P->oHist) + 20 * i : nullptr;
     SplitArgs b = a;
     b.X = d[i].B;
     b.ld = d[i].ldb;
@@ -200,6 +257,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     b.D = gat<__half>(c, oDB[i]);
     b.maxbits = gat<unsigned long long>(c, oMB[i]);
     b.exps = gat<int32_t>(c, oEB[i]);
+    b.hist = autom[i] ? gat<unsigned long long>(c, P->oHist) + 20 * i + 10 : nullptr;
     jobs[2 * i] = a;
     jobs[2 * i + 1] = b;
     // units: rows per rowmax unit 256 (strided) / 8 (contiguous); digit tiles 32 x 64
@@ -211,8 +269,8 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     dg[2 * i + 2] = dg[2 * i + 1] + dg_units(b);
 
     GroupCall& g = calls[i];
-    OZG_CUDA(make_digit_tmap(&g.tmA, a.D, d[i].k, d[i].m, Kp, s[i], 128));
-    OZG_CUDA(make_digit_tmap(&g.tmB, b.D, d[i].k, d[i].n, Kp, s[i], BN));
+    OZG_CUDA(make_digit_tmap(&g.tmA, a.D, d[i].k, d[i].m, Kp, planes[i], 128));
+    OZG_CUDA(make_digit_tmap(&g.tmB, b.D, d[i].k, d[i].n, Kp, planes[i], BN));
     g.rows = d[i].m;
     g.cols = d[i].n;
     g.m = d[i].m;
@@ -268,6 +326,44 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     ck.gate = flags + i;
   }
   c->check_seed += 1;
+  std::vector<SelectJob> sel;
+  std::vector<RepairJob> rep;
+  std::vector<GroupCall> calls2;
+  std::vector<CheckArgs> chk2;
+  if (any_auto) {
+    sel.resize(count);
+    rep.resize(count);
+    calls2 = calls;
+    chk2 = chk;
+    GroupCall* calls_dev = gat<GroupCall>(c, P->oCalls);
+    for (int64_t i = 0; i < count; ++i) {
+      SelectJob& J = sel[i];
+      J.histA = gat<unsigned long long>(c, P->oHist) + 20 * i;
+      J.histB = J.histA + 10;
+      J.m = d[i].m;
+      J.n = d[i].n;
+      J.k = d[i].k;
+      J.s_out1 = &calls_dev[i].s;  // the grouped kernel reads the call's slice count here
+      J.s_out2 = gat<int>(c, P->oSused) + i;
+      J.s_cap = planes[i];
+      J.active = autom[i];
+      RepairJob& R = rep[i];
+      R.auto_mode = autom[i];
+      R.beta_nz = d[i].beta != 0.0;
+      R.err = gat<double>(c, P->oErrs) + i;
+      R.skip2 = gat<int>(c, P->oSkip2) + i;
+      R.nonfinite = flags + i;
+      R.C = d[i].C;
+      R.saved = (autom[i] && d[i].beta != 0.0) ? gat<double>(c, oSv[i]) : nullptr;
+      R.m = d[i].m;
+      R.n = d[i].n;
+      R.ldc = d[i].ldc;
+      calls2[i].s = std::min(s[i], planes[i]);
+      calls2[i].nonfinite = R.skip2;  // the re-run launch skips every call not being re-run
+      chk2[i].err_out = gat<double>(c, P->oErrs2) + i;
+      chk2[i].gate = R.skip2;
+    }
+  }
   P->rowmax_units = rm.back();
   P->digit_units = dg.back();
   cudaStream_t st = c->stream;
@@ -279,6 +375,16 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oNative), nat.data(), sizeof(NativeArgs) * nat.size(), cudaMemcpyHostToDevice, st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oFlagPtrs), fptr.data(), sizeof(int*) * fptr.size(), cudaMemcpyHostToDevice, st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oChecks), chk.data(), sizeof(CheckArgs) * chk.size(), cudaMemcpyHostToDevice, st));
+  if (any_auto) {
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oSel), sel.data(), sizeof(SelectJob) * count, cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oRep), rep.data(), sizeof(RepairJob) * count, cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oSavePre), sp.data(), sizeof(int64_t) * (count + 1),
+                             cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oCalls2), calls2.data(), sizeof(GroupCall) * count,
+                             cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oChecks2), chk2.data(), sizeof(CheckArgs) * count,
+                             cudaMemcpyHostToDevice, st));
+  }
   OZG_CUDA(cudaStreamSynchronize(st));  // host tables are stack-owned
   return OZG_OK;
 }
@@ -294,7 +400,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
   if (!c || count < 0 || (count > 0 && !descs)) return OZG_ERR_INVALID;
   if (count == 0) return OZG_OK;
   if (count > (1 << 20)) return OZG_ERR_UNSUPPORTED;
-  std::vector<char> TA(count), TB(count);
+  std::vector<char> TA(count), TB(count), autom_all(count, 0);
   std::vector<int> s(count);
   bool bad = false;
   for (int64_t i = 0; i < count; ++i) {
@@ -302,6 +408,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     const int si = slices ? slices[i] : 0;
     if (!rc && (si < 0 || si > OZG_MAX_SLICES)) rc = -14;
     s[i] = si == 0 ? c->fallback_slices : si;
+    autom_all[i] = (si == 0 && c->sel_s_hi > 0) ? 1 : 0;
     if (reps) {
       std::memset(&reps[i], 0, sizeof(ozg_report));
       reps[i].status = rc;
@@ -318,7 +425,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     const ozg_gemm_desc& d = descs[i];
     if (d.m == 0 || d.n == 0 || d.k == 0 || d.alpha == 0.0) {
       int rc = ozg_dgemm(c, d.transa, d.transb, d.m, d.n, d.k, d.alpha, d.A, d.lda, d.B, d.ldb, d.beta, d.C, d.ldc,
-                         s[i], nullptr);
+                         slices ? slices[i] : 0, nullptr);
       if (rc) return rc;
       if (reps) reps[i].samples = 0;
       continue;
@@ -330,16 +437,18 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
   if (work.empty()) return OZG_OK;
   cudaSetDevice(c->device);
   const int64_t n = (int64_t)work.size();
-  std::vector<char> wa(n), wb(n);
+  std::vector<char> wa(n), wb(n), wauto(n);
   for (int64_t i = 0; i < n; ++i) {
     wa[i] = TA[widx[i]];
     wb[i] = TB[widx[i]];
+    wauto[i] = autom_all[widx[i]];
   }
   uint64_t key = 1469598103934665603ull;
   key = fnv(key, work.data(), sizeof(ozg_gemm_desc) * n);
   key = fnv(key, ws.data(), sizeof(int) * n);
   key = fnv(key, &c->check_samples, sizeof(int));
   key = fnv(key, &c->autotune, sizeof(int));
+  key = fnv(key, wauto.data(), n);
 
   GroupPlan* P = c->plan.get();
   const bool reuse = P && P->key == key && P->epoch == c->gws_epoch;
@@ -364,7 +473,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
       float best = 1e30f;
       for (int v = 0; v < 2; ++v) {
         std::unique_ptr<GroupPlan, PlanDeleter> T(new GroupPlan());
-        int rc = build_plan(c, n, work.data(), ws, wa, wb, v, T.get());
+        int rc = build_plan(c, n, work.data(), ws, wa, wb, wauto, v, T.get());
         if (rc) return rc;
         cudaEvent_t e0 = pool_get(c), e1 = pool_get(c);
         if (!e0 || !e1) return OZG_ERR_CUDA;
@@ -387,7 +496,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
       c->tune[key] = variant;
     }
     std::unique_ptr<GroupPlan, PlanDeleter> NP(new GroupPlan());
-    int rc = build_plan(c, n, work.data(), ws, wa, wb, variant, NP.get());
+    int rc = build_plan(c, n, work.data(), ws, wa, wb, wauto, variant, NP.get());
     if (rc) return rc;
     NP->key = key;
     if (c->graphs && c->stream != nullptr) {
@@ -414,19 +523,28 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     if (rc) return rc;
   }
   if (reps) {
-    std::vector<int> fl(n);
-    std::vector<double> er(n, NAN);
-    OZG_CUDA(cudaMemcpyAsync(fl.data(), gat<int>(c, P->oFlags), sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int> fl(n), su(n, 0), sk(n, 1);
+    std::vector<double> er(n, NAN), er2(n, NAN);
+    cudaStream_t st = c->stream;
+    OZG_CUDA(cudaMemcpyAsync(fl.data(), gat<int>(c, P->oFlags), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
     if (P->nsamp > 0)
-      OZG_CUDA(cudaMemcpyAsync(er.data(), gat<double>(c, P->oErrs), sizeof(double) * n, cudaMemcpyDeviceToHost,
-                               c->stream));
-    OZG_CUDA(cudaStreamSynchronize(c->stream));
+      OZG_CUDA(cudaMemcpyAsync(er.data(), gat<double>(c, P->oErrs), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (P->any_auto) {
+      OZG_CUDA(cudaMemcpyAsync(su.data(), gat<int>(c, P->oSused), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(sk.data(), gat<int>(c, P->oSkip2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(er2.data(), gat<double>(c, P->oErrs2), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    }
+    OZG_CUDA(cudaStreamSynchronize(st));
     for (int64_t i = 0; i < n; ++i) {
       ozg_report& r = reps[widx[i]];
+      const bool au = P->any_auto && wauto[i];
+      const bool rerun = au && !fl[i] && !sk[i];
       r.nonfinite = fl[i];
-      r.slices_used = fl[i] ? -1 : ws[i];
+      r.selected = au ? su[i] : 0;
+      r.repaired = rerun ? 1 : 0;
+      r.slices_used = fl[i] ? -1 : (au ? (rerun ? ws[i] : su[i]) : ws[i]);
       r.samples = (P->nsamp > 0 && !fl[i]) ? P->nsamp : 0;
-      r.est_err = r.samples ? er[i] : NAN;
+      r.est_err = r.samples ? (rerun ? er2[i] : er[i]) : NAN;
     }
   }
   return OZG_OK;

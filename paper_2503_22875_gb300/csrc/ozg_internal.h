@@ -25,6 +25,7 @@ struct SplitArgs {
   unsigned long long* maxbits = nullptr;  // [rows] scratch, zeroed by the launcher
   int32_t* exps = nullptr;        // [rows] output exponents
   int* nonfinite = nullptr;       // set to 1 if any entry is Inf/NaN
+  unsigned long long* hist = nullptr;  // selector features: 10 gap-histogram counters (nullable)
 };
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 
@@ -51,6 +52,7 @@ struct GemmArgs {
   const int* nonfinite = nullptr;  // if non-null and set, the kernel exits (native path takes over)
   int grid = 0;                 // CTAs to launch (<= tiles); Rws must hold grid tiles
   int variant = 0;              // tile width: 0 -> BN = 256, 1 -> BN = 128
+  const int* s_dev = nullptr;   // if set, the slice count is read here (device-chosen); s = plane count
 };
 
 // Grouped (batched) GEMM: one persistent launch over the tiles of many independent problems.
@@ -135,6 +137,21 @@ cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, in
 // prefix arrays: njobs + 1 entries, prefix[0] = 0, prefix[njobs] = units
 cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int64_t* rowmax_prefix_dev, int64_t rowmax_units,
                                  const int64_t* digit_prefix_dev, int64_t digit_units, int njobs, cudaStream_t st);
+// grouped automatic calls: after the check, skip2[c] = 0 for the calls to re-run (automatic,
+// finite, sampled error above the target), 1 otherwise; save / restore C of automatic calls
+// with beta != 0 (restore only for the calls being re-run)
+struct RepairJob {
+  int auto_mode = 0, beta_nz = 0;
+  const double* err = nullptr;
+  int* skip2 = nullptr;
+  const int* nonfinite = nullptr;
+  double* C = nullptr;
+  double* saved = nullptr;
+  int64_t m = 0, n = 0, ldc = 0;
+};
+cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, cudaStream_t st);
+cudaError_t launch_save_restore_batched(const RepairJob* jobs_dev, const int64_t* prefix_dev, int64_t units,
+                                        int njobs, int restore, cudaStream_t st);
 // native FP64 for the real calls whose *flags_dev[c] != 0 (list, prefix, total: device scratch
 // of ncalls, ncalls + 1 and 2 entries)
 cudaError_t launch_native_batched(const NativeArgs* calls_dev, int ncalls, const int* const* flags_dev, int* list_dev,
@@ -143,5 +160,47 @@ cudaError_t launch_native_batched(const NativeArgs* calls_dev, int ncalls, const
 // C = beta * C (beta == 0: zero fill), m x n, complex if cplx
 cudaError_t launch_scale_c(double* C, int64_t m, int64_t n, int64_t ldc, const double* beta, int cplx,
                            cudaStream_t st);
+
+// ---------------------------------------------------------------------------------- selector
+constexpr int kSelIn = 24, kSelH = 64, kSelOut = 11;
+constexpr int kSelParams = kSelH * kSelIn + kSelH + kSelH * kSelH + kSelH + kSelOut * kSelH + kSelOut;
+struct SelectorDev {
+  float mean[kSelIn], inv_std[kSelIn];
+  uint16_t W1[kSelH * kSelIn];  // BF16 bit patterns, row-major [out][in]
+  float b1[kSelH];
+  uint16_t W2[kSelH * kSelH];
+  float b2[kSelH];
+  uint16_t W3[kSelOut * kSelH];
+  float b3[kSelOut];
+  float threshold;
+  int s_lo, fallback, pad;
+};
+struct SelectJob {
+  const unsigned long long* histA = nullptr;
+  const unsigned long long* histB = nullptr;
+  int64_t m = 0, n = 0, k = 0;
+  int* s_out1 = nullptr;  // e.g. the grouped call's slice count
+  int* s_out2 = nullptr;  // e.g. the report slot
+  int s_cap = 0, active = 0;
+};
+cudaError_t launch_gap_hist_pair(const SplitArgs& a, const SplitArgs& b, cudaStream_t st);
+cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int64_t* digit_prefix_dev, int64_t units,
+                                    int njobs, cudaStream_t st);
+// M may be null: then only feat_out is written
+cudaError_t launch_select_single(const SelectorDev* M, const unsigned long long* hA, const unsigned long long* hB,
+                                 int64_t m, int64_t n, int64_t k, float log10_target, int s_cap, int* s_out,
+                                 float* feat_out, float* prob_out, cudaStream_t st);
+cudaError_t launch_select_batched(const SelectorDev* M, const SelectJob* jobs_dev, int njobs, float log10_target,
+                                  cudaStream_t st);
+int read_selector_file(const char* path, SelectorDev* out);
+// after the check of an automatic call: not_repaired = (err <= target); when not, restore C from
+// `saved` (m x n, ld m, w doubles per element) if restore != 0
+cudaError_t launch_repair_prep(const double* err, double target, int* not_repaired, const double* saved, double* C,
+                               int64_t m, int64_t n, int64_t ldc, int w, int restore, cudaStream_t st);
+// training: theta = [W1, b1, W2, b2, W3, b3] FP32 master weights (kSelParams floats)
+cudaError_t launch_mlp_grads(const float* theta, const float* X, const int* y, int B, float* grad, float* loss,
+                             cudaStream_t st);
+cudaError_t launch_adam(float* theta, const float* grad, float* m1, float* m2, int step, float lr, float b1, float b2,
+                        float eps, float scale, cudaStream_t st);
 
 }  // namespace ozg

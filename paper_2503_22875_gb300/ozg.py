@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+SELECTOR_PARAMS = 6475
 
 
 class OzgError(RuntimeError):
@@ -40,7 +41,8 @@ class GemmDesc(ctypes.Structure):
 
 class Report(ctypes.Structure):
     _fields_ = [("slices_used", ctypes.c_int), ("nonfinite", ctypes.c_int), ("status", ctypes.c_int),
-                ("samples", ctypes.c_int), ("est_err", ctypes.c_double)]
+                ("samples", ctypes.c_int), ("est_err", ctypes.c_double), ("selected", ctypes.c_int),
+                ("repaired", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -75,6 +77,13 @@ def load():
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_load_selector.argtypes = [vp, ctypes.c_char_p]
+    L.ozg_set_target_error.argtypes = [vp, dbl]
+    L.ozg_selector_features.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, vp, vp]
+    L.ozg_selector_set_params.argtypes = [vp, vp]
+    L.ozg_selector_get_params.argtypes = [vp, vp]
+    L.ozg_selector_grads.argtypes = [vp, vp, vp, i32, vp, vp]
+    L.ozg_selector_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, vp]
     L.ozg_set_graphs.argtypes = [vp, i32]
     L.ozg_set_fallback_slices.argtypes = [vp, i32]
     L.ozg_set_autotune.argtypes = [vp, i32, ctypes.c_char_p]
@@ -199,6 +208,39 @@ class Context:
     def set_autotune(self, enable: bool, cache_path: str | None = None):
         _check(load().ozg_set_autotune(self._h, int(bool(enable)), cache_path.encode() if cache_path else None),
                "ozg_set_autotune")
+
+    # ---- learned slice selector
+    def load_selector(self, path: str):
+        _check(load().ozg_load_selector(self._h, path.encode()), "ozg_load_selector")
+
+    def set_target_error(self, target: float):
+        _check(load().ozg_set_target_error(self._h, float(target)), "ozg_set_target_error")
+
+    def selector_features(self, transa, transb, m, n, k, A, lda, B, ldb, feat_out, prob_out=None, s_out=None):
+        _check(load().ozg_selector_features(self._h, _c(transa), _c(transb), m, n, k, _p(A), lda, _p(B), ldb,
+                                            _p(feat_out), _p(prob_out), _p(s_out)), "ozg_selector_features")
+
+    def selector_set_params(self, theta: np.ndarray):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(load().ozg_selector_set_params(self._h, t.ctypes.data), "ozg_selector_set_params")
+
+    def selector_get_params(self) -> np.ndarray:
+        t = np.zeros(SELECTOR_PARAMS, dtype=np.float32)
+        _check(load().ozg_selector_get_params(self._h, t.ctypes.data), "ozg_selector_get_params")
+        return t
+
+    def selector_grads(self, X, y, B):
+        g = np.zeros(SELECTOR_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(load().ozg_selector_grads(self._h, _p(X), _p(y), int(B), g.ctypes.data, ctypes.byref(loss)),
+               "ozg_selector_grads")
+        return float(loss.value), g
+
+    def selector_train_step(self, X, y, B, lr):
+        loss = ctypes.c_float()
+        _check(load().ozg_selector_train_step(self._h, _p(X), _p(y), int(B), float(lr), ctypes.byref(loss)),
+               "ozg_selector_train_step")
+        return float(loss.value)
 
     def native_dgemm(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc):
         _check(load().ozg_native_dgemm(self._h, _c(transa), _c(transb), m, n, k, float(alpha), _p(A), lda, _p(B),

@@ -79,3 +79,22 @@ def grouped_batch(count: int = 2048, lo: int = 32, hi: int = 2048, phi_hi: float
 
 def call_matrices(c: GemmCall):
     return wide_exponent_pair(c.m, c.n, c.k, c.phi, seed=c.seed)
+
+
+def grouped_batch_device(count: int = 2048, lo: int = 32, hi: int = 2048, phi_hi: float = 4.0, seed: int = 4,
+                         device: str = "cuda"):
+    """The grouped batch drawn directly on the GPU (torch generator, seeded): the same shape and
+    spread distribution as grouped_batch, for benchmark-sized batches.  Returns a list of
+    (m, n, k, phi, A, B) with A (m x k) and B (k x n) as column-major torch tensors."""
+    import torch
+    calls = grouped_batch(count, lo, hi, phi_hi, seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = []
+    for c in calls:
+        def draw(rows, cols):
+            u = torch.rand((cols, rows), generator=gen, device=device, dtype=torch.float64)
+            z = torch.randn((cols, rows), generator=gen, device=device, dtype=torch.float64)
+            return (u - 0.5) * torch.exp(c.phi * z)  # shape (cols, rows): column-major rows x cols
+        out.append((c.m, c.n, c.k, c.phi, draw(c.m, c.k), draw(c.k, c.n)))
+    return out

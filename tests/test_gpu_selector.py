@@ -1,0 +1,176 @@
+"""Learned slice selector on the GPU: features, gradients and decisions against the oracle, the
+automatic path (selection, check, re-run at the fallback count) against the emulation oracle,
+and the labels of the training data against the oracle's double-double errors."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_22875_gb300 import selector, workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def ozg():
+    from paper_2503_22875_gb300 import build, ozg
+    build.build()
+    ozg.load()
+    return ozg
+
+
+def wide(shape, phi, seed):
+    X = workloads.wide_exponent(shape, phi, workloads.rng(seed))
+    X.flat[::13] = 0.0
+    return np.asfortranarray(X)
+
+
+@pytest.mark.parametrize("ta,tb,phi", [("N", "N", 3.0), ("T", "N", 6.0), ("N", "T", 0.5), ("T", "T", 2.0)])
+def test_features_match_oracle(ozg, ta, tb, phi):
+    m, n, k = 150, 90, 333
+    A = wide((m, k) if ta == "N" else (k, m), phi, 401)
+    B = wide((k, n) if tb == "N" else (n, k), phi, 402)
+    ctx = ozg.Context()
+    ctx.set_target_error(1e-11)
+    f = torch.zeros(24, dtype=torch.float32, device="cuda")
+    ctx.selector_features(ta, tb, m, n, k, ozg.to_device(A), A.shape[0], ozg.to_device(B), B.shape[0], f)
+    g = f.cpu().numpy()
+    o = oracle.features(A, B, 1e-11, ta, tb)
+    np.testing.assert_array_equal(g[3:23], o[3:23])
+    np.testing.assert_allclose(g[[0, 1, 2, 23]], o[[0, 1, 2, 23]], rtol=1e-6)
+    ctx.close()
+
+
+def test_gradients_match_oracle(ozg):
+    r = np.random.default_rng(410)
+    theta = (r.normal(0, 0.2, selector.PARAMS)).astype(np.float32)
+    X = r.normal(size=(200, 24)).astype(np.float32)
+    y = r.integers(0, 11, 200).astype(np.int32)
+    ctx = ozg.Context()
+    ctx.selector_set_params(theta)
+    loss, g = ctx.selector_grads(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), 200)
+    lo, go = oracle.mlp_loss_grad(theta, X, y)
+    assert abs(loss - lo) <= 1e-5 * abs(lo)
+    assert np.linalg.norm(g - go) <= 1e-4 * np.linalg.norm(go)
+    ctx.close()
+
+
+def test_training_reduces_loss(ozg):
+    r = np.random.default_rng(411)
+    X = r.normal(size=(2048, 24)).astype(np.float32)
+    w = r.normal(size=(24, 11))
+    y = (X @ w).argmax(1).astype(np.int32)  # a learnable rule
+    ctx = ozg.Context()
+    theta, mean, std, losses = selector.train(ctx, X, y, epochs=30, batch=256, lr=3e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    ctx.close()
+
+
+def random_model(path, seed, thr=0.9, fallback=10, bias=None):
+    r = np.random.default_rng(seed)
+    theta = r.normal(0, 0.3, selector.PARAMS).astype(np.float32)
+    if bias is not None:  # force one class: zero last-layer weights, large bias on that class
+        p = selector.split_theta(theta)
+        theta[selector.PARAMS - 11 - 11 * 64:selector.PARAMS - 11] = 0.0
+        theta[selector.PARAMS - 11:] = -20.0
+        theta[selector.PARAMS - 11 + bias] = 20.0
+    mean = r.normal(size=24).astype(np.float32)
+    std = np.abs(r.normal(size=24)).astype(np.float32) + 0.5
+    selector.write_model(str(path), theta, mean, std, thr, fallback)
+    return selector.read_model(str(path))
+
+
+def test_decision_matches_cpu_emulation(ozg, tmp_path):
+    path = tmp_path / "rand.ozgsel"
+    model = random_model(path, 420)
+    ctx = ozg.Context()
+    ctx.load_selector(str(path))
+    f = torch.zeros(24, dtype=torch.float32, device="cuda")
+    p = torch.zeros(11, dtype=torch.float32, device="cuda")
+    sdev = torch.zeros(1, dtype=torch.int32, device="cuda")
+    agree = 0
+    for i, phi in enumerate(np.linspace(0, 6, 12)):
+        m, n, k = 40 + 17 * i, 70 + 5 * i, 100 + 31 * i
+        A, B = wide((m, k), phi, 500 + i), wide((k, n), phi, 600 + i)
+        ctx.selector_features("N", "N", m, n, k, ozg.to_device(A), m, ozg.to_device(B), k, f, p, sdev)
+        s_cpu, probs = oracle.mlp_select(model, f.cpu().numpy(), 12)
+        np.testing.assert_allclose(p.cpu().numpy(), probs, rtol=1e-5, atol=1e-7)
+        cum = np.cumsum(probs)
+        near = np.any(np.abs(cum - model["thr"]) < 1e-5)
+        assert int(sdev.item()) == s_cpu or near
+        agree += int(sdev.item()) == s_cpu
+    assert agree >= 11
+    ctx.close()
+
+
+def emu_check(ozg, C, A, B, s, alpha=1.0, beta=0.0, C0=None):
+    E = oracle.dgemm_emu(A, B, s, "N", "N", alpha, beta, C0)
+    tol = 4 * (s + 2) * U * abs(alpha) * oracle.abs_product(A, B) + 2 * U * np.abs(E)
+    if C0 is not None:
+        tol = tol + 2 * U * abs(beta) * np.abs(C0)
+    assert (np.abs(C - E) <= tol).all()
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.5])
+def test_auto_single_call_select_and_repair(ozg, tmp_path, beta):
+    m, n, k = 130, 260, 200
+    A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=430)
+    C0 = np.asfortranarray(workloads.rng(431).uniform(-1, 1, (m, n)))
+    for bias, expect_repair in ((0, True), (10, False)):  # s = 2 (too small) or s = 12
+        path = tmp_path / f"bias{bias}.ozgsel"
+        random_model(path, 440 + bias, fallback=9, bias=bias)
+        ctx = ozg.Context()
+        ctx.load_selector(str(path))
+        ctx.set_fallback_slices(9)
+        dC = ozg.to_device(C0)
+        rep = ctx.dgemm("N", "N", m, n, k, 1.0, ozg.to_device(A), m, ozg.to_device(B), k, beta, dC, m, 0, report=True)
+        assert rep.selected == 2 + bias and rep.repaired == int(expect_repair)
+        assert rep.slices_used == (9 if expect_repair else 12)
+        assert rep.samples >= 64 and rep.est_err <= 1e-12
+        emu_check(ozg, ozg.from_device(dC, m, n), A, B, rep.slices_used, 1.0, beta, C0 if beta else None)
+        ctx.close()
+
+
+def test_auto_grouped_mixed(ozg, tmp_path):
+    path = tmp_path / "b0.ozgsel"
+    random_model(path, 450, fallback=8, bias=0)  # always s = 2: every automatic call is re-run
+    st = torch.cuda.Stream()
+    ctx = ozg.Context(stream=st)
+    ctx.load_selector(str(path))
+    ctx.set_fallback_slices(8)
+    batch = []
+    for i in range(12):
+        m, n, k = 30 + 23 * i, 50 + 11 * i, 40 + 37 * i
+        A, B = workloads.wide_exponent_pair(m, n, k, 0.5 * (i % 5), seed=460 + i)
+        beta = 0.0 if i % 3 else 1.5
+        C0 = np.asfortranarray(workloads.rng(470 + i).uniform(-1, 1, (m, n)))
+        s = 0 if i % 2 == 0 else 5
+        batch.append((m, n, k, A, B, beta, C0, s, ozg.to_device(A), ozg.to_device(B), ozg.to_device(C0)))
+    calls = [("N", "N", m, n, k, 1.0, dA, m, dB, k, beta, dC, m) for (m, n, k, A, B, beta, C0, s, dA, dB, dC) in batch]
+    with torch.cuda.stream(st):
+        reps = ctx.dgemm_grouped(calls, [b[7] for b in batch], report=True)
+    for r, (m, n, k, A, B, beta, C0, s, dA, dB, dC) in zip(reps, batch):
+        if s == 0:
+            assert r.selected == 2 and r.repaired == 1 and r.slices_used == 8
+        else:
+            assert r.selected == 0 and r.repaired == 0 and r.slices_used == 5
+        emu_check(ozg, ozg.from_device(dC, m, n), A, B, r.slices_used, 1.0, beta, C0 if beta else None)
+    ctx.close()
+
+
+def test_training_labels_against_oracle(ozg):
+    ctx = ozg.Context()
+    X, y, meta = selector.make_dataset(ctx, 6, seed=480, lo=64, hi=200, chunk=3, keep_blocks=True)
+    for p, (As, Bs) in enumerate(meta["blocks"]):
+        Am = np.asfortranarray(As.T)   # (bm, k)
+        Bm = np.asfortranarray(Bs.T)   # (k, bn)
+        for ci, s in enumerate(range(2, 13)):
+            C = oracle.dgemm_emu(Am, Bm, s)
+            full = oracle.rel_err_vs_dd(C, Am, Bm)
+            gpu = meta["errs"][p, ci]
+            # the sampled estimate is never above the true maximum, up to the epilogue's FP64
+            # rounding tolerance (the GPU's C and the oracle's C differ by at most that much)
+            assert gpu <= full + 4 * (s + 2) * U
+            assert gpu >= full / 100
+    ctx.close()
