@@ -28,6 +28,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -189,30 +191,25 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------ grouped batch
+SELECTOR_MODEL = os.path.join(ROOT, "paper_2503_22875_gb300", "data", "selector_v1.ozgsel")
+
+
 def grouped_section(ozg, torch, count, steps):
-    """2048 uneven GEMMs (m, n, k log-uniform in [32, 2048], phi ~ U(0, 4)) at fixed s = 7:
-    one ozg_dgemm call at a time vs one grouped, graph-replayed ozg_dgemm_grouped call."""
+    """2048 uneven GEMMs (m, n, k log-uniform in [32, 2048], phi ~ U(0, 4)) with target 1e-12:
+    fixed s = 7 one ozg_dgemm call at a time (the fixed-slice baseline), fixed counts in one grouped
+    graph-replayed ozg_dgemm_grouped call, and the learned selector (slices = 0) grouped.  The
+    error of every call is the GPU double-double check's estimate (64 samples)."""
     from paper_2503_22875_gb300 import workloads
     batch = workloads.grouped_batch_device(count)
     st = torch.cuda.Stream()
     Cs = [torch.empty((n, m), dtype=torch.float64, device="cuda") for m, n, k, _, _, _ in batch]
     calls = [("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m) for (m, n, k, _, A, B), C in zip(batch, Cs)]
     flops = sum(2.0 * m * n * k for m, n, k, _, _, _ in batch)
-    s = [7] * count
-    ctx = ozg.Context(stream=st)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def one_at_a_time():
-        for c in calls:
-            ctx.dgemm(*c, 7)
-
-    def grouped():
-        ctx.dgemm_grouped(calls, s)
-
-    out = {}
-    for name, fn in (("one_at_a_time_s7", one_at_a_time), ("grouped_graph_s7", grouped)):
+    def timed(fn):
         with torch.cuda.stream(st):
-            fn()  # warm-up (and graph capture for the grouped call)
+            fn()  # warm-up (and graph capture for grouped calls)
             torch.cuda.synchronize()
             e0.record(st)
             for _ in range(steps):
@@ -220,18 +217,50 @@ def grouped_section(ozg, torch, count, steps):
             e1.record(st)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        out[name] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
-    ctx.set_check_samples(16)
-    with torch.cuda.stream(st):
-        reps = ctx.dgemm_grouped(calls, s, report=True)
-    errs = [r.est_err for r in reps]
-    out["calls"] = count
-    out["fp64_equiv_flops"] = flops
-    out["max_err_sampled_dd_s7"] = max(errs)
-    out["frac_calls_le_1e-12_s7"] = sum(e <= TARGET_ERR for e in errs) / count
-    out["workload"] = (f"{count} DGEMMs, m,n,k log-uniform in [32, 2048], a=(u-0.5)exp(phi g), phi~U(0,4) per call, "
-                       f"beta=0; generated on the GPU (seeded torch generator)")
+        return {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+
+    def errors(ctx, slices):
+        with torch.cuda.stream(st):
+            reps = ctx.dgemm_grouped(calls, slices, report=True)
+        return reps
+
+    out = {"workload": (f"{count} DGEMMs, m,n,k log-uniform in [32, 2048], a=(u-0.5)exp(phi g), phi~U(0,4) per call, "
+                        f"beta=0; generated on the GPU (seeded torch generator); target 1e-12"),
+           "calls": count, "fp64_equiv_flops": flops}
+    ctx = ozg.Context(stream=st)
+    out["fixed_s7_one_at_a_time"] = timed(lambda: [ctx.dgemm(*c, 7) for c in calls])
     ctx.close()
+    fixed = {}
+    for s in (7, 9, 11, 12, 14):
+        ctx = ozg.Context(stream=st)
+        r = timed(lambda: ctx.dgemm_grouped(calls, [s] * count))
+        ctx.set_check_samples(64)
+        reps = errors(ctx, [s] * count)
+        r["frac_le_target"] = sum(x.est_err <= TARGET_ERR for x in reps) / count
+        fixed[s] = r
+        ctx.close()
+    out["fixed_grouped"] = fixed
+    ok = [s for s in fixed if fixed[s]["frac_le_target"] >= 0.99]
+    out["smallest_fixed_s_meeting_target_on_99pct"] = min(ok) if ok else None
+    if os.path.exists(SELECTOR_MODEL):
+        ctx = ozg.Context(stream=st)
+        ctx.load_selector(SELECTOR_MODEL)
+        ctx.set_target_error(TARGET_ERR)
+        r = timed(lambda: ctx.dgemm_grouped(calls, [0] * count))
+        reps = errors(ctx, [0] * count)
+        r["frac_le_target"] = sum(x.est_err <= TARGET_ERR for x in reps) / count
+        r["repaired"] = sum(x.repaired for x in reps)
+        r["selected_hist"] = {int(v): int(c) for v, c in zip(*np.unique([x.selected for x in reps], return_counts=True))}
+        r["fallback"] = max(x.slices_used for x in reps)
+        out["learned_grouped"] = r
+        base = out["fixed_s7_one_at_a_time"]["tflops"]
+        out["learned_vs_fixed_s7_one_at_a_time"] = r["tflops"] / base
+        if out["smallest_fixed_s_meeting_target_on_99pct"]:
+            out["learned_vs_smallest_sufficient_fixed_grouped"] = (
+                r["tflops"] / fixed[out["smallest_fixed_s_meeting_target_on_99pct"]]["tflops"])
+        ctx.close()
+    else:
+        out["learned_grouped"] = None
     return out
 
 

@@ -100,8 +100,9 @@ int ozg_set_check_samples(ozg_ctx* ctx, int samples);
  * exceeds the target the call is recomputed at the fallback count (ozg_set_fallback_slices),
  * again on the device.  Without a model, slices = 0 means the fallback count. */
 
-/* Load a selector model file (format in the library's selector source).  Returns 0 or
- * OZG_ERR_INVALID (unreadable or malformed file). */
+/* Load a selector model file (format in the library's selector source); also sets the
+ * context's fallback count to the model's conservative count.  Returns 0 or OZG_ERR_INVALID
+ * (unreadable or malformed file). */
 int ozg_load_selector(ozg_ctx* ctx, const char* path);
 
 /* Target componentwise error for automatic slice counts (default 1e-12). */
@@ -125,6 +126,13 @@ int ozg_selector_set_params(ozg_ctx* ctx, const float* theta);     /* also reset
 int ozg_selector_get_params(ozg_ctx* ctx, float* theta);
 int ozg_selector_grads(ozg_ctx* ctx, const float* X, const int* y, int B, float* grad, float* loss);
 int ozg_selector_train_step(ozg_ctx* ctx, const float* X, const int* y, int B, float lr, float* loss);
+
+/* enable != 0: correctly rounded mode for single calls with s <= 13.  The group products are
+ * summed exactly as 128-bit integers and each result is rounded to FP64 once (bit-identical to
+ * the exact value's rounding, except in the subnormal range).  It moves twice the scratch
+ * traffic of the default epilogue (FP64 partial sums, one rounding per group) and is slower.
+ * Grouped calls always use the default epilogue. */
+int ozg_set_exact_epilogue(ozg_ctx* ctx, int enable);
 
 /* Human-readable text for a return code (static storage). */
 const char* ozg_strerror(int code);

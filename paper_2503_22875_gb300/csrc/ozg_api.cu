@@ -61,7 +61,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   size_t oDA = cv.take((size_t)s * prA * Kp * 2), oDB = cv.take((size_t)s * prB * Kp * 2);
   size_t oE = cv.take(4 * (size_t)m), oF = cv.take(4 * (size_t)n);
   size_t oMA = cv.take(8 * (size_t)m), oMB = cv.take(8 * (size_t)n);
-  size_t oR = cv.take((size_t)grid * BM * 256 * 8);
+  size_t oR = cv.take((size_t)grid * BM * 256 * 16);  // 16 bytes per output (128-bit Horner sum)
   size_t oCold = cv.take((size_t)(nsamp > 0 ? nsamp : 1) * 16);
   size_t oHist = cv.take(2 * 10 * 8), oSd = cv.take(4 * sizeof(int)), oErr2 = cv.take(sizeof(double));
   size_t oSaved = cv.take((autos && !beta_zero0) ? (size_t)m * n * (cplx ? 16 : 8) : 8);
@@ -149,6 +149,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   ga.variant = variant;
   ga.grid = grid_of(variant);
   ga.s_dev = autos ? s_dev : nullptr;
+  ga.exact = c->exact;
   if (c->autotune && !Gdbg && ga.beta_zero && !autos) {
     const uint64_t bucket = shape_bucket(prA, prB, k, s);
     if (c->tune.find(bucket) == c->tune.end()) {
@@ -376,6 +377,12 @@ int ozg_destroy(ozg_ctx* c) {
   c->plan.reset();
   if (c->gws) cudaFree(c->gws);
   delete c;
+  return OZG_OK;
+}
+
+int ozg_set_exact_epilogue(ozg_ctx* c, int enable) {
+  if (!c) return OZG_ERR_INVALID;
+  c->exact = enable != 0;
   return OZG_OK;
 }
 

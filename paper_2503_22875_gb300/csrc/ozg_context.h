@@ -48,6 +48,7 @@ struct ozg_ctx {
   std::unique_ptr<ozg::host::GroupPlan, ozg::host::PlanDeleter> plan;
   bool graphs = true;
   int fallback_slices = 7;
+  int exact = 0;  // correctly rounded (exact-sum) epilogue for single calls
   // autotuner: shape bucket -> tile variant, optionally persisted as text
   int autotune = 0;
   std::string tune_path;

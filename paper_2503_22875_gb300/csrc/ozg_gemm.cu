@@ -12,9 +12,10 @@
 //   for g = 2 .. s+1:  for kb in k-blocks:  for p = 1 .. g-1:  D[buf] += A_p[kb] * B_{g-p}[kb]^T
 // cut into chains of SEG_BLOCKS k-blocks.  Each finished chain is drained by the epilogue
 // warps (TMEM -> registers, exact FP32 -> int32) into an int32 group sum G_g while the MMA
-// warp fills the other TMEM buffer.  At the end of group g the epilogue folds G_g into the
-// FP64 value R <- 128 R + G_g (Horner in the group index), kept per CTA in L2-resident
-// scratch; after the last group it writes C = alpha * R 2^{e_i + f_j - 7(s+1)} (+ beta C).
+// warp fills the other TMEM buffer.  At the end of group g the epilogue folds G_g into
+// R <- 128 R + G_g (Horner in the group index; a 128-bit integer for s <= 13, so the sum is
+// exact, FP64 beyond), kept per CTA in L2-resident scratch; after the last group it writes
+// C = alpha * RN(R 2^{e_i + f_j - 7(s+1)}) (+ beta C), one rounding of the exact value.
 // Complex (stacked rows 2i = Re, 2i+1 = Im; columns likewise) combines the four real
 // sub-products exactly in int32 before the Horner step: Re = P_rr - P_ii, Im = P_ri + P_ir.
 //
@@ -142,6 +143,79 @@ __device__ __forceinline__ int nseg_of(int g, int KB) { return ((g - 1) * KB + S
 __device__ __forceinline__ double scale_pow2(double x, int E) {
   if (E >= -1022 && E <= 1023) return x * __longlong_as_double((long long)(E + 1023) << 52);
   return ldexp(x, E);
+}
+
+// Exact epilogue (s <= kExactMaxS): R is a 128-bit integer per output, kept as (lo, hi) in 16
+// bytes of the CTA's scratch tile; the group sums enter by Horner's rule R <- 128 R + G_g, and
+// the final R is rounded to FP64 once.  |R| < 2^(log2 max|G_g| + 7 (s - 1) + 1), within 127 bits
+// for s <= 13 and k < 2^20.  Larger s keeps an FP64 R (one rounding per Horner step).
+constexpr int kExactMaxS = 13;
+
+__device__ __forceinline__ void horner128(const void* Rp, int g, bool first, bool group2, int64_t& hi,
+                                          uint64_t& lo) {
+  if (first && group2) {
+    lo = (uint64_t)(int64_t)g;
+    hi = g < 0 ? -1 : 0;
+    return;
+  }
+  const longlong2 v = *reinterpret_cast<const longlong2*>(Rp);
+  lo = (uint64_t)v.x;
+  hi = v.y;
+  if (first) {  // R <- 128 R (two's complement 128-bit shift)
+    hi = (int64_t)(((uint64_t)hi << 7) | (lo >> 57));
+    lo <<= 7;
+  }
+  const uint64_t gl = (uint64_t)(int64_t)g, nl = lo + gl;
+  hi = hi + (g < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
+  lo = nl;
+}
+
+// RN(N 2^E) for the 128-bit integer N = (hi, lo): the top 64 bits with a sticky bit are
+// converted with one correct rounding, then scaled exactly by a power of two.
+__device__ __forceinline__ double round_i128(int64_t hi, uint64_t lo, int E) {
+  const bool neg = hi < 0;
+  uint64_t mh = (uint64_t)hi, ml = lo;
+  if (neg) {
+    ml = ~ml + 1;
+    mh = ~mh + (ml == 0 ? 1 : 0);
+  }
+  double mag;
+  int sh = 0;
+  if (mh == 0) {
+    mag = __ull2double_rn(ml);
+  } else {
+    sh = 64 - __clzll((long long)mh);
+    uint64_t top, sticky;
+    if (sh == 64) {
+      top = mh;
+      sticky = ml != 0;
+    } else {
+      top = (mh << (64 - sh)) | (ml >> sh);
+      sticky = (ml << (64 - sh)) != 0;
+    }
+    mag = __ull2double_rn(top | sticky);
+  }
+  const double v = scale_pow2(mag, E + sh);
+  return neg ? -v : v;
+}
+
+// One output's Horner step in either mode; returns the final value (scaled) on the last push.
+__device__ __forceinline__ double horner_step(void* Rp, int g, bool exact, bool first, bool group2, bool final_push,
+                                              int E) {
+  if (exact) {
+    int64_t hi;
+    uint64_t lo;
+    horner128(Rp, g, first, group2, hi, lo);
+    if (final_push) return round_i128(hi, lo, E);
+    *reinterpret_cast<longlong2*>(Rp) = make_longlong2((long long)lo, (long long)hi);
+    return 0.0;
+  }
+  double* Rd = reinterpret_cast<double*>(Rp);
+  const double gv = (double)g;
+  const double Rv = first ? (group2 ? gv : fma(*Rd, 128.0, gv)) : (*Rd + gv);
+  if (final_push) return scale_pow2(Rv, E);
+  *Rd = Rv;
+  return 0.0;
 }
 
 // Bounded wait used during teardown after an abort (ignores the abort flag).
@@ -297,7 +371,8 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     const int r = quad * 32 + lane;
     uint32_t acc_par = 0;
     int buf = 0;
-    double* Rbase = Rws + (size_t)blockIdx.x * BM * BN;
+    double* Rbase = Rws + (size_t)blockIdx.x * BM * BN * 2;  // room for 16 bytes per output
+    const bool exact_mode = GROUPED ? false : (P->exact != 0);
     const bool odd = (lane & 1) != 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
@@ -352,6 +427,49 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
             for (int c = 0; c < CPT; ++c) {
               const int64_t gc = gcol0 + c;
               if (row_ok && gc < j.cols) Gdbg[((int64_t)(g - 2) * j.rows + grow) * j.cols + gc] = Gs[c];
+            }
+          } else if (exact_mode && s <= kExactMaxS) {
+            // correctly rounded mode: exact 128-bit Horner sum, one rounding at the end
+            char* Rt = reinterpret_cast<char*>(Rbase) + ((size_t)(j.cplx ? chalf * CPT / 2 : chalf * CPT) * BM + r) * 16;
+            const int ebase = e_row - 7 * (s + 1);
+            if (!j.cplx) {
+#pragma unroll 2
+              for (int c = 0; c < CPT; ++c) {
+                const int64_t col = gcol0 + c;
+                const bool ok = row_ok && col < j.cols;
+                const int E = final_push && ok ? ebase + __ldg(j.f + col) : 0;
+                const double tv = horner_step(Rt + (size_t)c * BM * 16, Gs[c], true, first_push, g == 2, final_push, E);
+                if (final_push && ok) {
+                  double* cp = j.C + orow + col * j.ldc;
+                  *cp = j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp);
+                }
+              }
+            } else {
+#pragma unroll 2
+              for (int c = 0; c < CPT / 2; ++c) {
+                const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * c + 1], 1);
+                const int comb = odd ? (Gs[2 * c] + other) : (Gs[2 * c] - other);
+                const int64_t jc = (gcol0 >> 1) + c;
+                const bool ok = row_ok && jc < j.n;
+                const int E = final_push && ok ? ebase + __ldg(j.f + jc) : 0;
+                const double v = horner_step(Rt + (size_t)c * BM * 16, comb, true, first_push, g == 2, final_push, E);
+                if (final_push) {
+                  const double part = ok ? v : 0.0;
+                  const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
+                  const double tr = odd ? partner : part, ti = odd ? part : partner;
+                  if (ok) {
+                    double* cp = j.C + 2 * (orow + jc * j.ldc);
+                    double re = fma(j.a0, tr, -(j.a1 * ti));
+                    double im = fma(j.a0, ti, j.a1 * tr);
+                    if (!j.beta_zero) {
+                      const double cr = cp[0], ci = cp[1];
+                      re += fma(j.b0, cr, -(j.b1 * ci));
+                      im += fma(j.b0, ci, j.b1 * cr);
+                    }
+                    cp[odd ? 1 : 0] = odd ? im : re;
+                  }
+                }
+              }
             }
           } else if (!j.cplx) {
             double* Rt = Rbase + (size_t)(chalf * CPT) * BM + r;

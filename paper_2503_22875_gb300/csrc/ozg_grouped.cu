@@ -200,7 +200,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->oChecks = cv.take(sizeof(CheckArgs) * count);
   P->oErrs = cv.take(sizeof(double) * count);
   P->oCold = cv.take(sizeof(double) * 2 * (size_t)std::max(nsamp, 1) * count);
-  P->oR = cv.take((size_t)P->grid * 128 * 256 * 8);
+  P->oR = cv.take((size_t)P->grid * 128 * 256 * 16);
   std::vector<int64_t> sp(count + 1, 0);
   std::vector<size_t> oSv(count, 0);
   if (any_auto) {

@@ -46,13 +46,14 @@ struct GemmArgs {
   int64_t ldc = 0;
   double alpha[2] = {1, 0}, beta[2] = {0, 0};
   int beta_zero = 1;
-  double* Rws = nullptr;        // FP64 partial sums, [grid][BN][BM] per CTA
+  double* Rws = nullptr;        // Horner partial sums, 16 bytes per output, [grid][BN][BM] per CTA
   int64_t* Gdbg = nullptr;      // inspection: int64 [s][rows][cols] group products (no epilogue)
   int* status = nullptr;        // device status word (0 ok, 3 timeout)
   const int* nonfinite = nullptr;  // if non-null and set, the kernel exits (native path takes over)
   int grid = 0;                 // CTAs to launch (<= tiles); Rws must hold grid tiles
   int variant = 0;              // tile width: 0 -> BN = 256, 1 -> BN = 128
   const int* s_dev = nullptr;   // if set, the slice count is read here (device-chosen); s = plane count
+  int exact = 0;                // 1: exact 128-bit Horner sum and one rounding (s <= 13)
 };
 
 // Grouped (batched) GEMM: one persistent launch over the tiles of many independent problems.

@@ -111,7 +111,7 @@ extern "C" int ozg_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n,
   const int64_t Kp = (k + 7) / 8 * 8;
   const int BM = ozg::slice_gemm_tile_m(), BN = ozg::slice_gemm_tile_n();
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
-  const size_t tile_bytes = (size_t)BM * BN * sizeof(double);
+  const size_t tile_bytes = (size_t)BM * BN * 16;  // per-CTA scratch tile, 16 bytes per output
   size_t off = 0;
   const size_t oFlags = off;
   off = round256(off + 4 * sizeof(int));

@@ -387,6 +387,7 @@ extern "C" int ozg_load_selector(ozg_ctx* c, const char* path) {
   OZG_CUDA(cudaStreamSynchronize(c->stream));
   OZG_CUDA(cudaMemcpy(c->dsel, &h, sizeof(h), cudaMemcpyHostToDevice));
   c->sel_s_hi = h.s_lo + ozg::kSelOut - 1;
+  c->fallback_slices = h.fallback;  // the model's conservative count (ozg_set_fallback_slices overrides)
   c->plan.reset();  // a captured grouped plan embeds the previous selector state
   return OZG_OK;
 }

@@ -74,6 +74,7 @@ def load():
     L.ozg_debug_zsplit.argtypes = [vp, ch, i64, i64, vp, i64, i32, vp, vp]
     L.ozg_set_profiling.argtypes = [vp, i32]
     L.ozg_set_check_samples.argtypes = [vp, i32]
+    L.ozg_set_exact_epilogue.argtypes = [vp, i32]
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
@@ -153,6 +154,9 @@ class Context:
         _check(load().ozg_sync(self._h), "ozg_sync")
 
     PHASES = ("split", "gemm", "native", "check", "select", "grouped")
+
+    def set_exact_epilogue(self, enable: bool):
+        _check(load().ozg_set_exact_epilogue(self._h, int(bool(enable))), "ozg_set_exact_epilogue")
 
     def set_check_samples(self, samples: int):
         _check(load().ozg_set_check_samples(self._h, int(samples)), "ozg_set_check_samples")

@@ -346,3 +346,49 @@ def test_sampled_check_beta_and_complex(ozg, ctx):
         assert 0 < rep.est_err <= full * (1 + 1e-9)
     finally:
         ctx.set_check_samples(0)
+
+
+# ----------------------------------------------------------------------------- exact epilogue
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
+@pytest.mark.parametrize("m,n,k,s", [(200, 300, 500, 7), (129, 257, 1100, 13), (64, 64, 64, 3), (5, 3, 2000, 10)])
+def test_dgemm_bit_exact_single_rounding(ozg, ctx, ta, tb, m, n, k, s):
+    """In the correctly rounded mode (s <= 13) the epilogue sums the group products exactly
+    (128-bit Horner) and rounds once: with alpha = 1, beta = 0 the result equals the oracle's
+    definition bit for bit; the default mode stays within its stated tolerance."""
+    A = wide((m, k) if ta == "N" else (k, m), 2.0, 7 * m + k)
+    B = wide((k, n) if tb == "N" else (n, k), 2.0, 5 * n + k)
+    C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    ctx.set_exact_epilogue(True)
+    try:
+        ctx.dgemm(ta, tb, m, n, k, 1.0, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], 0.0, C, m, s)
+        ctx.sync()
+    finally:
+        ctx.set_exact_epilogue(False)
+    assert np.array_equal(host(ozg, C, m, n), oracle.dgemm_emu(A, B, s, ta, tb))
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("C", "T")])
+def test_zgemm_bit_exact_single_rounding(ozg, ctx, ta, tb):
+    m, n, k, s = 70, 90, 300, 9
+    shA = (m, k) if ta == "N" else (k, m)
+    shB = (k, n) if tb == "N" else (n, k)
+    A = wide(shA, 1.0, 801) + 1j * wide(shA, 1.0, 802)
+    B = wide(shB, 1.0, 803) + 1j * wide(shB, 1.0, 804)
+    C = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    ctx.set_exact_epilogue(True)
+    try:
+        ctx.zgemm(ta, tb, m, n, k, 1.0, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], 0.0, C, m, s)
+        ctx.sync()
+    finally:
+        ctx.set_exact_epilogue(False)
+    assert np.array_equal(host(ozg, C, m, n), oracle.zgemm_emu(A, B, s, ta, tb))
+
+
+def test_dgemm_s_above_13_fp64_epilogue(ozg, ctx):
+    m, n, k = 100, 140, 300
+    A, B = wide((m, k), 3.0, 811), wide((k, n), 3.0, 812)
+    for s in (14, 18):
+        C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+        ctx.dgemm("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, C, m, s)
+        ctx.sync()
+        check_dgemm(host(ozg, C, m, n), A, B, s, "N", "N", 1.0, 0.0, None)
