@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grouped", action="store_true", help="skip the grouped-batch comparison")
     ap.add_argument("--grouped-count", type=int, default=2048)
+    ap.add_argument("--no-zgemm", action="store_true", help="skip the complex (KKR-like ZGEMM) section")
     return ap.parse_args()
 
 
@@ -264,6 +265,48 @@ def grouped_section(ozg, torch, count, steps):
     return out
 
 
+def zgemm_section(ozg, torch, steps):
+    """KKR-like complex128 ZGEMM, n = 113 x 32 = 3616 (stand-in for the MuST ZGEMMs of Sec. 3.2):
+    emulated at s = 4..10 (FP64-equivalent 8 n^3 flops) with the sampled double-double error
+    (|A||B|-relative, and the paper's per-part max_real / max_imag), and the native FP64 kernel."""
+    from paper_2503_22875_gb300 import workloads
+    A, B = workloads.kkr_like_pair(113, 32, seed=3)
+    n = A.shape[0]
+    dA, dB = ozg.to_device(A), ozg.to_device(B)
+    dC = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    st = torch.cuda.Stream()
+    ctx = ozg.Context(stream=st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flops = 8.0 * n ** 3
+    out = {"workload": f"KKR-like ZGEMM n={n} (113 blocks of 32), complex normal x exp(-|r_i - r_j|) + (1+0.1i) diag",
+           "by_slices": {}}
+    for s in range(4, 11):
+        with torch.cuda.stream(st):
+            ctx.set_check_samples(0)
+            ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(steps):
+                ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            ctx.set_check_samples(64)
+            rep = ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s, report=True)
+        out["by_slices"][s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "err_sampled_dd": rep.est_err,
+                               "max_real": rep.max_real, "max_imag": rep.max_imag}
+    ok = [s for s, v in out["by_slices"].items() if v["err_sampled_dd"] <= TARGET_ERR]
+    out["smallest_s_meeting_target"] = min(ok) if ok else None
+    with torch.cuda.stream(st):
+        e0.record(st)
+        ctx.native_zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n)
+        e1.record(st)
+        e1.synchronize()
+    out["native_fp64_tflops"] = flops / (e0.elapsed_time(e1) / 1e3) / 1e12
+    ctx.close()
+    return out
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import numpy as np
@@ -377,6 +420,9 @@ def run_gpu(args):
     tn1.synchronize()
     native_tflops = flops / (tn0.elapsed_time(tn1) / 1e3) / 1e12
 
+    zgemm = None
+    if not args.no_zgemm:
+        zgemm = zgemm_section(ozg, torch, max(1, min(args.steps, 3)))
     grouped = None
     if not args.no_grouped:
         grouped = grouped_section(ozg, torch, args.grouped_count, max(1, min(args.steps, 5)))
@@ -414,6 +460,7 @@ def run_gpu(args):
         "e2e": {"value": flops * world / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n},
         "grouped_batch": grouped,
+        "zgemm_kkr": zgemm,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

@@ -66,6 +66,9 @@ typedef struct ozg_report {
   int selected;           /* slice count the learned selector chose (0: the count was fixed) */
   int repaired;           /* 1: the check rejected the selected count and the call was re-run at
                              the fallback count (slices_used then holds the fallback) */
+  double max_real;        /* complex calls: max over the samples of |Re C - Re C_dd| / |Re C_dd| and */
+  double max_imag;        /* the same for Im: the per-part relative error of the paper's MuST study
+                             (Sec. 3.2); NaN for real calls or when not checked */
 } ozg_report;
 
 /* Create a context on the current CUDA device.  workspace_bytes pre-reserves device
@@ -205,12 +208,23 @@ int ozg_set_graphs(ozg_ctx* ctx, int enable);
 /* Slice count used for calls that request 0 (default 7). */
 int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
 
-/* Tile-shape autotuner: enable != 0 times both tile widths (128 x 256 and 128 x 128 output
- * tiles) the first time a shape bucket (rounded log2 of m, n, k and the slice count) or a grouped
- * batch is seen, keeps the faster, and appends single-call choices to cache_path (may be NULL)
- * as "bucket variant" lines that later contexts read back.  Tuning runs only for calls with
- * beta == 0, where both widths give bit-identical C; other calls use the padding heuristic. */
+/* Tile variants of the slice-product kernel.  Bit 0 picks the output tile (0: 128 x 256,
+ * 1: 128 x 128); bit 1 spreads each intermediate epilogue accumulation over the next chains'
+ * drains instead of running it at once (pays for long k, costs for short k).  All four variants
+ * give bit-identical C. */
+#define OZG_NUM_TILE_VARIANTS 4
+
+/* Tile-variant autotuner: enable != 0 times the four variants the first time a shape bucket
+ * (rounded log2 of m, n, k and the slice count) or a grouped batch is seen, keeps the fastest,
+ * and appends single-call choices to cache_path (may be NULL) as "bucket variant" lines that
+ * later contexts read back.  Tuning runs only for calls with beta == 0 (C is then write-only);
+ * other calls use the heuristic: the width that pads least, deferral when k >= 2048 (for a
+ * grouped batch: when the mean k weighted by m n s^2 is >= 2048). */
 int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
+
+/* Force tile variant 0..3 for every later call (single and grouped), or -1 (default) for the
+ * autotuned / heuristic choice.  Returns OZG_ERR_INVALID for other values. */
+int ozg_set_tile_variant(ozg_ctx* ctx, int variant);
 
 /* ---- inspection entry points (used by the parity tests; same kernels as the GEMM path) ---- */
 

@@ -55,7 +55,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     const int BN = ozg::slice_gemm_tile_n_of(variant);
     const int64_t tiles = ((prA + BM - 1) / BM) * ((prB + BN - 1) / BN);
     return (int)(tiles < c->num_sms ? tiles : c->num_sms);
-  };
+  };  // depends on the tile width (bit 0) only
   const int grid = grid_of(0) > grid_of(1) ? grid_of(0) : grid_of(1);  // R scratch for either width
   Carve cv;
   size_t oDA = cv.take((size_t)s * prA * Kp * 2), oDB = cv.take((size_t)s * prB * Kp * 2);
@@ -124,6 +124,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   OZG_CUDA(ozg::make_digit_tmap(&tmA, sa.D, k, prA, Kp, s, BM));
   OZG_CUDA(ozg::make_digit_tmap(&tmB[0], sb.D, k, prB, Kp, s, ozg::slice_gemm_tile_n_of(0)));
   OZG_CUDA(ozg::make_digit_tmap(&tmB[1], sb.D, k, prB, Kp, s, ozg::slice_gemm_tile_n_of(1)));
+  // tmB[v & 1] serves variant v
   int variant = choose_variant(c, prA, prB, k, s);
   ozg::GemmArgs ga;
   ga.rows = prA;
@@ -147,22 +148,25 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   ga.status = c->dflags;
   ga.nonfinite = Gdbg ? nullptr : nonfinite;
   ga.variant = variant;
+  ga.defer = (variant >> 1) & 1;
   ga.grid = grid_of(variant);
   ga.s_dev = autos ? s_dev : nullptr;
   ga.exact = c->exact;
-  if (c->autotune && !Gdbg && ga.beta_zero && !autos) {
+  if (c->autotune && c->force_variant < 0 && !Gdbg && ga.beta_zero && !autos) {
     const uint64_t bucket = shape_bucket(prA, prB, k, s);
     if (c->tune.find(bucket) == c->tune.end()) {
-      // time both widths on this call (C is write-only here and both give the same bits)
+      // time the four variants (two widths x deferred pushes) on this call (C is write-only
+      // here and every variant gives the same bits)
       float best = 1e30f;
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < 4; ++v) {
         ozg::GemmArgs gt = ga;
         gt.variant = v;
+        gt.defer = (v >> 1) & 1;
         gt.grid = grid_of(v);
         cudaEvent_t e0 = pool_get(c), e1 = pool_get(c);
         if (!e0 || !e1) return OZG_ERR_CUDA;
         OZG_CUDA(cudaEventRecord(e0, st));
-        cudaError_t le = ozg::launch_slice_gemm(tmA, tmB[v], gt, st);
+        cudaError_t le = ozg::launch_slice_gemm(tmA, tmB[v & 1], gt, st);
         OZG_CUDA(cudaEventRecord(e1, st));
         float ms = 1e30f;
         if (le == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
@@ -176,6 +180,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
       }
       tune_store(c, bucket, variant);
       ga.variant = variant;
+      ga.defer = (variant >> 1) & 1;
       ga.grid = grid_of(variant);
     }
   }
@@ -205,13 +210,14 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     ck.seed = c->check_seed++;
     ck.cold = at<double>(c, oCold);
     ck.err_out = c->dcheck;
+    ck.part_err = cplx ? c->dcheck + 1 : nullptr;
     ck.gate = nonfinite;
     PhaseScope ps(c, OZG_PHASE_CHECK);
     OZG_CUDA(ozg::launch_check_pre(ck, st));
   }
   {
     PhaseScope ps(c, OZG_PHASE_GEMM);
-    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB[ga.variant], ga, st));
+    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB[ga.variant & 1], ga, st));
   }
   if (Gdbg) return OZG_OK;
 
@@ -250,17 +256,19 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     g2.s = s_rep;
     g2.s_dev = nullptr;
     g2.nonfinite = s_dev + 1;  // the kernel exits unless the repair is needed
-    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB[g2.variant], g2, st));
+    OZG_CUDA(ozg::launch_slice_gemm(tmA, tmB[g2.variant & 1], g2, st));
     ozg::CheckArgs ck2 = ck;
     ck2.err_out = at<double>(c, oErr2);
+    ck2.part_err = nullptr;
     ck2.gate = s_dev + 1;
     OZG_CUDA(ozg::launch_check_post(ck2, st));
   }
   if (rep) {
     int h = 0, sd[2] = {s, 1};
-    double err = 0.0, err2 = 0.0;
+    double err = 0.0, err2 = 0.0, parts[2] = {NAN, NAN};
     OZG_CUDA(cudaMemcpyAsync(&h, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (nsamp > 0) OZG_CUDA(cudaMemcpyAsync(&err, c->dcheck, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (nsamp > 0 && cplx) OZG_CUDA(cudaMemcpyAsync(parts, c->dcheck + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (autos) {
       OZG_CUDA(cudaMemcpyAsync(sd, s_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
       OZG_CUDA(cudaMemcpyAsync(&err2, at<double>(c, oErr2), sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -270,6 +278,8 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     rep->slices_used = h ? -1 : (autos ? (sd[1] ? sd[0] : s_rep) : s);
     rep->samples = (nsamp > 0 && !h) ? nsamp : 0;
     rep->est_err = rep->samples ? ((autos && !sd[1]) ? err2 : err) : NAN;
+    rep->max_real = (rep->samples && cplx && !(autos && !sd[1])) ? parts[0] : NAN;
+    rep->max_imag = (rep->samples && cplx && !(autos && !sd[1])) ? parts[1] : NAN;
     rep->selected = autos ? sd[0] : 0;
     rep->repaired = (autos && !h && !sd[1]) ? 1 : 0;
   }
@@ -288,6 +298,8 @@ int gemm_entry(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, in
     std::memset(rep, 0, sizeof(*rep));
     rep->slices_used = native ? -1 : slices;
     rep->est_err = NAN;
+    rep->max_real = NAN;
+    rep->max_imag = NAN;
   }
   if (m == 0 || n == 0) return OZG_OK;
   const bool alpha_zero = alpha[0] == 0.0 && (!cplx || alpha[1] == 0.0);
@@ -338,7 +350,7 @@ int ozg_create(ozg_ctx** out, size_t workspace_bytes) {
   OZG_CUDA(cudaGetDevice(&c->device));
   OZG_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   OZG_CUDA(ozg::prepare_kernels());
-  if (cudaMalloc(&c->dcheck, sizeof(double)) != cudaSuccess) {
+  if (cudaMalloc(&c->dcheck, 4 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return OZG_ERR_ALLOC;

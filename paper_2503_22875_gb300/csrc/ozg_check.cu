@@ -3,7 +3,10 @@
 // arithmetic of Sec. 2.2: TwoProd by fma, TwoSum) and returns
 //   max |C_ij - ref_ij| / (|alpha| (|A||B|)_ij + |beta| |C_old,ij|)
 // -- the componentwise error relative to |A||B|.  One warp per sample; lanes split k.
-// For complex data the four real sub-sums are tracked and both parts are checked.
+// For complex data the four real sub-sums are tracked and both parts are checked; optionally the
+// per-part errors relative to the parts themselves are reported as well, the max_real / max_imag
+// accuracy measure of the paper's MuST study (Sec. 3.2, relative error of the real and of the
+// imaginary part, maximised over the sampled entries).
 #include "ozg_internal.h"
 
 namespace ozg {
@@ -132,7 +135,14 @@ __device__ void check_one(const CheckArgs& P, int sample, int lane, double* err_
       ri = dd_add_prod(ri, P.beta[1], cr_old);
     }
     const double* cp = P.C + 2 * (i + j * P.ldc);
-    const double d = fmax(fabs((cp[0] - rr.hi) - rr.lo), fabs((cp[1] - ri.hi) - ri.lo));
+    const double dre = fabs((cp[0] - rr.hi) - rr.lo), dim = fabs((cp[1] - ri.hi) - ri.lo);
+    const double d = fmax(dre, dim);
+    if (P.part_err != nullptr) {  // per-part error relative to the part itself (max_real / max_imag)
+      const double pr = rr.hi != 0.0 ? dre / fabs(rr.hi) : (dre > 0 ? INFINITY : 0.0);
+      const double pi = ri.hi != 0.0 ? dim / fabs(ri.hi) : (dim > 0 ? INFINITY : 0.0);
+      atomicMax(reinterpret_cast<unsigned long long*>(P.part_err), (unsigned long long)__double_as_longlong(pr));
+      atomicMax(reinterpret_cast<unsigned long long*>(P.part_err + 1), (unsigned long long)__double_as_longlong(pi));
+    }
     const double scale = (fabs(P.alpha[0]) + fabs(P.alpha[1])) * sabs +
                          (fabs(P.beta[0]) + fabs(P.beta[1])) * (fabs(cr_old) + fabs(ci_old));
     err = scale > 0 ? d / scale : (d > 0 ? INFINITY : 0.0);
@@ -198,6 +208,7 @@ cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, in
 cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st) {
   if (a.nsamp <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.err_out, 0, sizeof(double), st);
+  if (e == cudaSuccess && a.part_err != nullptr) e = cudaMemsetAsync(a.part_err, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int warps_per_block = 4;
   check_post<<<(a.nsamp + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(a);

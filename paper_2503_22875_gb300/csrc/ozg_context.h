@@ -51,6 +51,7 @@ struct ozg_ctx {
   int exact = 0;  // correctly rounded (exact-sum) epilogue for single calls
   // autotuner: shape bucket -> tile variant, optionally persisted as text
   int autotune = 0;
+  int force_variant = -1;  // >= 0: every call uses this tile variant
   std::string tune_path;
   std::unordered_map<uint64_t, int> tune;
   bool tune_loaded = false;
@@ -108,7 +109,8 @@ T* gat(ozg_ctx* c, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(c->gws) + off);
 }
 
-// tile variant for one GEMM shape: the autotuned choice if known, else the padding heuristic
+// tile variant for one GEMM shape (bit 0: BN = 128, bit 1: deferred pushes): the autotuned
+// choice if known, else the heuristic (least padding; deferral for k >= 2048)
 int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s);
 uint64_t shape_bucket(int64_t rows, int64_t cols, int64_t k, int s);
 void tune_store(ozg_ctx* c, uint64_t bucket, int variant);

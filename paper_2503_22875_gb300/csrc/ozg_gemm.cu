@@ -218,6 +218,29 @@ __device__ __forceinline__ double horner_step(void* Rp, int g, bool exact, bool 
   return 0.0;
 }
 
+// FP64 Horner step for columns [c0, c1) of a thread's group sums (non-final pushes).  Complex:
+// columns come in (Re, Im) pairs combined exactly across the lane pair before the step.
+__device__ __forceinline__ void push_fp64_range(const int* Gs, double* Rt, int c0, int c1, bool first, bool group2,
+                                                bool cplx, bool odd) {
+  if (!cplx) {
+#pragma unroll 4
+    for (int c = c0; c < c1; ++c) {
+      const double gv = (double)Gs[c];
+      double* Rp = Rt + (size_t)c * 128;
+      *Rp = first ? (group2 ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+    }
+  } else {
+#pragma unroll 2
+    for (int c = c0 / 2; c < c1 / 2; ++c) {
+      const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * c + 1], 1);
+      const int comb = odd ? (Gs[2 * c] + other) : (Gs[2 * c] - other);
+      const double gv = (double)comb;
+      double* Rp = Rt + (size_t)c * 128;
+      *Rp = first ? (group2 ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+    }
+  }
+}
+
 // Bounded wait used during teardown after an abort (ignores the abort flag).
 __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
   long long t0 = clock64();
@@ -373,6 +396,14 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     int buf = 0;
     double* Rbase = Rws + (size_t)blockIdx.x * BM * BN * 2;  // room for 16 bytes per output
     const bool exact_mode = GROUPED ? false : (P->exact != 0);
+    const bool defer_ok = GROUPED ? (G->defer != 0) : (P->defer != 0);
+    // An intermediate FP64 push is spread over the drains that precede the next push, so that
+    // it overlaps the MMA warp's next chains instead of stalling them (the MMA runs at most one
+    // chain ahead of the drains).  Final pushes, exact-mode and inspection pushes run at once.
+    int Gs[CPT];
+    int pend_c = CPT, pend_chunk = CPT;
+    bool pend_first = false, pend_g2 = false;
+    double* pend_Rt = nullptr;
     const bool odd = (lane & 1) != 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
@@ -410,17 +441,38 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           acc_par ^= 1u << buf;
           buf ^= 1;
           const bool group_end = (seg == nseg - 1);
-          if (!(group_end || ((seg + 1) % push_segs) == 0)) continue;
+          const bool push_now = group_end || ((seg + 1) % push_segs) == 0;
+          if (pend_c < CPT) {  // advance the pending push; complete it before the next one
+            const int c1 = push_now ? CPT : min(CPT, pend_c + pend_chunk);
+            push_fp64_range(Gs, pend_Rt, pend_c, c1, pend_first, pend_g2, j.cplx != 0, odd);
+            pend_c = c1;
+          }
+          if (!push_now) continue;
           const bool final_push = group_end && g == s + 1;
           // ---- push the group sums into R (or, for inspection, export them) ----
           // Pushes happen once per group (per 64 chains at most): the sums move to a
           // thread-local array indexed at run time, so the FP64 work below runs in a rolled
           // loop with few live registers while Gr stays in registers for the drains above.
-          int Gs[CPT];
 #pragma unroll
           for (int c = 0; c < CPT; ++c) {
             Gs[c] = Gr[c];
             Gr[c] = 0;
+          }
+          const bool exact_now = exact_mode && s <= kExactMaxS;
+          if (!final_push && !exact_now && Gdbg == nullptr) {
+            // drains before the next push: the rest of this group, or the next group's chains
+            const int left = group_end ? nseg_of(g + 1, j.KB) : nseg - (seg + 1);
+            const int drains = min(left, push_segs);
+            if (defer_ok && drains >= 2) {
+              pend_c = 0;
+              pend_chunk = (CPT + drains - 2) / (drains - 1);
+              pend_chunk = (pend_chunk + 1) & ~1;  // whole (Re, Im) column pairs
+              pend_first = first_push;
+              pend_g2 = (g == 2);
+              pend_Rt = Rbase + (size_t)((j.cplx ? chalf * CPT / 2 : chalf * CPT)) * BM + r;
+              first_push = false;
+              continue;
+            }
           }
           if (Gdbg != nullptr) {
 #pragma unroll 1
@@ -428,7 +480,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
               const int64_t gc = gcol0 + c;
               if (row_ok && gc < j.cols) Gdbg[((int64_t)(g - 2) * j.rows + grow) * j.cols + gc] = Gs[c];
             }
-          } else if (exact_mode && s <= kExactMaxS) {
+          } else if (exact_now) {
             // correctly rounded mode: exact 128-bit Horner sum, one rounding at the end
             char* Rt = reinterpret_cast<char*>(Rbase) + ((size_t)(j.cplx ? chalf * CPT / 2 : chalf * CPT) * BM + r) * 16;
             const int ebase = e_row - 7 * (s + 1);
@@ -585,7 +637,7 @@ cudaError_t set_smem_once(Kern k, size_t bytes, bool& done) {
 
 int slice_gemm_tile_m() { return BM; }
 int slice_gemm_tile_n() { return 256; }
-int slice_gemm_tile_n_of(int variant) { return variant == 1 ? 128 : 256; }
+int slice_gemm_tile_n_of(int variant) { return (variant & 1) ? 128 : 256; }
 size_t slice_gemm_smem_bytes() { return Cfg<256>::SMEM; }
 
 cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
@@ -614,7 +666,7 @@ cudaError_t prepare_kernels() {
 cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& a, cudaStream_t st) {
   if (a.grid <= 0) return cudaSuccess;
   cudaError_t e;
-  if (a.variant == 1) {
+  if (a.variant & 1) {
     static bool done = false;
     if ((e = set_smem_once(slice_gemm_kernel<128>, Cfg<128>::SMEM, done)) != cudaSuccess) return e;
     slice_gemm_kernel<128><<<a.grid, THREADS, Cfg<128>::SMEM, st>>>(tmA, tmB, a);
@@ -629,7 +681,7 @@ cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, co
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st) {
   if (grid <= 0 || g.ntiles <= 0) return cudaSuccess;
   cudaError_t e;
-  if (variant == 1) {
+  if (variant & 1) {
     static bool done = false;
     if ((e = set_smem_once(slice_gemm_grouped_kernel<128>, Cfg<128>::SMEM, done)) != cudaSuccess) return e;
     slice_gemm_grouped_kernel<128><<<grid, THREADS, Cfg<128>::SMEM, st>>>(g);

@@ -58,7 +58,7 @@ std::vector<GroupTile> balanced_tiles(const ozg_gemm_desc* d, const std::vector<
     double cost;
     GroupTile t;
   };
-  const int BN = tile_n_of(variant);
+  const int BN = tile_n_of(variant & 1);
   std::vector<T> all;
   for (int64_t c = 0; c < count; ++c) {
     const int64_t tm = (d[c].m + 127) / 128, tn = (d[c].n + BN - 1) / BN, kb = (d[c].k + 63) / 64;
@@ -106,6 +106,7 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   g.calls = gat<GroupCall>(c, P.oCalls);
   g.status = c->dflags;
   g.Rws = gat<double>(c, P.oR);
+  g.defer = (P.variant >> 1) & 1;
   OZG_CUDA(launch_slice_gemm_grouped(g, P.variant, P.grid, st));
   OZG_CUDA(launch_native_batched(gat<NativeArgs>(c, P.oNative), P.ncalls, gat<const int*>(c, P.oFlagPtrs),
                                  gat<int>(c, P.oNList), gat<int64_t>(c, P.oNPre), gat<int64_t>(c, P.oNTot),
@@ -414,6 +415,8 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
       reps[i].status = rc;
       reps[i].slices_used = s[i];
       reps[i].est_err = NAN;
+      reps[i].max_real = NAN;
+      reps[i].max_imag = NAN;
     }
     if (rc) bad = true;
   }
@@ -455,23 +458,29 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
   PhaseScope ps(c, OZG_PHASE_GROUPED);
   if (!reuse) {
     c->plan.reset();
-    // tile width: autotuned per batch when every call writes C without reading it (both widths
-    // give bit-identical results), else the padding heuristic summed over the batch
+    // tile variant (width, deferred pushes): autotuned per batch when every call writes C without
+    // reading it (all variants give bit-identical results), else the padding heuristic summed
+    // over the batch, with deferred pushes when the work-weighted mean k is long
     int variant;
-    double pad0 = 0, pad1 = 0;
+    double pad0 = 0, pad1 = 0, wk = 0, w = 0;
     bool all_beta_zero = true;
     for (int64_t i = 0; i < n; ++i) {
       pad0 += (double)((work[i].m + 127) / 128) * ((work[i].n + 255) / 256) * 256 * ws[i] * ws[i];
       pad1 += (double)((work[i].m + 127) / 128) * ((work[i].n + 127) / 128) * 128 * ws[i] * ws[i];
+      const double wi = (double)work[i].m * work[i].n * ws[i] * ws[i];
+      wk += wi * work[i].k;
+      w += wi;
       all_beta_zero = all_beta_zero && work[i].beta == 0.0;
     }
-    variant = pad1 < pad0 ? 1 : 0;
+    variant = (pad1 < pad0 ? 1 : 0) | (w > 0 && wk >= 2048.0 * w ? 2 : 0);
     auto tuned = c->tune.find(key);
-    if (tuned != c->tune.end()) {
+    if (c->force_variant >= 0) {
+      variant = c->force_variant;
+    } else if (tuned != c->tune.end()) {
       variant = tuned->second;
     } else if (c->autotune && all_beta_zero) {
       float best = 1e30f;
-      for (int v = 0; v < 2; ++v) {
+      for (int v = 0; v < 4; ++v) {
         std::unique_ptr<GroupPlan, PlanDeleter> T(new GroupPlan());
         int rc = build_plan(c, n, work.data(), ws, wa, wb, wauto, v, T.get());
         if (rc) return rc;
@@ -561,6 +570,13 @@ extern "C" int ozg_set_fallback_slices(ozg_ctx* c, int s) {
   if (!c) return OZG_ERR_INVALID;
   if (s < 1 || s > OZG_MAX_SLICES) return -2;
   c->fallback_slices = s;
+  return OZG_OK;
+}
+
+extern "C" int ozg_set_tile_variant(ozg_ctx* c, int variant) {
+  if (!c || variant < -1 || variant >= OZG_NUM_TILE_VARIANTS) return OZG_ERR_INVALID;
+  c->force_variant = variant;
+  c->plan.reset();  // a cached grouped plan may hold another variant
   return OZG_OK;
 }
 

@@ -103,7 +103,7 @@ static void tune_load(ozg_ctx* c) {
   while (std::getline(in, line)) {
     unsigned long long b = 0;
     int v = 0;
-    if (std::sscanf(line.c_str(), "%llx %d", &b, &v) == 2 && (v == 0 || v == 1)) c->tune[b] = v;
+    if (std::sscanf(line.c_str(), "%llx %d", &b, &v) == 2 && v >= 0 && v <= 3) c->tune[b] = v;
   }
 }
 
@@ -114,18 +114,21 @@ void tune_store(ozg_ctx* c, uint64_t bucket, int variant) {
   out << std::hex << bucket << std::dec << " " << variant << "\n";
 }
 
-// Padding heuristic: the tile width that wastes the least output area (ties -> BN = 256).
-static int padding_choice(int64_t rows, int64_t cols) {
+// Heuristic variant: the tile width that wastes the least output area (ties -> BN = 256), and
+// deferred epilogue pushes for long k (their pushes then overlap the next chains' MMAs; for
+// short k the epilogue is the bottleneck and immediate pushes measured faster).
+static int heuristic_variant(int64_t rows, int64_t cols, int64_t k) {
   (void)rows;
   const int64_t p256 = (cols + 255) / 256 * 256, p128 = (cols + 127) / 128 * 128;
-  return p128 < p256 ? 1 : 0;
+  return (p128 < p256 ? 1 : 0) | (k >= 2048 ? 2 : 0);
 }
 
 int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s) {
+  if (c->force_variant >= 0) return c->force_variant;
   tune_load(c);
   auto it = c->tune.find(shape_bucket(rows, cols, k, s));
   if (it != c->tune.end()) return it->second;
-  return padding_choice(rows, cols);
+  return heuristic_variant(rows, cols, k);
 }
 
 }  // namespace host

@@ -51,7 +51,8 @@ struct GemmArgs {
   int* status = nullptr;        // device status word (0 ok, 3 timeout)
   const int* nonfinite = nullptr;  // if non-null and set, the kernel exits (native path takes over)
   int grid = 0;                 // CTAs to launch (<= tiles); Rws must hold grid tiles
-  int variant = 0;              // tile width: 0 -> BN = 256, 1 -> BN = 128
+  int variant = 0;              // bit 0: tile width (0 -> BN = 256, 1 -> BN = 128); bit 1: defer
+  int defer = 0;                // 1: spread intermediate epilogue pushes over the next drains
   const int* s_dev = nullptr;   // if set, the slice count is read here (device-chosen); s = plane count
   int exact = 0;                // 1: exact 128-bit Horner sum and one rounding (s <= 13)
 };
@@ -78,6 +79,7 @@ struct GroupArgs {
   const GroupCall* calls = nullptr;
   int* status = nullptr;
   double* Rws = nullptr;
+  int defer = 0;  // as GemmArgs::defer
 };
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st);
 // set the kernels' dynamic shared-memory limits (once per process, before any stream capture)
@@ -126,6 +128,7 @@ struct CheckArgs {
   double* cold = nullptr;     // [nsamp][2] C_old at the samples (beta != 0)
   double* err_out = nullptr;  // max error (device double), reset by launch_check_post
   const int* gate = nullptr;  // skip when *gate != 0 (call routed to native FP64)
+  double* part_err = nullptr;  // complex: [2] max relative error of the real / imaginary parts
 };
 cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st);
 cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st);

@@ -42,7 +42,7 @@ class GemmDesc(ctypes.Structure):
 class Report(ctypes.Structure):
     _fields_ = [("slices_used", ctypes.c_int), ("nonfinite", ctypes.c_int), ("status", ctypes.c_int),
                 ("samples", ctypes.c_int), ("est_err", ctypes.c_double), ("selected", ctypes.c_int),
-                ("repaired", ctypes.c_int)]
+                ("repaired", ctypes.c_int), ("max_real", ctypes.c_double), ("max_imag", ctypes.c_double)]
 
 
 def lib_path() -> str:
@@ -88,6 +88,7 @@ def load():
     L.ozg_set_graphs.argtypes = [vp, i32]
     L.ozg_set_fallback_slices.argtypes = [vp, i32]
     L.ozg_set_autotune.argtypes = [vp, i32, ctypes.c_char_p]
+    L.ozg_set_tile_variant.argtypes = [vp, i32]
     L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
     _lib = L
     return L
@@ -212,6 +213,11 @@ class Context:
     def set_autotune(self, enable: bool, cache_path: str | None = None):
         _check(load().ozg_set_autotune(self._h, int(bool(enable)), cache_path.encode() if cache_path else None),
                "ozg_set_autotune")
+
+    def set_tile_variant(self, variant: int):
+        """Force tile variant 0..3 (bit 0: 128-wide tiles, bit 1: deferred epilogue pushes), or -1
+        for the autotuned / heuristic choice."""
+        _check(load().ozg_set_tile_variant(self._h, int(variant)), "ozg_set_tile_variant")
 
     # ---- learned slice selector
     def load_selector(self, path: str):

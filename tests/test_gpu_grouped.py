@@ -1,5 +1,6 @@
 """Grouped emulated DGEMM (one persistent launch over many uneven GEMMs, CUDA-graph replay,
-tile-width autotuner) against the oracle, call by call."""
+tile-variant autotuner) against the oracle, call by call; the four tile variants agree bit for
+bit."""
 import numpy as np
 import pytest
 
@@ -141,4 +142,41 @@ def test_single_call_autotune_cache_and_bits(ozg, tmp_path):
         ctx.close()
     assert torch.equal(res[0], res[1]) and torch.equal(res[1], res[2])
     lines = path.read_text().split()
-    assert len(lines) == 2 and lines[1] in ("0", "1")  # one bucket tuned once, then read back
+    assert len(lines) == 2 and lines[1] in ("0", "1", "2", "3")  # one bucket tuned once, then read back
+
+
+def test_tile_variants_bit_identical(ozg):
+    """The four tile variants (128 x 256 / 128 x 128 tiles, immediate / deferred epilogue pushes)
+    give the same bits: single real and complex calls with beta != 0, and a grouped batch."""
+    m, n, k, s = 200, 300, 2100, 8   # ragged tiles, several k-segments per pair
+    A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=340)
+    C0 = np.asfortranarray(workloads.rng(341).uniform(-1, 1, (m, n)))
+    Z = workloads.kkr_like_pair(nblk=5, bs=32, seed=342)
+    mz, nz, kz = 150, 97, 160
+    Az, Bz = np.asfortranarray(Z[0][:mz, :kz]), np.asfortranarray(Z[1][:kz, :nz])
+    Z0 = np.asfortranarray(workloads.rng(343).normal(size=(mz, nz)) + 1j * workloads.rng(344).normal(size=(mz, nz)))
+    batch = make_batch(ozg, 12, seed=345)
+    dA, dB, dAz, dBz = (ozg.to_device(x) for x in (A, B, Az, Bz))
+    res = []
+    for v in range(4):
+        ctx = ozg.Context()
+        ctx.set_tile_variant(v)
+        dC, dZ = ozg.to_device(C0), ozg.to_device(Z0)
+        ctx.dgemm("N", "N", m, n, k, -0.5, dA, m, dB, k, 0.75, dC, m, s)
+        ctx.zgemm("N", "N", mz, nz, kz, 0.5 - 2j, dAz, mz, dBz, kz, 1.5 + 0.25j, dZ, mz, 6)
+        for b in batch:
+            b["dC"].copy_(ozg.to_device(b["C0"]))
+        torch.cuda.synchronize()
+        ctx.dgemm_grouped(calls_of(batch), [b["s"] for b in batch])
+        ctx.sync()
+        res.append([dC.clone(), dZ.clone()] + [b["dC"].clone() for b in batch])
+        ctx.close()
+    for r in res[1:]:
+        assert all(torch.equal(x, y) for x, y in zip(res[0], r))
+    check_batch(ozg, batch)
+    E = oracle.dgemm_emu(A, B, s, "N", "N", -0.5, 0.75, C0)
+    AB = oracle.abs_product(A, B, "N", "N")
+    C = ozg.from_device(res[0][0], m, n)
+    assert (np.abs(C - E) <= 4 * (s + 2) * U * 0.5 * AB + 2 * U * np.abs(E) + 2 * U * 0.75 * np.abs(C0)).all()
+    with pytest.raises(ozg.OzgError):
+        ozg.Context().set_tile_variant(4)

@@ -392,3 +392,24 @@ def test_dgemm_s_above_13_fp64_epilogue(ozg, ctx):
         ctx.dgemm("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, C, m, s)
         ctx.sync()
         check_dgemm(host(ozg, C, m, n), A, B, s, "N", "N", 1.0, 0.0, None)
+
+
+def test_check_reports_paper_part_errors_for_complex(ozg, ctx):
+    """max_real / max_imag: per-part error relative to the part (the MuST study's measure), never
+    above the maximum over all entries computed by the oracle."""
+    m, n, k, s = 60, 50, 200, 5
+    A = wide((m, k), 1.0, 901) + 1j * wide((m, k), 1.0, 902)
+    B = wide((k, n), 1.0, 903) + 1j * wide((k, n), 1.0, 904)
+    dC = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    ctx.set_check_samples(128)
+    try:
+        rep = ctx.zgemm("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, dC, m, s, report=True)
+    finally:
+        ctx.set_check_samples(0)
+    C = host(ozg, dC, m, n)
+    rh, rl, ih, il = oracle.zgemm_dd(A, B)
+    full_re = np.max(np.abs(C.real - rh - rl) / np.abs(rh))
+    full_im = np.max(np.abs(C.imag - ih - il) / np.abs(ih))
+    assert 0 < rep.max_real <= full_re * (1 + 1e-9)
+    assert 0 < rep.max_imag <= full_im * (1 + 1e-9)
+    assert rep.max_real >= full_re / 1e4 and rep.max_imag >= full_im / 1e4
