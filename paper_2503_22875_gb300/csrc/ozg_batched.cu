@@ -7,15 +7,13 @@
 //   * native: FP64 GEMM (real) for the calls whose inputs held Inf/NaN, on a device-compacted list;
 //   * check: the sampled double-double error of every call (one warp per sample).
 #include "ozg_internal.h"
+#include "ozg_split_dev.cuh"
 
 namespace ozg {
 namespace {
 
-constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
-constexpr uint64_t kInfBits = 0x7FF0000000000000ull;
-
+// largest j with prefix[j] <= unit (prefix[0] = 0, prefix[njobs] = total)
 __device__ __forceinline__ int find_job(const int64_t* prefix, int njobs, int64_t unit) {
-  // largest j with prefix[j] <= unit (prefix[0] = 0, prefix[njobs] = total)
   int lo = 0, hi = njobs - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -25,34 +23,6 @@ __device__ __forceinline__ int find_job(const int64_t* prefix, int njobs, int64_
       hi = mid - 1;
   }
   return lo;
-}
-
-__device__ __forceinline__ int exponent_from_maxbits(unsigned long long mb) {
-  if (mb == 0) return 0;
-  int eb = (int)(mb >> 52);
-  if (eb) return eb - 1022;
-  return (64 - __clzll((long long)mb)) - 1074;
-}
-
-__device__ __forceinline__ unsigned __int128 fixed_point(uint64_t b, int e, int s7) {
-  int eb = (int)((b >> 52) & 0x7FF);
-  uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-  int ex;
-  if (eb == 0) {
-    ex = -1074;
-  } else {
-    mant |= 1ull << 52;
-    ex = eb - 1075;
-  }
-  int sh = ex - e + s7;
-  if (sh >= 0) return sh < 128 ? ((unsigned __int128)mant << sh) : (unsigned __int128)0;
-  if (sh > -64) return (unsigned __int128)(mant >> (-sh));
-  return 0;
-}
-
-__device__ __forceinline__ uint16_t digit_half_bits(unsigned __int128 F, int shift, bool neg) {
-  int d = (int)((uint32_t)(F >> shift) & 127u);
-  return __half_as_ushort(__int2half_rn(neg ? -d : d));
 }
 
 // element (i, l) of the job's op(X) as raw bits; complex gives (re, im) with conjugation applied
@@ -69,115 +39,111 @@ __device__ __forceinline__ void load_elem(const SplitArgs& J, int64_t i, int64_t
   }
 }
 
-// Units: strided jobs -> 256 rows per unit (thread per row); contiguous -> 8 rows (warp per row).
-__global__ void __launch_bounds__(256) rowmax_batched(const SplitArgs* jobs, const int64_t* prefix, int njobs) {
-  const int64_t unit = blockIdx.x;
-  const int jb = find_job(prefix, njobs, unit);
-  const SplitArgs J = jobs[jb];
-  const int64_t u = unit - prefix[jb];
+// Row maxima.  A unit is 32 rows x 128 k of a strided job (lanes = consecutive rows, the eight
+// warps interleave along k, 16 loads in flight per thread) or 8 rows x 1024 k of a contiguous
+// job (a warp per row, lanes along k).  Partial maxima merge by atomicMax into the zeroed maxbits.
+__global__ void __launch_bounds__(256) rowmax_batched(const SplitArgs* jobs, const int2* units) {
+  const int2 ur = units[blockIdx.x];
+  const SplitArgs J = jobs[ur.x];
+  const int64_t u = ur.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long mx = 0;
   if (J.strided) {
-    const int64_t row = u * 256 + threadIdx.x;
-    if (row >= J.rows) return;
-    for (int64_t l = 0; l < J.k; ++l) {
-      uint64_t re, im;
-      load_elem(J, row, l, re, im);
-      re &= kAbsMask;
-      im &= kAbsMask;
-      re = re > im ? re : im;
-      mx = re > mx ? re : mx;
+    __shared__ unsigned long long red[8][32];
+    const int64_t kt = (J.k + kRmStridedK - 1) / kRmStridedK;
+    const int64_t row = (u / kt) * 32 + lane, l0 = (u % kt) * kRmStridedK + w;
+    if (row < J.rows) {
+#pragma unroll
+      for (int i = 0; i < kRmStridedK / 8; ++i) {
+        const int64_t l = l0 + 8 * i;
+        if (l < J.k) {
+          uint64_t re, im;
+          load_elem(J, row, l, re, im);
+          re &= kAbsMask;
+          im &= kAbsMask;
+          re = re > im ? re : im;
+          mx = re > mx ? re : mx;
+        }
+      }
     }
-    J.maxbits[row] = mx;
-    if (mx >= kInfBits) atomicExch(J.nonfinite, 1);
+    red[w][lane] = mx;
+    __syncthreads();
+    if (w == 0 && row < J.rows) {
+#pragma unroll
+      for (int i = 1; i < 8; ++i) mx = red[i][lane] > mx ? red[i][lane] : mx;
+      if (mx) {
+        atomicMax(&J.maxbits[row], mx);
+        if (mx >= kInfBits) atomicExch(J.nonfinite, 1);
+      }
+    }
   } else {
-    const int64_t row = u * 8 + threadIdx.x / 32;
-    const int lane = threadIdx.x & 31;
+    const int64_t kt = (J.k + kRmContigK - 1) / kRmContigK;
+    const int64_t row = (u / kt) * 8 + w, l0 = (u % kt) * kRmContigK + lane;
     if (row >= J.rows) return;
-    for (int64_t l = lane; l < J.k; l += 32) {
-      uint64_t re, im;
-      load_elem(J, row, l, re, im);
-      re &= kAbsMask;
-      im &= kAbsMask;
-      re = re > im ? re : im;
-      mx = re > mx ? re : mx;
+#pragma unroll 8
+    for (int i = 0; i < kRmContigK / 32; ++i) {
+      const int64_t l = l0 + 32 * i;
+      if (l < J.k) {
+        uint64_t re, im;
+        load_elem(J, row, l, re, im);
+        re &= kAbsMask;
+        im &= kAbsMask;
+        re = re > im ? re : im;
+        mx = re > mx ? re : mx;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       unsigned long long t = __shfl_xor_sync(0xffffffffu, mx, o);
       mx = t > mx ? t : mx;
     }
-    if (lane == 0) {
-      J.maxbits[row] = mx;
+    if (lane == 0 && mx) {
+      atomicMax(&J.maxbits[row], mx);
       if (mx >= kInfBits) atomicExch(J.nonfinite, 1);
     }
   }
 }
 
-// Units: 32 rows x 64 k tiles.  Thread t computes row t/8 and the 8 consecutive k at (t%8)*8.
-__global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, const int64_t* prefix, int njobs) {
-  __shared__ uint64_t tile[2][64][33];
-  const int64_t unit = blockIdx.x;
-  const int jb = find_job(prefix, njobs, unit);
-  const SplitArgs J = jobs[jb];
-  const int64_t u = unit - prefix[jb];
+// Digits (real jobs: the grouped GEMM is real).  A unit is 32 rows x 64 k.  Thread t computes
+// row t/8 and the 8 consecutive k at (t%8)*8; strided jobs are staged (transposed) through
+// shared memory so that the global loads stay coalesced.
+__global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, const int2* units) {
+  __shared__ uint64_t tile[64][33];
+  const int2 ur = units[blockIdx.x];
+  const SplitArgs J = jobs[ur.x];
+  const int64_t u = ur.y;
   const int64_t ltiles = (J.k + 63) / 64;
   const int64_t r0 = (u / ltiles) * 32, l0 = (u % ltiles) * 64;
   const int tid = threadIdx.x;
   const int r = tid / 8, lg = (tid % 8) * 8;
   const int64_t row = r0 + r;
-  uint64_t bre[8], bim[8];
+  const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
+  uint64_t b[8];
   if (J.strided) {
-    // stage through shared memory: consecutive threads read consecutive rows of one column
     const int rr = tid % 32;
+    const bool rok = r0 + rr < J.rows;
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int li = tid / 32 + 8 * q;
-      uint64_t re = 0, im = 0;
-      if (r0 + rr < J.rows && l0 + li < J.k) load_elem(J, r0 + rr, l0 + li, re, im);
-      tile[0][li][rr] = re;
-      tile[1][li][rr] = im;
+      tile[li][rr] = (rok && l0 + li < J.k) ? __ldg(X + (r0 + rr) + (l0 + li) * J.ld) : 0ull;
     }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      bre[q] = tile[0][lg + q][r];
-      bim[q] = tile[1][lg + q][r];
-    }
+    for (int q = 0; q < 8; ++q) b[q] = tile[lg + q][r];
   } else {
+    const bool rok = row < J.rows;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      bre[q] = 0;
-      bim[q] = 0;
-      if (row < J.rows && l0 + lg + q < J.k) load_elem(J, row, l0 + lg + q, bre[q], bim[q]);
-    }
+    for (int q = 0; q < 8; ++q) b[q] = (rok && l0 + lg + q < J.k) ? __ldg(X + row * J.ld + l0 + lg + q) : 0ull;
   }
   if (row >= J.rows || l0 + lg >= J.k) return;
   const int e = exponent_from_maxbits(J.maxbits[row]);
   if (l0 + lg == 0) J.exps[row] = e;
-  const int s7 = 7 * J.s;
-  const int parts = J.cplx ? 2 : 1;
-  for (int part = 0; part < parts; ++part) {
-    unsigned __int128 F[8];
-    bool neg[8];
+  DigitSrc ds[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const uint64_t b = part ? bim[q] : bre[q];
-      F[q] = fixed_point(b, e, s7);
-      neg[q] = (b >> 63) != 0;
-    }
-    const int64_t orow = J.cplx ? 2 * row + part : row;
-    for (int t = 1; t <= J.s; ++t) {
-      const int sh = 7 * (J.s - t);
-      uint16_t h[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) h[q] = digit_half_bits(F[q], sh, neg[q]);
-      uint4 out;
-      out.x = h[0] | ((uint32_t)h[1] << 16);
-      out.y = h[2] | ((uint32_t)h[3] << 16);
-      out.z = h[4] | ((uint32_t)h[5] << 16);
-      out.w = h[6] | ((uint32_t)h[7] << 16);
-      *reinterpret_cast<uint4*>(J.D + ((int64_t)(t - 1) * J.plane_rows + orow) * J.Kp + l0 + lg) = out;
-    }
-  }
+  for (int q = 0; q < 8; ++q) ds[q] = digit_src(b[q], e);
+  __half* out = J.D + row * J.Kp + l0 + lg;
+  const int64_t plane = J.plane_rows * J.Kp;
+  for (int t = 1; t <= J.s; ++t) *reinterpret_cast<uint4*>(out + (int64_t)(t - 1) * plane) = digits8(ds, t);
 }
 
 // ---------------------------------------------------------------------------- native fallback
@@ -286,13 +252,12 @@ cudaError_t launch_save_restore_batched(const RepairJob* jobs_dev, const int64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int64_t* rowmax_prefix_dev, int64_t rowmax_units,
-                                 const int64_t* digit_prefix_dev, int64_t digit_units, int njobs, cudaStream_t st) {
-  if (njobs <= 0) return cudaSuccess;
-  if (rowmax_units > 0) rowmax_batched<<<(unsigned)rowmax_units, 256, 0, st>>>(jobs_dev, rowmax_prefix_dev, njobs);
+cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t rowmax_units,
+                                 const int2* digit_units_dev, int64_t digit_units, cudaStream_t st) {
+  if (rowmax_units > 0) rowmax_batched<<<(unsigned)rowmax_units, 256, 0, st>>>(jobs_dev, rowmax_units_dev);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (digit_units > 0) digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_prefix_dev, njobs);
+  if (digit_units > 0) digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_units_dev);
   return cudaGetLastError();
 }
 

@@ -13,9 +13,13 @@
 // cut into chains of SEG_BLOCKS k-blocks.  Each finished chain is drained by the epilogue
 // warps (TMEM -> registers, exact FP32 -> int32) into an int32 group sum G_g while the MMA
 // warp fills the other TMEM buffer.  At the end of group g the epilogue folds G_g into
-// R <- 128 R + G_g (Horner in the group index; a 128-bit integer for s <= 13, so the sum is
-// exact, FP64 beyond), kept per CTA in L2-resident scratch; after the last group it writes
-// C = alpha * RN(R 2^{e_i + f_j - 7(s+1)}) (+ beta C), one rounding of the exact value.
+// R <- 128 R + G_g (Horner in the group index), kept per CTA in L2-resident scratch, in exact
+// int64 windows of as many groups as cannot overflow (5 or 6 in practice); two windows make an
+// exact 128-bit sum, later windows continue in FP64.  After the last group it writes
+// C = alpha * RN(R 2^{e_i + f_j - 7(s+1)}) (+ beta C): for up to two windows (s <= 10 at any k
+// that fits in memory) one rounding of the exact value, done with integer instructions, so
+// with alpha = 1, beta = 0 the epilogue issues no FP64 instruction at all -- FP64 is the
+// slowest pipe of this GPU.  The opt-in exact mode keeps a 128-bit Horner sum (s <= 13).
 // Complex (stacked rows 2i = Re, 2i+1 = Im; columns likewise) combines the four real
 // sub-products exactly in int32 before the Horner step: Re = P_rr - P_ii, Im = P_ri + P_ir.
 //
@@ -52,7 +56,9 @@ struct Cfg {
   static constexpr int STAGES = BN_ == 256 ? 4 : 6;
   static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN_ * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr uint32_t IDESC = umma_idesc_f16_f32(BM, BN_);
-  static constexpr uint32_t TMEM_COLS = 2 * BN_;  // two BN-column FP32 accumulators
+  // two BN-column FP32 accumulators; 128-wide tiles also keep the int64 window words (two
+  // columns per output) in the other half
+  static constexpr uint32_t TMEM_COLS = 512;
   static constexpr int CPT = BN_ / 2;             // columns per epilogue thread
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
@@ -218,25 +224,216 @@ __device__ __forceinline__ double horner_step(void* Rp, int g, bool exact, bool 
   return 0.0;
 }
 
-// FP64 Horner step for columns [c0, c1) of a thread's group sums (non-final pushes).  Complex:
-// columns come in (Re, Im) pairs combined exactly across the lane pair before the step.
-__device__ __forceinline__ void push_fp64_range(const int* Gs, double* Rt, int c0, int c1, bool first, bool group2,
-                                                bool cplx, bool odd) {
-  if (!cplx) {
-#pragma unroll 4
-    for (int c = c0; c < c1; ++c) {
-      const double gv = (double)Gs[c];
-      double* Rp = Rt + (size_t)c * 128;
-      *Rp = first ? (group2 ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+// ---- integer windows (default epilogue) ----------------------------------------------------
+// The group sums enter R by Horner's rule in exact int64 arithmetic, c consecutive groups per
+// window, where c is the largest count whose worst case stays below 2^63:
+//   |G_g| <= (g - 1) * kpad * 127^2 (x2 for the complex combine) <= gmax < 2^L,
+//   |window| < gmax * 128^(c-1) * 128/127 < 2^(L + 7 (c - 1) + 1)   =>   c = (62 - L) / 7 + 1.
+// Two windows form the exact 128-bit N = W0 128^len1 + W1, rounded to FP64 once with integer
+// instructions only; a third and later window continue in FP64 (one rounding per window).
+__device__ __forceinline__ int window_len(int s, int KB, int cplx) {
+  const unsigned long long gmax =
+      (unsigned long long)s * (unsigned long long)KB * (unsigned long long)BK * 16129ull * (cplx ? 2ull : 1ull);
+  const int L = 64 - __clzll((long long)gmax);
+  const int c = (62 - L) / 7 + 1;
+  return c < 1 ? 1 : c;
+}
+
+// (a 2^sh + b) as a 128-bit two's complement integer (hi, lo), 1 <= sh <= 63.
+__device__ __forceinline__ void i128_shl_add(long long a, int sh, long long b, long long& hi, unsigned long long& lo) {
+  lo = (unsigned long long)a << sh;
+  hi = a >> (64 - sh);
+  const unsigned long long nl = lo + (unsigned long long)b;
+  hi += (b < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
+  lo = nl;
+}
+
+// RN(N 2^E) for the 128-bit integer N = (hi, lo), built with integer instructions: normalise the
+// magnitude so its leading one is bit 127, keep 53 bits, round to nearest (ties to even) on the
+// guard bit and the sticky OR of the rest, and assemble sign, biased exponent and fraction.
+// Results outside the normal range take the conversion-based path.
+__device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long lo, int E) {
+  const bool neg = hi < 0;
+  unsigned long long mh = (unsigned long long)hi, ml = lo;
+  if (neg) {
+    ml = ~ml + 1;
+    mh = ~mh + (ml == 0 ? 1 : 0);
+  }
+  if ((mh | ml) == 0) return 0.0;
+  const int lz = mh != 0 ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
+  unsigned long long nh, nl;
+  if (lz == 0) {
+    nh = mh;
+    nl = ml;
+  } else if (lz < 64) {
+    nh = (mh << lz) | (ml >> (64 - lz));
+    nl = ml << lz;
+  } else {
+    nh = ml << (lz - 64);
+    nl = 0;
+  }
+  unsigned long long m = nh >> 11;  // 53 bits, leading one at bit 52
+  const unsigned long long guard = (nh >> 10) & 1ull;
+  const bool sticky = (nh & 0x3FFull) != 0 || nl != 0;
+  int x = (127 - lz) + E;  // N 2^E lies in [2^x, 2^(x+1))
+  m += (guard != 0 && (sticky || (m & 1ull))) ? 1ull : 0ull;
+  if (m == (1ull << 53)) {
+    m >>= 1;
+    ++x;
+  }
+  if (x < -1022 || x > 1023) return round_i128(hi, lo, E);
+  const unsigned long long bits =
+      (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(x + 1023) << 52) | (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+// Window-closing or final step of one output, given the first slot's word s0 (int64 W0 while
+// widx == 1, FP64 bits from the second window's close on) and the active window Rw after this
+// push.  Final: returns RN(N 2^E).  Closing: returns the new s0 word.
+__device__ __forceinline__ double final_val(long long s0, long long Rw, int widx, int wlen, int E) {
+  if (widx == 0) return rn_i128_pow2(Rw < 0 ? -1 : 0, (unsigned long long)Rw, E);
+  if (widx == 1) {
+    long long hi;
+    unsigned long long lo;
+    i128_shl_add(s0, 7 * wlen, Rw, hi, lo);
+    return rn_i128_pow2(hi, lo, E);
+  }
+  return scale_pow2(fma(__longlong_as_double(s0), scale_pow2(1.0, 7 * wlen), (double)Rw), E);
+}
+__device__ __forceinline__ long long close_val(long long s0, long long Rw, int widx, int wlen) {
+  if (widx == 1) {
+    long long hi;
+    unsigned long long lo;
+    i128_shl_add(s0, 7 * wlen, Rw, hi, lo);
+    return __double_as_longlong(rn_i128_pow2(hi, lo, 0));
+  }
+  return __double_as_longlong(fma(__longlong_as_double(s0), scale_pow2(1.0, 7 * wlen), (double)Rw));
+}
+
+enum PushKind { kPlain = 0, kSpill = 1, kClose = 2, kFinal = 3 };
+
+// Everything a push needs besides the group sums.
+struct PushArgs {
+  int kind, widx, wlen;
+  bool first, wstart;     // first push of its group; first push of its window
+  uint32_t rtm;           // TMEM address of this thread's window words (TMEM-resident mode)
+  long long* Ra;          // the active window's scratch slot (L2-resident mode)
+  long long* S0;          // the first window's scratch slot
+  int64_t gcol0, orow;
+  bool row_ok, unit_ab, odd;
+  int ebase;
+};
+
+// One push for NCH consecutive outputs o0 .. o0+NCH-1 of this thread.  The active window lives
+// in TMEM (TMR: two 32-bit columns per output, one 32x32b.x32 load and store per 16 outputs) or
+// in the CTA's L2-resident scratch (loads batched NCH deep before any use, to keep that many in
+// flight).  Complex: the (Re, Im) column pairs are combined exactly across the lane pair first.
+template <int NCH, bool TMR>
+__device__ __forceinline__ void push_chunk(const int* Gs, int o0, const PushArgs& a, const TileJob& j) {
+  static_assert(!TMR || NCH == 16, "TMEM chunks are 32 columns");
+  int vv[NCH];
+  if (!j.cplx) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) vv[i] = Gs[o0 + i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) {
+      const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * (o0 + i) + 1], 1);
+      vv[i] = a.odd ? (Gs[2 * (o0 + i)] + other) : (Gs[2 * (o0 + i)] - other);
+    }
+  }
+  long long rw[NCH];
+  if (!(a.first && a.wstart)) {
+    long long ro[NCH];
+    if (TMR) {
+      uint32_t t[32];
+      tmem_ld32(a.rtm + 2 * o0, t);
+      tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) ro[i] = (long long)(((unsigned long long)t[2 * i + 1] << 32) | t[2 * i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) ro[i] = a.Ra[(size_t)(o0 + i) * BM];
+    }
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) rw[i] = a.first ? (long long)((unsigned long long)ro[i] << 7) + vv[i] : ro[i] + vv[i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) rw[i] = vv[i];
+  }
+  if (a.kind == kPlain) {
+    if (TMR) {
+      uint32_t t[32];
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) {
+        t[2 * i] = (uint32_t)(unsigned long long)rw[i];
+        t[2 * i + 1] = (uint32_t)((unsigned long long)rw[i] >> 32);
+      }
+      tmem_st32(a.rtm + 2 * o0, t);
+      tmem_st_wait();
+    } else {
+#pragma unroll
+      for (int i = 0; i < NCH; ++i) a.Ra[(size_t)(o0 + i) * BM] = rw[i];
+    }
+    return;
+  }
+  if (a.kind == kSpill) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) a.S0[(size_t)(o0 + i) * BM] = rw[i];
+    return;
+  }
+  long long s0[NCH];
+  if (a.widx >= 1) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s0[i] = a.S0[(size_t)(o0 + i) * BM];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s0[i] = 0;
+  }
+  if (a.kind == kClose) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) a.S0[(size_t)(o0 + i) * BM] = close_val(s0[i], rw[i], a.widx, a.wlen);
+    return;
+  }
+  // column exponents of the chunk, fetched together (one latency for the chunk)
+  int fe[NCH];
+  const int64_t c0 = j.cplx ? (a.gcol0 >> 1) + o0 : a.gcol0 + o0;
+  const int64_t climit = j.cplx ? j.n : j.cols;
+#pragma unroll
+  for (int i = 0; i < NCH; ++i) fe[i] = c0 + i < climit ? __ldg(j.f + c0 + i) : 0;
+  if (!j.cplx) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) {
+      const int64_t col = c0 + i;
+      if (a.row_ok && col < j.cols) {
+        const double tv = final_val(s0[i], rw[i], a.widx, a.wlen, a.ebase + fe[i]);
+        double* cp = j.C + a.orow + col * j.ldc;
+        *cp = a.unit_ab ? tv : (j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp));
+      }
     }
   } else {
-#pragma unroll 2
-    for (int c = c0 / 2; c < c1 / 2; ++c) {
-      const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * c + 1], 1);
-      const int comb = odd ? (Gs[2 * c] + other) : (Gs[2 * c] - other);
-      const double gv = (double)comb;
-      double* Rp = Rt + (size_t)c * 128;
-      *Rp = first ? (group2 ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) {
+      const int64_t jc = c0 + i;
+      const bool ok = a.row_ok && jc < j.n;
+      const double part = ok ? final_val(s0[i], rw[i], a.widx, a.wlen, a.ebase + fe[i]) : 0.0;
+      const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
+      if (ok) {
+        double* cp = j.C + 2 * (a.orow + jc * j.ldc);
+        if (a.unit_ab) {
+          cp[a.odd ? 1 : 0] = part;
+        } else {
+          const double tr = a.odd ? partner : part, ti = a.odd ? part : partner;
+          double re = fma(j.a0, tr, -(j.a1 * ti));
+          double im = fma(j.a0, ti, j.a1 * tr);
+          if (!j.beta_zero) {
+            const double cr = cp[0], ci = cp[1];
+            re += fma(j.b0, cr, -(j.b1 * ci));
+            im += fma(j.b0, ci, j.b1 * cr);
+          }
+          cp[a.odd ? 1 : 0] = a.odd ? im : re;
+        }
+      }
     }
   }
 }
@@ -397,13 +594,17 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     double* Rbase = Rws + (size_t)blockIdx.x * BM * BN * 2;  // room for 16 bytes per output
     const bool exact_mode = GROUPED ? false : (P->exact != 0);
     const bool defer_ok = GROUPED ? (G->defer != 0) : (P->defer != 0);
-    // An intermediate FP64 push is spread over the drains that precede the next push, so that
-    // it overlaps the MMA warp's next chains instead of stalling them (the MMA runs at most one
-    // chain ahead of the drains).  Final pushes, exact-mode and inspection pushes run at once.
+    // Active window words: in TMEM columns 2 BN .. 4 BN for 128-wide tiles (the accumulators
+    // use 0 .. 2 BN; two 32-bit columns per output), else in the CTA's scratch tile.
+    constexpr bool TMR = (BN == 128);
+    constexpr int NCH = TMR ? 16 : 8;  // outputs per push chunk
+    const uint32_t rtm = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(2 * BN + chalf * CPT * 2);
+    // A plain push can be spread over the drains that precede the next push, so that it
+    // overlaps the MMA warp's next chains instead of stalling them (the MMA runs at most one
+    // chain ahead of the drains).  Other pushes run at once.
     int Gs[CPT];
-    int pend_c = CPT, pend_chunk = CPT;
-    bool pend_first = false, pend_g2 = false;
-    double* pend_Rt = nullptr;
+    int pend_o = CPT, pend_chunk = CPT, pend_nout = CPT;
+    PushArgs pend;
     const bool odd = (lane & 1) != 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
@@ -415,7 +616,27 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
       const int64_t orow = j.cplx ? (grow >> 1) : grow;
       const int e_row = (row_ok && j.e != nullptr) ? j.e[orow] : 0;
       const int64_t gcol0 = (int64_t)j.tn * BN + chalf * CPT;
+      const int win = window_len(s, j.KB, j.cplx);
+      const int nout = j.cplx ? CPT / 2 : CPT;  // outputs of this thread
+      // scratch slots: S0 (first window, later the FP64 partial), S1 (windows 1, 2, ... when the
+      // active window is not in TMEM)
+      long long* S0t = reinterpret_cast<long long*>(Rbase) + (size_t)(j.cplx ? chalf * CPT / 2 : chalf * CPT) * BM + r;
+      long long* S1t = S0t + (size_t)BM * BN;
+      PushArgs pa;
+      pa.rtm = rtm;
+      pa.S0 = S0t;
+      pa.gcol0 = gcol0;
+      pa.orow = orow;
+      pa.row_ok = row_ok;
+      pa.unit_ab = j.beta_zero && j.a0 == 1.0 && j.a1 == 0.0;  // C = RN(T): no FP64 work
+      pa.odd = odd;
+      pa.ebase = e_row - 7 * (s + 1);
       for (int g = 2; g <= s + 1; ++g) {
+        const int widx = (g - 2) / win, pos = (g - 2) % win;
+        const int wlen = min(win, s - widx * win);
+        pa.widx = widx;
+        pa.wlen = wlen;
+        pa.Ra = widx == 0 ? S0t : S1t;
         int Gr[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) Gr[c] = 0;
@@ -442,13 +663,30 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           buf ^= 1;
           const bool group_end = (seg == nseg - 1);
           const bool push_now = group_end || ((seg + 1) % push_segs) == 0;
-          if (pend_c < CPT) {  // advance the pending push; complete it before the next one
-            const int c1 = push_now ? CPT : min(CPT, pend_c + pend_chunk);
-            push_fp64_range(Gs, pend_Rt, pend_c, c1, pend_first, pend_g2, j.cplx != 0, odd);
-            pend_c = c1;
+          if (pend_o < pend_nout) {  // advance the pending push; complete it before the next one
+            const int o1 = push_now ? pend_nout : min(pend_nout, pend_o + pend_chunk);
+#pragma unroll 1
+            for (int o = pend_o; o < o1; o += NCH) push_chunk<NCH, TMR>(Gs, o, pend, j);
+            pend_o = o1;
           }
           if (!push_now) continue;
           const bool final_push = group_end && g == s + 1;
+          const bool exact_now = exact_mode && s <= kExactMaxS;
+          pa.first = first_push;
+          pa.wstart = first_push && pos == 0;
+          const bool win_end = group_end && pos == wlen - 1;
+          pa.kind = final_push ? kFinal : !win_end ? kPlain : widx >= 1 ? kClose : TMR ? kSpill : kPlain;
+          if (TMR && !exact_now && Gdbg == nullptr && pa.kind != kFinal) {
+            // TMEM-resident windows: non-final pushes go straight from the registers (chunk offsets are
+            // compile-time constants, so Gr stays in registers)
+#pragma unroll
+            for (int o = 0; o < CPT; o += NCH)
+              if (o < nout) push_chunk<NCH, TMR>(Gr, o, pa, j);
+#pragma unroll
+            for (int c = 0; c < CPT; ++c) Gr[c] = 0;
+            first_push = false;
+            continue;
+          }
           // ---- push the group sums into R (or, for inspection, export them) ----
           // Pushes happen once per group (per 64 chains at most): the sums move to a
           // thread-local array indexed at run time, so the FP64 work below runs in a rolled
@@ -458,18 +696,16 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
             Gs[c] = Gr[c];
             Gr[c] = 0;
           }
-          const bool exact_now = exact_mode && s <= kExactMaxS;
-          if (!final_push && !exact_now && Gdbg == nullptr) {
+          if (pa.kind == kPlain && !exact_now && Gdbg == nullptr) {
             // drains before the next push: the rest of this group, or the next group's chains
             const int left = group_end ? nseg_of(g + 1, j.KB) : nseg - (seg + 1);
             const int drains = min(left, push_segs);
             if (defer_ok && drains >= 2) {
-              pend_c = 0;
-              pend_chunk = (CPT + drains - 2) / (drains - 1);
-              pend_chunk = (pend_chunk + 1) & ~1;  // whole (Re, Im) column pairs
-              pend_first = first_push;
-              pend_g2 = (g == 2);
-              pend_Rt = Rbase + (size_t)((j.cplx ? chalf * CPT / 2 : chalf * CPT)) * BM + r;
+              pend = pa;
+              pend_o = 0;
+              pend_nout = nout;
+              pend_chunk = (nout + drains - 2) / (drains - 1);
+              pend_chunk = (pend_chunk + NCH - 1) / NCH * NCH;
               first_push = false;
               continue;
             }
@@ -523,62 +759,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                 }
               }
             }
-          } else if (!j.cplx) {
-            double* Rt = Rbase + (size_t)(chalf * CPT) * BM + r;
-            if (!final_push) {
-#pragma unroll 4
-              for (int c = 0; c < CPT; ++c) {
-                const double gv = (double)Gs[c];
-                double* Rp = Rt + (size_t)c * BM;
-                *Rp = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
-              }
-            } else {
-              const int ebase = e_row - 7 * (s + 1);
-#pragma unroll 4
-              for (int c = 0; c < CPT; ++c) {
-                const double gv = (double)Gs[c];
-                const double* Rp = Rt + (size_t)c * BM;
-                const double Rv = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
-                const int64_t col = gcol0 + c;
-                if (row_ok && col < j.cols) {
-                  const double tv = scale_pow2(Rv, ebase + __ldg(j.f + col));
-                  double* cp = j.C + orow + col * j.ldc;
-                  *cp = j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp);
-                }
-              }
-            }
           } else {
-            double* Rt = Rbase + (size_t)(chalf * CPT / 2) * BM + r;
-            const int ebase = e_row - 7 * (s + 1);
-#pragma unroll 2
-            for (int c = 0; c < CPT / 2; ++c) {
-              // even lane (Re row) holds (rr, ri), odd lane (Im row) holds (ir, ii) at columns 2c, 2c+1
-              const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * c + 1], 1);
-              const int comb = odd ? (Gs[2 * c] + other) : (Gs[2 * c] - other);
-              double* Rp = Rt + (size_t)c * BM;
-              const double gv = (double)comb;
-              const double Rv = first_push ? ((g == 2) ? gv : fma(*Rp, 128.0, gv)) : (*Rp + gv);
-              if (!final_push) {
-                *Rp = Rv;
-              } else {
-                const int64_t jc = (gcol0 >> 1) + c;
-                const bool ok = row_ok && jc < j.n;
-                const double part = ok ? scale_pow2(Rv, ebase + __ldg(j.f + jc)) : 0.0;
-                const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
-                const double tr = odd ? partner : part, ti = odd ? part : partner;
-                if (ok) {
-                  double* cp = j.C + 2 * (orow + jc * j.ldc);
-                  double re = fma(j.a0, tr, -(j.a1 * ti));
-                  double im = fma(j.a0, ti, j.a1 * tr);
-                  if (!j.beta_zero) {
-                    const double cr = cp[0], ci = cp[1];
-                    re += fma(j.b0, cr, -(j.b1 * ci));
-                    im += fma(j.b0, ci, j.b1 * cr);
-                  }
-                  cp[odd ? 1 : 0] = odd ? im : re;
-                }
-              }
-            }
+#pragma unroll 1
+            for (int o = 0; o < nout; o += NCH) push_chunk<NCH, TMR>(Gs, o, pa, j);
           }
           first_push = false;
         }

@@ -23,7 +23,7 @@ struct GroupPlan {
   int64_t rowmax_units = 0, digit_units = 0;
   cudaGraphExec_t exec = nullptr;
   size_t oFlags = 0, flags_bytes = 0, oMax = 0, max_bytes = 0;
-  size_t oJobs = 0, oRmPre = 0, oDgPre = 0, oCalls = 0, oTiles = 0, oNative = 0, oFlagPtrs = 0;
+  size_t oJobs = 0, oRmTab = 0, oDgTab = 0, oCalls = 0, oTiles = 0, oNative = 0, oFlagPtrs = 0;
   size_t oNList = 0, oNPre = 0, oNTot = 0, oChecks = 0, oErrs = 0, oCold = 0, oR = 0;
   std::vector<int> s_used;
   // automatic (selector) calls
@@ -89,12 +89,11 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oFlags), 0, P.flags_bytes, st));
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
-  OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int64_t>(c, P.oRmPre), P.rowmax_units,
-                                gat<int64_t>(c, P.oDgPre), P.digit_units, P.njobs, st));
+  OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units,
+                                gat<int2>(c, P.oDgTab), P.digit_units, st));
   if (P.any_auto) {
     OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
-    OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int64_t>(c, P.oDgPre), P.digit_units, P.njobs,
-                                     st));
+    OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, st));
     OZG_CUDA(launch_select_batched(c->dsel, gat<SelectJob>(c, P.oSel), P.ncalls, (float)std::log10(c->target), st));
     OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
                                          P.ncalls, 0, st));
@@ -189,8 +188,20 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   }
   P->njobs = (int)(2 * count);
   P->oJobs = cv.take(sizeof(SplitArgs) * 2 * count);
-  P->oRmPre = cv.take(sizeof(int64_t) * (2 * count + 1));
-  P->oDgPre = cv.take(sizeof(int64_t) * (2 * count + 1));
+  // work-unit tables of the batched split (job j = 2i for A, 2i + 1 for B of call i)
+  std::vector<int2> rmtab, dgtab;
+  for (int64_t i = 0; i < count; ++i)
+    for (int side = 0; side < 2; ++side) {
+      SplitArgs x;
+      x.rows = side ? d[i].n : d[i].m;
+      x.k = d[i].k;
+      x.strided = side ? (TB[i] == 'T') : (TA[i] == 'N');
+      const int job = (int)(2 * i + side);
+      for (int64_t u = 0, nu = rowmax_units_of(x); u < nu; ++u) rmtab.push_back(make_int2(job, (int)u));
+      for (int64_t u = 0, nu = digit_units_of(x); u < nu; ++u) dgtab.push_back(make_int2(job, (int)u));
+    }
+  P->oRmTab = cv.take(sizeof(int2) * std::max<size_t>(rmtab.size(), 1));
+  P->oDgTab = cv.take(sizeof(int2) * std::max<size_t>(dgtab.size(), 1));
   P->oCalls = cv.take(sizeof(GroupCall) * count + 64);
   P->oTiles = cv.take(sizeof(GroupTile) * tiles.size());
   P->oNative = cv.take(sizeof(NativeArgs) * count);
@@ -227,7 +238,6 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->epoch = c->gws_epoch;
 
   std::vector<SplitArgs> jobs(2 * count);
-  std::vector<int64_t> rm(2 * count + 1, 0), dg(2 * count + 1, 0);
   std::vector<GroupCall> calls(count);
   std::vector<NativeArgs> nat(count);
   std::vector<const int*> fptr(count);
@@ -262,12 +272,6 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     jobs[2 * i] = a;
     jobs[2 * i + 1] = b;
     // units: rows per rowmax unit 256 (strided) / 8 (contiguous); digit tiles 32 x 64
-    auto rm_units = [](const SplitArgs& x) { return x.strided ? (x.rows + 255) / 256 : (x.rows + 7) / 8; };
-    auto dg_units = [](const SplitArgs& x) { return ((x.rows + 31) / 32) * ((x.k + 63) / 64); };
-    rm[2 * i + 1] = rm[2 * i] + rm_units(a);
-    rm[2 * i + 2] = rm[2 * i + 1] + rm_units(b);
-    dg[2 * i + 1] = dg[2 * i] + dg_units(a);
-    dg[2 * i + 2] = dg[2 * i + 1] + dg_units(b);
 
     GroupCall& g = calls[i];
     OZG_CUDA(make_digit_tmap(&g.tmA, a.D, d[i].k, d[i].m, Kp, planes[i], 128));
@@ -365,12 +369,16 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
       chk2[i].gate = R.skip2;
     }
   }
-  P->rowmax_units = rm.back();
-  P->digit_units = dg.back();
+  P->rowmax_units = (int64_t)rmtab.size();
+  P->digit_units = (int64_t)dgtab.size();
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs), jobs.data(), sizeof(SplitArgs) * jobs.size(), cudaMemcpyHostToDevice, st));
-  OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oRmPre), rm.data(), sizeof(int64_t) * rm.size(), cudaMemcpyHostToDevice, st));
-  OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oDgPre), dg.data(), sizeof(int64_t) * dg.size(), cudaMemcpyHostToDevice, st));
+  if (!rmtab.empty())
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oRmTab), rmtab.data(), sizeof(int2) * rmtab.size(), cudaMemcpyHostToDevice,
+                             st));
+  if (!dgtab.empty())
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oDgTab), dgtab.data(), sizeof(int2) * dgtab.size(), cudaMemcpyHostToDevice,
+                             st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oCalls), calls.data(), sizeof(GroupCall) * calls.size(), cudaMemcpyHostToDevice, st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oTiles), tiles.data(), sizeof(GroupTile) * tiles.size(), cudaMemcpyHostToDevice, st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oNative), nat.data(), sizeof(NativeArgs) * nat.size(), cudaMemcpyHostToDevice, st));

@@ -139,8 +139,17 @@ cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, in
 
 // ---------------------------------------------------------------------------------- batched
 // prefix arrays: njobs + 1 entries, prefix[0] = 0, prefix[njobs] = units
-cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int64_t* rowmax_prefix_dev, int64_t rowmax_units,
-                                 const int64_t* digit_prefix_dev, int64_t digit_units, int njobs, cudaStream_t st);
+// Batched split: one launch per pass over every job of a batch.  Work units come from device
+// tables of (job, unit within the job): row-max units are 32 rows x kRmStridedK k of a strided
+// job or 8 rows x kRmContigK k of a contiguous one; digit units are 32 rows x 64 k.
+constexpr int kRmStridedK = 128, kRmContigK = 1024;
+inline int64_t rowmax_units_of(const SplitArgs& x) {
+  return x.strided ? ((x.rows + 31) / 32) * ((x.k + kRmStridedK - 1) / kRmStridedK)
+                   : ((x.rows + 7) / 8) * ((x.k + kRmContigK - 1) / kRmContigK);
+}
+inline int64_t digit_units_of(const SplitArgs& x) { return ((x.rows + 31) / 32) * ((x.k + 63) / 64); }
+cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t rowmax_units,
+                                 const int2* digit_units_dev, int64_t digit_units, cudaStream_t st);
 // grouped automatic calls: after the check, skip2[c] = 0 for the calls to re-run (automatic,
 // finite, sampled error above the target), 1 otherwise; save / restore C of automatic calls
 // with beta != 0 (restore only for the calls being re-run)
@@ -188,8 +197,8 @@ struct SelectJob {
   int s_cap = 0, active = 0;
 };
 cudaError_t launch_gap_hist_pair(const SplitArgs& a, const SplitArgs& b, cudaStream_t st);
-cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int64_t* digit_prefix_dev, int64_t units,
-                                    int njobs, cudaStream_t st);
+cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* digit_units_dev, int64_t units,
+                                    cudaStream_t st);
 // M may be null: then only feat_out is written
 cudaError_t launch_select_single(const SelectorDev* M, const unsigned long long* hA, const unsigned long long* hB,
                                  int64_t m, int64_t n, int64_t k, float log10_target, int s_cap, int* s_out,

@@ -77,25 +77,14 @@ __global__ void __launch_bounds__(256) gap_hist_pair(SplitArgs a, SplitArgs b, i
   if (threadIdx.x < 10 && sh[threadIdx.x]) atomicAdd(&J.hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
 }
 
-__device__ __forceinline__ int find_unit_job(const int64_t* prefix, int njobs, int64_t unit) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= unit)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
 
-__global__ void __launch_bounds__(256) gap_hist_batched(const SplitArgs* jobs, const int64_t* prefix, int njobs) {
+__global__ void __launch_bounds__(256) gap_hist_batched(const SplitArgs* jobs, const int2* units) {
   __shared__ unsigned int sh[10];
   if (threadIdx.x < 10) sh[threadIdx.x] = 0;
   __syncthreads();
-  const int jb = find_unit_job(prefix, njobs, blockIdx.x);
-  const SplitArgs J = jobs[jb];
-  if (J.hist != nullptr) hist_tile(J, (int64_t)blockIdx.x - prefix[jb], sh);
+  const int2 ur = units[blockIdx.x];
+  const SplitArgs J = jobs[ur.x];
+  if (J.hist != nullptr) hist_tile(J, (int64_t)ur.y, sh);
   __syncthreads();
   if (J.hist != nullptr && threadIdx.x < 10 && sh[threadIdx.x])
     atomicAdd(&J.hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
@@ -311,10 +300,10 @@ cudaError_t launch_gap_hist_pair(const SplitArgs& a, const SplitArgs& b, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int64_t* digit_prefix_dev, int64_t units,
-                                    int njobs, cudaStream_t st) {
-  if (units <= 0 || njobs <= 0) return cudaSuccess;
-  gap_hist_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, digit_prefix_dev, njobs);
+cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* digit_units_dev, int64_t units,
+                                    cudaStream_t st) {
+  if (units <= 0) return cudaSuccess;
+  gap_hist_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, digit_units_dev);
   return cudaGetLastError();
 }
 

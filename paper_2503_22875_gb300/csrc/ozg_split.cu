@@ -6,41 +6,10 @@
 // needed: the fixed-point value is the 53-bit significand shifted).  HBM-bound: one read of
 // op(X) for the maxima, one read plus s fp16 writes for the digits.
 #include "ozg_internal.h"
+#include "ozg_split_dev.cuh"
 
 namespace ozg {
 namespace {
-
-constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
-constexpr uint64_t kInfBits = 0x7FF0000000000000ull;
-
-__device__ __forceinline__ int exponent_from_maxbits(unsigned long long mb) {
-  if (mb == 0) return 0;
-  int eb = (int)(mb >> 52);
-  if (eb) return eb - 1022;                 // normal: max = 1.f 2^(eb-1023) = 0.1f 2^(eb-1022)
-  return (64 - __clzll((long long)mb)) - 1074;  // subnormal: max in [2^(L-1), 2^L) 2^-1074
-}
-
-// floor(|x| 2^{s7 - e}) as a 128-bit integer; requires |x| < 2^e (true for every entry of the row)
-__device__ __forceinline__ unsigned __int128 fixed_point(uint64_t b, int e, int s7) {
-  int eb = (int)((b >> 52) & 0x7FF);
-  uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-  int ex;
-  if (eb == 0) {
-    ex = -1074;
-  } else {
-    mant |= 1ull << 52;
-    ex = eb - 1075;
-  }
-  int sh = ex - e + s7;
-  if (sh >= 0) return sh < 128 ? ((unsigned __int128)mant << sh) : (unsigned __int128)0;
-  if (sh > -64) return (unsigned __int128)(mant >> (-sh));
-  return 0;
-}
-
-__device__ __forceinline__ uint16_t digit_half_bits(unsigned __int128 F, int shift, bool neg) {
-  int d = (int)((uint32_t)(F >> shift) & 127u);
-  return __half_as_ushort(__int2half_rn(neg ? -d : d));
-}
 
 __device__ __forceinline__ void flag_nonfinite(uint64_t absbits, int* nonfinite) {
   if (absbits >= kInfBits) atomicExch(nonfinite, 1);
@@ -121,7 +90,6 @@ __global__ void digits_contig(const double* __restrict__ X, int64_t ld, int64_t 
   int64_t row = gid / groups, l0 = (gid % groups) * 8;
   int e = exponent_from_maxbits(maxbits[row]);
   if (l0 == 0) exps[row] = e;
-  int s7 = 7 * s;
   const int nparts = CPLX ? 2 : 1;
   uint64_t bits[2][8];
 #pragma unroll
@@ -137,26 +105,12 @@ __global__ void digits_contig(const double* __restrict__ X, int64_t ld, int64_t 
   }
 #pragma unroll
   for (int part = 0; part < nparts; ++part) {
-    unsigned __int128 F[8];
-    bool neg[8];
+    DigitSrc ds[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      F[j] = fixed_point(bits[part][j], e, s7);
-      neg[j] = (bits[part][j] >> 63) != 0;
-    }
+    for (int j = 0; j < 8; ++j) ds[j] = digit_src(bits[part][j], e);
     int64_t orow = CPLX ? 2 * row + part : row;
-    for (int t = 1; t <= s; ++t) {
-      int sh = 7 * (s - t);
-      uint4 out;
-      uint16_t h[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = digit_half_bits(F[j], sh, neg[j]);
-      out.x = h[0] | ((uint32_t)h[1] << 16);
-      out.y = h[2] | ((uint32_t)h[3] << 16);
-      out.z = h[4] | ((uint32_t)h[5] << 16);
-      out.w = h[6] | ((uint32_t)h[7] << 16);
-      *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0) = out;
-    }
+    for (int t = 1; t <= s; ++t)
+      *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0) = digits8(ds, t);
   }
 }
 
@@ -197,30 +151,14 @@ __global__ void __launch_bounds__(256) digits_strided(const double* __restrict__
   if (row >= rows || l0 + lg >= k) return;
   int e = exponent_from_maxbits(maxbits[row]);
   if (l0 + lg == 0) exps[row] = e;
-  int s7 = 7 * s;
 #pragma unroll
   for (int part = 0; part < W; ++part) {
-    unsigned __int128 F[8];
-    bool neg[8];
+    DigitSrc ds[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint64_t b = tile[lg + j][W * r + part];
-      F[j] = fixed_point(b, e, s7);
-      neg[j] = (b >> 63) != 0;
-    }
+    for (int j = 0; j < 8; ++j) ds[j] = digit_src(tile[lg + j][W * r + part], e);
     int64_t orow = CPLX ? 2 * row + part : row;
-    for (int t = 1; t <= s; ++t) {
-      int sh = 7 * (s - t);
-      uint16_t h[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = digit_half_bits(F[j], sh, neg[j]);
-      uint4 out;
-      out.x = h[0] | ((uint32_t)h[1] << 16);
-      out.y = h[2] | ((uint32_t)h[3] << 16);
-      out.z = h[4] | ((uint32_t)h[5] << 16);
-      out.w = h[6] | ((uint32_t)h[7] << 16);
-      *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0 + lg) = out;
-    }
+    for (int t = 1; t <= s; ++t)
+      *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0 + lg) = digits8(ds, t);
   }
 }
 

@@ -2,10 +2,11 @@
 
   * split exponents and INT8 digits: bit-exact (integer work)
   * integer group products G_g from the tensor-core kernel: bit-exact
-  * emulated DGEMM / ZGEMM: within a tolerance derived from the FP64 epilogue (Horner over the
-    s groups in FP64, one rounding per step) -- |C_gpu - C_oracle| <= 4 (s + 2) u |alpha| (|A||B|)
-    + 2 u |C| + u |beta| |C0| -- and within the a priori bound of the method against
-    double-double.
+  * emulated DGEMM / ZGEMM: bit-exact where the epilogue's exact int64 windows cover every group
+    (at most two windows: s <= 10 at any k, s <= 12 for k <= 512), else within a tolerance
+    derived from the FP64 continuation (one rounding per later window) -- |C_gpu - C_oracle| <=
+    4 (s + 2) u |alpha| (|A||B|) + 2 u |C| + u |beta| |C0| -- and within the a priori bound of
+    the method against double-double.
   * native FP64 kernel: within gamma_k of double-double.
 """
 import numpy as np
@@ -352,9 +353,9 @@ def test_sampled_check_beta_and_complex(ozg, ctx):
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
 @pytest.mark.parametrize("m,n,k,s", [(200, 300, 500, 7), (129, 257, 1100, 13), (64, 64, 64, 3), (5, 3, 2000, 10)])
 def test_dgemm_bit_exact_single_rounding(ozg, ctx, ta, tb, m, n, k, s):
-    """In the correctly rounded mode (s <= 13) the epilogue sums the group products exactly
-    (128-bit Horner) and rounds once: with alpha = 1, beta = 0 the result equals the oracle's
-    definition bit for bit; the default mode stays within its stated tolerance."""
+    """In the opt-in correctly rounded mode (s <= 13) the epilogue sums the group products
+    exactly (128-bit Horner) and rounds once: with alpha = 1, beta = 0 the result equals the
+    oracle's definition bit for bit, also where the default mode needs a third window."""
     A = wide((m, k) if ta == "N" else (k, m), 2.0, 7 * m + k)
     B = wide((k, n) if tb == "N" else (n, k), 2.0, 5 * n + k)
     C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
@@ -382,6 +383,63 @@ def test_zgemm_bit_exact_single_rounding(ozg, ctx, ta, tb):
     finally:
         ctx.set_exact_epilogue(False)
     assert np.array_equal(host(ozg, C, m, n), oracle.zgemm_emu(A, B, s, ta, tb))
+
+
+def windows(s, k, cplx=False):
+    """Number of exact int64 windows the default epilogue uses: the largest group count c with
+    (s k_pad 127^2 [x2 complex]) 128^(c-1) 128/127 < 2^63, and ceil(s / c) windows."""
+    gmax = s * (-(-k // 64) * 64) * 127 * 127 * (2 if cplx else 1)
+    c = max(1, (62 - gmax.bit_length()) // 7 + 1)
+    return -(-s // c)
+
+
+@pytest.mark.parametrize("ta,tb,m,n,k,s,alpha,beta", [
+    ("N", "N", 200, 300, 500, 7, 1.0, 0.0),
+    ("T", "N", 77, 50, 300, 12, 1.0, 0.0),
+    ("N", "T", 300, 130, 8200, 7, -0.5, 0.25),   # long k: chains and pushes split a group
+    ("T", "T", 5, 3, 2000, 10, 3.0, 1.0),
+    ("N", "N", 129, 257, 64, 3, 1.0, 0.0),
+])
+def test_dgemm_default_bit_exact_two_windows(ozg, ctx, ta, tb, m, n, k, s, alpha, beta):
+    """With at most two int64 windows the default epilogue sums the group products exactly and
+    rounds once (integer instructions), so it equals the oracle's definition bit for bit, alpha
+    and beta included (same fma order)."""
+    assert windows(s, k) <= 2
+    A = wide((m, k) if ta == "N" else (k, m), 2.0, 3 * m + k)
+    B = wide((k, n) if tb == "N" else (n, k), 2.0, 3 * n + k)
+    C0 = np.asfortranarray(workloads.rng(m + n).uniform(-1, 1, (m, n)))
+    C = dev(ozg, C0)
+    ctx.dgemm(ta, tb, m, n, k, alpha, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], beta, C, m, s)
+    ctx.sync()
+    assert np.array_equal(host(ozg, C, m, n), oracle.dgemm_emu(A, B, s, ta, tb, alpha, beta, C0))
+
+
+@pytest.mark.parametrize("ta,tb,alpha,beta", [("N", "N", 1.0, 0.0), ("C", "T", 0.5 - 2j, 1.5 + 0.25j)])
+def test_zgemm_default_bit_exact_two_windows(ozg, ctx, ta, tb, alpha, beta):
+    m, n, k, s = 70, 90, 300, 9
+    assert windows(s, k, cplx=True) <= 2
+    shA = (m, k) if ta == "N" else (k, m)
+    shB = (k, n) if tb == "N" else (n, k)
+    A = wide(shA, 1.0, 821) + 1j * wide(shA, 1.0, 822)
+    B = wide(shB, 1.0, 823) + 1j * wide(shB, 1.0, 824)
+    C0 = np.asfortranarray(workloads.rng(825).normal(size=(m, n)) + 1j * workloads.rng(826).normal(size=(m, n)))
+    C = dev(ozg, C0)
+    ctx.zgemm(ta, tb, m, n, k, alpha, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], beta, C, m, s)
+    ctx.sync()
+    assert np.array_equal(host(ozg, C, m, n), oracle.zgemm_emu(A, B, s, ta, tb, alpha, beta, C0))
+
+
+@pytest.mark.parametrize("k,s", [(1100, 13), (300, 14), (300, 18), (5000, 16)])
+def test_dgemm_three_or_more_windows_fp64(ozg, ctx, k, s):
+    """Beyond two windows the partial sum continues in FP64 (one rounding per window): within the
+    stated tolerance of the oracle."""
+    assert windows(s, k) >= 3
+    m, n = 90, 130
+    A, B = wide((m, k), 3.0, 831 + k), wide((k, n), 3.0, 832 + k)
+    C = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+    ctx.dgemm("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, C, m, s)
+    ctx.sync()
+    check_dgemm(host(ozg, C, m, n), A, B, s, "N", "N", 1.0, 0.0, None)
 
 
 def test_dgemm_s_above_13_fp64_epilogue(ozg, ctx):
