@@ -209,17 +209,19 @@ int ozg_set_graphs(ozg_ctx* ctx, int enable);
 int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
 
 /* Tile variants of the slice-product kernel.  Bit 0 picks the output tile (0: 128 x 256,
- * 1: 128 x 128); bit 1 spreads each intermediate epilogue accumulation over the next chains'
- * drains instead of running it at once (pays for long k, costs for short k).  All four variants
- * give bit-identical C. */
+ * 1: 128 x 128).  Bit 1: for 128 x 256 tiles, spread each intermediate epilogue accumulation
+ * over the next chains' drains instead of running it at once (pays for long k, costs for short
+ * k); for 128 x 128 tiles, stage one 64-wide k slice per pipeline stage in 6 stages instead of
+ * two in 3 (deeper prefetch, more issue overhead).  All four variants give bit-identical C. */
 #define OZG_NUM_TILE_VARIANTS 4
 
 /* Tile-variant autotuner: enable != 0 times the four variants the first time a shape bucket
  * (rounded log2 of m, n, k and the slice count) or a grouped batch is seen, keeps the fastest,
  * and appends single-call choices to cache_path (may be NULL) as "bucket variant" lines that
  * later contexts read back.  Tuning runs only for calls with beta == 0 (C is then write-only);
- * other calls use the heuristic: the width that pads least, deferral when k >= 2048 (for a
- * grouped batch: when the mean k weighted by m n s^2 is >= 2048). */
+ * other calls use the heuristic: the width that pads least; then for 128 x 256 tiles deferral
+ * when k >= 2048, for 128 x 128 tiles the deeper pipeline when s >= 10 (for a grouped batch,
+ * the means of k and s weighted by m n s^2). */
 int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
 
 /* Force tile variant 0..3 for every later call (single and grouped), or -1 (default) for the

@@ -148,20 +148,20 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   ga.status = c->dflags;
   ga.nonfinite = Gdbg ? nullptr : nonfinite;
   ga.variant = variant;
-  ga.defer = (variant >> 1) & 1;
+  ga.defer = ozg::variant_defers(variant);
   ga.grid = grid_of(variant);
   ga.s_dev = autos ? s_dev : nullptr;
   ga.exact = c->exact;
   if (c->autotune && c->force_variant < 0 && !Gdbg && ga.beta_zero && !autos) {
     const uint64_t bucket = shape_bucket(prA, prB, k, s);
     if (c->tune.find(bucket) == c->tune.end()) {
-      // time the four variants (two widths x deferred pushes) on this call (C is write-only
-      // here and every variant gives the same bits)
+      // time the four variants (two widths x stage shape or deferred pushes) on this call (C
+      // is write-only here and every variant gives the same bits)
       float best = 1e30f;
       for (int v = 0; v < 4; ++v) {
         ozg::GemmArgs gt = ga;
         gt.variant = v;
-        gt.defer = (v >> 1) & 1;
+        gt.defer = ozg::variant_defers(v);
         gt.grid = grid_of(v);
         cudaEvent_t e0 = pool_get(c), e1 = pool_get(c);
         if (!e0 || !e1) return OZG_ERR_CUDA;
@@ -180,7 +180,7 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
       }
       tune_store(c, bucket, variant);
       ga.variant = variant;
-      ga.defer = (variant >> 1) & 1;
+      ga.defer = ozg::variant_defers(variant);
       ga.grid = grid_of(variant);
     }
   }

@@ -10,7 +10,7 @@
 //
 // Per output tile (BM x BN of the (stacked) product) the schedule is group-major:
 //   for g = 2 .. s+1:  for kb in k-blocks:  for p = 1 .. g-1:  D[buf] += A_p[kb] * B_{g-p}[kb]^T
-// cut into chains of SEG_BLOCKS k-blocks.  Each finished chain is drained by the epilogue
+// cut into chains of at most 1024 products (k-blocks x pairs).  Each finished chain is drained by the epilogue
 // warps (TMEM -> registers, exact FP32 -> int32) into an int32 group sum G_g while the MMA
 // warp fills the other TMEM buffer.  At the end of group g the epilogue folds G_g into
 // R <- 128 R + G_g (Horner in the group index), kept per CTA in L2-resident scratch, in exact
@@ -41,20 +41,28 @@
 namespace ozg {
 namespace {
 
-constexpr int BM = 128, BK = 64;
+constexpr int BM = 128, BK = 64;  // BK: k width of one 128-byte swizzle atom (one TMA box)
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 128 + EPI_WARPS * 32;
 constexpr int REG_PRODUCER = 40, REG_EPILOGUE = 232;
 static_assert(128 * REG_PRODUCER + EPI_WARPS * 32 * REG_EPILOGUE <= THREADS * 168, "register split");
-constexpr int SEG_BLOCKS = 16;  // 16 * 64 = 1024 products per chain: 1024 * 127^2 = 16516096 < 2^24
-constexpr int GROUP_M = 8;      // tile raster: GROUP_M row-tiles share a sweep over the column tiles
-static_assert(SEG_BLOCKS * BK * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
+constexpr int CHAIN_K = 1024;  // products per accumulation chain: 1024 * 127^2 = 16516096 < 2^24
+constexpr int GROUP_M = 8;     // tile raster: GROUP_M row-tiles share a sweep over the column tiles
+static_assert(CHAIN_K * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
 
-template <int BN_>
+// One pipeline stage holds SUB 64-wide k sub-tiles of A and of B (SK = 64 SUB k).  With
+// 128-wide tiles, two per stage (3 stages) give eight MMAs per barrier round trip instead of
+// four -- one lane issuing a 128 x 128 x 64 block is slower than the tensor core executing it
+// -- while one per stage (6 stages) hides more load latency (large s: bigger working sets).
+template <int BN_, int SUB_>
 struct Cfg {
   static constexpr int BN = BN_;
-  static constexpr int STAGES = BN_ == 256 ? 4 : 6;
-  static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN_ * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int SUB = SUB_;
+  static constexpr int SK = SUB * BK;
+  static constexpr int SEG = CHAIN_K / SK;  // stages per chain
+  static constexpr int STAGES = BN_ == 256 ? 4 : (SUB_ == 2 ? 3 : 6);
+  static constexpr uint32_t SUBA_BYTES = BM * BK * 2, SUBB_BYTES = BN_ * BK * 2;
+  static constexpr uint32_t A_BYTES = SUB * SUBA_BYTES, B_BYTES = SUB * SUBB_BYTES, STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr uint32_t IDESC = umma_idesc_f16_f32(BM, BN_);
   // two BN-column FP32 accumulators; 128-wide tiles also keep the int64 window words (two
   // columns per output) in the other half
@@ -68,6 +76,7 @@ struct TileJob {
   const CUtensorMap* tmA;
   const CUtensorMap* tmB;
   int tm, tn, KB, s, cplx, skip;
+  int klast;  // 64-wide sub-tiles holding valid k in the last stage (1 .. SUB)
   int64_t rows, cols, n;  // stacked product rows / cols, output columns (complex: n)
   const int32_t* e;
   const int32_t* f;
@@ -87,7 +96,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = r / gsz;
 }
 
-template <int BN_, bool GROUPED>
+template <int BN_, int SUB_, bool GROUPED>
 __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* P,
                                            const GroupArgs* G) {
   TileJob j;
@@ -96,7 +105,8 @@ __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const 
     tile_coords(t, tiles_m, tiles_n, j.tm, j.tn);
     j.tmA = tmA;
     j.tmB = tmB;
-    j.KB = (int)((P->k + BK - 1) / BK);
+    j.KB = (int)((P->k + Cfg<BN_, SUB_>::SK - 1) / Cfg<BN_, SUB_>::SK);
+    j.klast = (int)((P->k - (int64_t)(j.KB - 1) * Cfg<BN_, SUB_>::SK + BK - 1) / BK);
     j.s = P->s_dev != nullptr ? *P->s_dev : P->s;
     j.cplx = P->cplx;
     j.skip = 0;
@@ -123,7 +133,8 @@ __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const 
     j.tn = gt.tn;
     j.tmA = &c->tmA;
     j.tmB = &c->tmB;
-    j.KB = (int)((c->k + BK - 1) / BK);
+    j.KB = (int)((c->k + Cfg<BN_, SUB_>::SK - 1) / Cfg<BN_, SUB_>::SK);
+    j.klast = (int)((c->k - (int64_t)(j.KB - 1) * Cfg<BN_, SUB_>::SK + BK - 1) / BK);
     j.s = c->s;
     j.cplx = c->cplx;
     j.skip = (c->nonfinite != nullptr && *c->nonfinite) ? 1 : 0;
@@ -143,12 +154,13 @@ __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const 
   return j;
 }
 
-__device__ __forceinline__ int nseg_of(int g, int KB) { return ((g - 1) * KB + SEG_BLOCKS - 1) / SEG_BLOCKS; }
+__device__ __forceinline__ int nseg_of(int g, int KB, int seg) { return ((g - 1) * KB + seg - 1) / seg; }
 
+__device__ __noinline__ double ldexp_slow(double x, int E) { return ldexp(x, E); }
 // x * 2^E with one rounding (the same result as ldexp); fast path when 2^E is a normal double
 __device__ __forceinline__ double scale_pow2(double x, int E) {
   if (E >= -1022 && E <= 1023) return x * __longlong_as_double((long long)(E + 1023) << 52);
-  return ldexp(x, E);
+  return ldexp_slow(x, E);
 }
 
 // Exact epilogue (s <= kExactMaxS): R is a 128-bit integer per output, kept as (lo, hi) in 16
@@ -231,9 +243,8 @@ __device__ __forceinline__ double horner_step(void* Rp, int g, bool exact, bool 
 //   |window| < gmax * 128^(c-1) * 128/127 < 2^(L + 7 (c - 1) + 1)   =>   c = (62 - L) / 7 + 1.
 // Two windows form the exact 128-bit N = W0 128^len1 + W1, rounded to FP64 once with integer
 // instructions only; a third and later window continue in FP64 (one rounding per window).
-__device__ __forceinline__ int window_len(int s, int KB, int cplx) {
-  const unsigned long long gmax =
-      (unsigned long long)s * (unsigned long long)KB * (unsigned long long)BK * 16129ull * (cplx ? 2ull : 1ull);
+__device__ __forceinline__ int window_len(int s, int64_t kpad, int cplx) {
+  const unsigned long long gmax = (unsigned long long)s * (unsigned long long)kpad * 16129ull * (cplx ? 2ull : 1ull);
   const int L = 64 - __clzll((long long)gmax);
   const int c = (62 - L) / 7 + 1;
   return c < 1 ? 1 : c;
@@ -247,6 +258,8 @@ __device__ __forceinline__ void i128_shl_add(long long a, int sh, long long b, l
   hi += (b < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
   lo = nl;
 }
+
+__device__ __noinline__ double round_i128_slow(long long hi, unsigned long long lo, int E) { return round_i128(hi, lo, E); }
 
 // RN(N 2^E) for the 128-bit integer N = (hi, lo), built with integer instructions: normalise the
 // magnitude so its leading one is bit 127, keep 53 bits, round to nearest (ties to even) on the
@@ -281,7 +294,7 @@ __device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long 
     m >>= 1;
     ++x;
   }
-  if (x < -1022 || x > 1023) return round_i128(hi, lo, E);
+  if (x < -1022 || x > 1023) return round_i128_slow(hi, lo, E);
   const unsigned long long bits =
       (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(x + 1023) << 52) | (m & ((1ull << 52) - 1));
   return __longlong_as_double((long long)bits);
@@ -324,22 +337,42 @@ struct PushArgs {
   int ebase;
 };
 
-// One push for NCH consecutive outputs o0 .. o0+NCH-1 of this thread.  The active window lives
+// One push for NCH consecutive outputs o0 .. o0+NCH-1 of this thread; vals holds the chunk's
+// group sums (vals[i], complex: the pair vals[2i], vals[2i+1]).  The active window lives
 // in TMEM (TMR: two 32-bit columns per output, one 32x32b.x32 load and store per 16 outputs) or
 // in the CTA's L2-resident scratch (loads batched NCH deep before any use, to keep that many in
 // flight).  Complex: the (Re, Im) column pairs are combined exactly across the lane pair first.
-template <int NCH, bool TMR>
-__device__ __forceinline__ void push_chunk(const int* Gs, int o0, const PushArgs& a, const TileJob& j) {
+// The scratch words S0 and the column exponents a closing or final push of outputs
+// o0 .. o0+NCH-1 needs, loaded ahead of the push (software pipelining across chunks).
+template <int NCH>
+__device__ __forceinline__ void prefetch_close(const PushArgs& a, const TileJob& j, int o0, long long (&s0)[NCH],
+                                               int (&fe)[NCH]) {
+  if (a.widx >= 1) {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s0[i] = a.S0[(size_t)(o0 + i) * BM];
+  } else {
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) s0[i] = 0;
+  }
+  const int64_t c0 = j.cplx ? (a.gcol0 >> 1) + o0 : a.gcol0 + o0;
+  const int64_t climit = j.cplx ? j.n : j.cols;
+#pragma unroll
+  for (int i = 0; i < NCH; ++i) fe[i] = (a.kind == kFinal && c0 + i < climit) ? __ldg(j.f + c0 + i) : 0;
+}
+
+template <int NCH, bool TMR, bool PRE = false>
+__device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushArgs& a, const TileJob& j,
+                                           const long long* s0_pre = nullptr, const int* fe_pre = nullptr) {
   static_assert(!TMR || NCH == 16, "TMEM chunks are 32 columns");
   int vv[NCH];
   if (!j.cplx) {
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) vv[i] = Gs[o0 + i];
+    for (int i = 0; i < NCH; ++i) vv[i] = vals[i];
   } else {
 #pragma unroll
     for (int i = 0; i < NCH; ++i) {
-      const int other = __shfl_xor_sync(0xffffffffu, Gs[2 * (o0 + i) + 1], 1);
-      vv[i] = a.odd ? (Gs[2 * (o0 + i)] + other) : (Gs[2 * (o0 + i)] - other);
+      const int other = __shfl_xor_sync(0xffffffffu, vals[2 * i + 1], 1);
+      vv[i] = a.odd ? (vals[2 * i] + other) : (vals[2 * i] - other);
     }
   }
   long long rw[NCH];
@@ -383,24 +416,22 @@ __device__ __forceinline__ void push_chunk(const int* Gs, int o0, const PushArgs
     return;
   }
   long long s0[NCH];
-  if (a.widx >= 1) {
+  int fe[NCH];
+  if (PRE) {
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) s0[i] = a.S0[(size_t)(o0 + i) * BM];
+    for (int i = 0; i < NCH; ++i) {
+      s0[i] = s0_pre[i];
+      fe[i] = fe_pre[i];
+    }
   } else {
-#pragma unroll
-    for (int i = 0; i < NCH; ++i) s0[i] = 0;
+    prefetch_close<NCH>(a, j, o0, s0, fe);
   }
   if (a.kind == kClose) {
 #pragma unroll
     for (int i = 0; i < NCH; ++i) a.S0[(size_t)(o0 + i) * BM] = close_val(s0[i], rw[i], a.widx, a.wlen);
     return;
   }
-  // column exponents of the chunk, fetched together (one latency for the chunk)
-  int fe[NCH];
   const int64_t c0 = j.cplx ? (a.gcol0 >> 1) + o0 : a.gcol0 + o0;
-  const int64_t climit = j.cplx ? j.n : j.cols;
-#pragma unroll
-  for (int i = 0; i < NCH; ++i) fe[i] = c0 + i < climit ? __ldg(j.f + c0 + i) : 0;
   if (!j.cplx) {
 #pragma unroll
     for (int i = 0; i < NCH; ++i) {
@@ -446,10 +477,10 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-template <int BN_, bool GROUPED>
+template <int BN_, int SUB_, bool GROUPED>
 __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtensorMap* tmB0, const GemmArgs* P,
                                           const GroupArgs* G) {
-  using K = Cfg<BN_>;
+  using K = Cfg<BN_, SUB_>;
   constexpr int BN = BN_, STAGES = K::STAGES, CPT = K::CPT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -496,7 +527,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         long long issued = 0;
         const CUtensorMap* last_map = nullptr;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-          const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
+          const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
           if (j.skip) continue;
           if (GROUPED && j.tmA != last_map) {
             tensormap_acquire(j.tmA);
@@ -508,9 +539,15 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
               for (int p = 1; p < g; ++p) {
                 if (!mbar_wait(&bar_empty[stage], phase ^ 1, abort_p, status)) goto producer_done;
                 uint8_t* sA = smem + stage * K::STAGE_BYTES;
-                mbar_arrive_expect_tx(&bar_full[stage], K::STAGE_BYTES);
-                tma_load_3d(j.tmA, &bar_full[stage], sA, kb * BK, j.tm * BM, p - 1);
-                tma_load_3d(j.tmB, &bar_full[stage], sA + K::A_BYTES, kb * BK, j.tn * BN, g - p - 1);
+                const int nsub = kb == j.KB - 1 ? j.klast : K::SUB;  // an all-zero tail sub-tile is skipped
+                mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)nsub * (K::SUBA_BYTES + K::SUBB_BYTES));
+#pragma unroll
+                for (int h = 0; h < K::SUB; ++h)
+                  if (h < nsub) {
+                    tma_load_3d(j.tmA, &bar_full[stage], sA + h * K::SUBA_BYTES, kb * K::SK + h * BK, j.tm * BM, p - 1);
+                    tma_load_3d(j.tmB, &bar_full[stage], sA + K::A_BYTES + h * K::SUBB_BYTES, kb * K::SK + h * BK,
+                                j.tn * BN, g - p - 1);
+                  }
                 ++issued;
                 if (++stage == STAGES) {
                   stage = 0;
@@ -540,14 +577,15 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         uint32_t acc_par = 0;  // bit b: parity of the next use of TMEM buffer b
         int buf = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-          const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
+          const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
           if (j.skip) continue;
           for (int g = 2; g <= j.s + 1; ++g) {
             const int nblk = (g - 1) * j.KB;
             int b = 0;
             for (int kb = 0; kb < j.KB; ++kb)
               for (int p = 1; p < g; ++p) {
-                if (b % SEG_BLOCKS == 0) {
+                const bool chain_start = (b % K::SEG) == 0;
+                if (chain_start) {
                   if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, status)) goto mma_done;
                   tc_fence_after();
                 }
@@ -555,12 +593,18 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                 tc_fence_after();
                 {
                   uint8_t* sA = smem + stage * K::STAGE_BYTES;
-                  uint64_t da = umma_desc_sw128(sA), db = umma_desc_sw128(sA + K::A_BYTES);
-                  uint32_t dt = tmem + (uint32_t)(buf * BN);
+                  const int nsub = kb == j.KB - 1 ? j.klast : K::SUB;
+                  const uint32_t dt = tmem + (uint32_t)(buf * BN);
 #pragma unroll
-                  for (int q = 0; q < BK / 16; ++q)
-                    umma_f16(dt, da + (uint64_t)(2 * q), db + (uint64_t)(2 * q), K::IDESC,
-                             (b % SEG_BLOCKS != 0 || q != 0) ? 1u : 0u);
+                  for (int h = 0; h < K::SUB; ++h)
+                    if (h < nsub) {
+                      const uint64_t da = umma_desc_sw128(sA + h * K::SUBA_BYTES);
+                      const uint64_t db = umma_desc_sw128(sA + K::A_BYTES + h * K::SUBB_BYTES);
+#pragma unroll
+                      for (int q = 0; q < BK / 16; ++q)
+                        umma_f16(dt, da + (uint64_t)(2 * q), db + (uint64_t)(2 * q), K::IDESC,
+                                 (!chain_start || h != 0 || q != 0) ? 1u : 0u);
+                    }
                 }
                 umma_commit(&bar_empty[stage]);
                 if (++stage == STAGES) {
@@ -568,7 +612,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                   phase ^= 1;
                 }
                 ++b;
-                if (b % SEG_BLOCKS == 0 || b == nblk) {
+                if (b % K::SEG == 0 || b == nblk) {
                   umma_commit(&bar_accf[buf]);
                   acc_par ^= 1u << buf;
                   buf ^= 1;
@@ -607,7 +651,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     PushArgs pend;
     const bool odd = (lane & 1) != 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const TileJob j = get_job<BN_, GROUPED>(t, tmA0, tmB0, P, G);
+      const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
       if (j.skip) continue;
       const int s = j.s;
       const int push_segs = j.cplx ? 32 : 64;  // int32 group sums stay below 2^31
@@ -616,7 +660,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
       const int64_t orow = j.cplx ? (grow >> 1) : grow;
       const int e_row = (row_ok && j.e != nullptr) ? j.e[orow] : 0;
       const int64_t gcol0 = (int64_t)j.tn * BN + chalf * CPT;
-      const int win = window_len(s, j.KB, j.cplx);
+      const int win = window_len(s, (int64_t)j.KB * K::SK, j.cplx);
       const int nout = j.cplx ? CPT / 2 : CPT;  // outputs of this thread
       // scratch slots: S0 (first window, later the FP64 partial), S1 (windows 1, 2, ... when the
       // active window is not in TMEM)
@@ -640,7 +684,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         int Gr[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) Gr[c] = 0;
-        const int nseg = nseg_of(g, j.KB);
+        const int nseg = nseg_of(g, j.KB, K::SEG);
         bool first_push = true;
         for (int seg = 0; seg < nseg; ++seg) {
           if (!mbar_wait(&bar_accf[buf], (acc_par >> buf) & 1, abort_p, status)) goto epi_done;
@@ -666,7 +710,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           if (pend_o < pend_nout) {  // advance the pending push; complete it before the next one
             const int o1 = push_now ? pend_nout : min(pend_nout, pend_o + pend_chunk);
 #pragma unroll 1
-            for (int o = pend_o; o < o1; o += NCH) push_chunk<NCH, TMR>(Gs, o, pend, j);
+            for (int o = pend_o; o < o1; o += NCH) push_chunk<NCH, TMR>(Gs + (j.cplx ? 2 * o : o), o, pend, j);
             pend_o = o1;
           }
           if (!push_now) continue;
@@ -676,12 +720,21 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           pa.wstart = first_push && pos == 0;
           const bool win_end = group_end && pos == wlen - 1;
           pa.kind = final_push ? kFinal : !win_end ? kPlain : widx >= 1 ? kClose : TMR ? kSpill : kPlain;
-          if (TMR && !exact_now && Gdbg == nullptr && pa.kind != kFinal) {
-            // TMEM-resident windows: non-final pushes go straight from the registers (chunk offsets are
-            // compile-time constants, so Gr stays in registers)
+          if (TMR && !exact_now && Gdbg == nullptr) {
+            // TMEM-resident windows: every push goes straight from the registers.  The chunk
+            // loop stays rolled (small code); after each chunk the array is rotated by one
+            // chunk, so the chunk is always Gr[0 ..] and every index is a compile-time constant.
+            const int W = j.cplx ? 2 : 1;  // group sums per output
+#pragma unroll 1
+            for (int o = 0; o < nout; o += NCH) {
+              push_chunk<NCH, TMR>(Gr, o, pa, j);
 #pragma unroll
-            for (int o = 0; o < CPT; o += NCH)
-              if (o < nout) push_chunk<NCH, TMR>(Gr, o, pa, j);
+              for (int c = 0; c < CPT - NCH; ++c) Gr[c] = Gr[c + NCH];
+              if (W == 2) {
+#pragma unroll
+                for (int c = 0; c < CPT - NCH; ++c) Gr[c] = Gr[c + NCH];
+              }
+            }
 #pragma unroll
             for (int c = 0; c < CPT; ++c) Gr[c] = 0;
             first_push = false;
@@ -698,7 +751,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           }
           if (pa.kind == kPlain && !exact_now && Gdbg == nullptr) {
             // drains before the next push: the rest of this group, or the next group's chains
-            const int left = group_end ? nseg_of(g + 1, j.KB) : nseg - (seg + 1);
+            const int left = group_end ? nseg_of(g + 1, j.KB, K::SEG) : nseg - (seg + 1);
             const int drains = min(left, push_segs);
             if (defer_ok && drains >= 2) {
               pend = pa;
@@ -761,7 +814,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
             }
           } else {
 #pragma unroll 1
-            for (int o = 0; o < nout; o += NCH) push_chunk<NCH, TMR>(Gs, o, pa, j);
+            for (int o = 0; o < nout; o += NCH) push_chunk<NCH, TMR>(Gs + (j.cplx ? 2 * o : o), o, pa, j);
           }
           first_push = false;
         }
@@ -778,17 +831,17 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
   }
 }
 
-template <int BN_>
+template <int BN_, int SUB_>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const GemmArgs P) {
   if (P.nonfinite != nullptr && *P.nonfinite) return;  // the native FP64 kernel handles this call
-  gemm_body<BN_, false>(&tmA, &tmB, &P, nullptr);
+  gemm_body<BN_, SUB_, false>(&tmA, &tmB, &P, nullptr);
 }
 
-template <int BN_>
+template <int BN_, int SUB_>
 __global__ void __launch_bounds__(THREADS, 1) slice_gemm_grouped_kernel(const GroupArgs G) {
-  gemm_body<BN_, true>(nullptr, nullptr, nullptr, &G);
+  gemm_body<BN_, SUB_, true>(nullptr, nullptr, nullptr, &G);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -821,7 +874,7 @@ cudaError_t set_smem_once(Kern k, size_t bytes, bool& done) {
 int slice_gemm_tile_m() { return BM; }
 int slice_gemm_tile_n() { return 256; }
 int slice_gemm_tile_n_of(int variant) { return (variant & 1) ? 128 : 256; }
-size_t slice_gemm_smem_bytes() { return Cfg<256>::SMEM; }
+size_t slice_gemm_smem_bytes() { return Cfg<256, 1>::SMEM; }
 
 cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
                             int box_rows) {
@@ -837,43 +890,63 @@ cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t prepare_kernels() {
-  static bool d0 = false, d1 = false, d2 = false, d3 = false;
+namespace {
+// Kernel instance of a variant: bit 0 -> 128-wide tiles; bit 1 -> deferred pushes (256-wide,
+// a kernel argument) or one 64-wide k sub-tile per stage with a deeper pipeline (128-wide).
+template <bool GROUPED, int BN_, int SUB_>
+cudaError_t launch_one(const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* a, const GroupArgs* g,
+                       int grid, cudaStream_t st) {
+  using K = Cfg<BN_, SUB_>;
+  static bool done = false;
   cudaError_t e;
-  if ((e = set_smem_once(slice_gemm_kernel<256>, Cfg<256>::SMEM, d0)) != cudaSuccess) return e;
-  if ((e = set_smem_once(slice_gemm_kernel<128>, Cfg<128>::SMEM, d1)) != cudaSuccess) return e;
-  if ((e = set_smem_once(slice_gemm_grouped_kernel<256>, Cfg<256>::SMEM, d2)) != cudaSuccess) return e;
-  return set_smem_once(slice_gemm_grouped_kernel<128>, Cfg<128>::SMEM, d3);
+  if (GROUPED) {
+    if ((e = set_smem_once(slice_gemm_grouped_kernel<BN_, SUB_>, K::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_grouped_kernel<BN_, SUB_><<<grid, THREADS, K::SMEM, st>>>(*g);
+  } else {
+    if ((e = set_smem_once(slice_gemm_kernel<BN_, SUB_>, K::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_kernel<BN_, SUB_><<<grid, THREADS, K::SMEM, st>>>(*tmA, *tmB, *a);
+  }
+  return cudaGetLastError();
+}
+template <bool GROUPED>
+cudaError_t launch_variant(int variant, const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* a,
+                           const GroupArgs* g, int grid, cudaStream_t st) {
+  if (!(variant & 1)) return launch_one<GROUPED, 256, 1>(tmA, tmB, a, g, grid, st);
+  if (variant & 2) return launch_one<GROUPED, 128, 1>(tmA, tmB, a, g, grid, st);
+  return launch_one<GROUPED, 128, 2>(tmA, tmB, a, g, grid, st);
+}
+}  // namespace
+
+// Shared-memory opt-in for every kernel instance, once per process (outside any graph capture).
+cudaError_t prepare_kernels() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<256, 1>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_kernel<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<128, 1>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_kernel<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<128, 2>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_grouped_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<256, 1>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_grouped_kernel<128, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<128, 1>::SMEM)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(slice_gemm_grouped_kernel<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Cfg<128, 2>::SMEM);
 }
 
 cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& a, cudaStream_t st) {
   if (a.grid <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (a.variant & 1) {
-    static bool done = false;
-    if ((e = set_smem_once(slice_gemm_kernel<128>, Cfg<128>::SMEM, done)) != cudaSuccess) return e;
-    slice_gemm_kernel<128><<<a.grid, THREADS, Cfg<128>::SMEM, st>>>(tmA, tmB, a);
-  } else {
-    static bool done = false;
-    if ((e = set_smem_once(slice_gemm_kernel<256>, Cfg<256>::SMEM, done)) != cudaSuccess) return e;
-    slice_gemm_kernel<256><<<a.grid, THREADS, Cfg<256>::SMEM, st>>>(tmA, tmB, a);
-  }
-  return cudaGetLastError();
+  return launch_variant<false>(a.variant, &tmA, &tmB, &a, nullptr, a.grid, st);
 }
 
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st) {
   if (grid <= 0 || g.ntiles <= 0) return cudaSuccess;
-  cudaError_t e;
-  if (variant & 1) {
-    static bool done = false;
-    if ((e = set_smem_once(slice_gemm_grouped_kernel<128>, Cfg<128>::SMEM, done)) != cudaSuccess) return e;
-    slice_gemm_grouped_kernel<128><<<grid, THREADS, Cfg<128>::SMEM, st>>>(g);
-  } else {
-    static bool done = false;
-    if ((e = set_smem_once(slice_gemm_grouped_kernel<256>, Cfg<256>::SMEM, done)) != cudaSuccess) return e;
-    slice_gemm_grouped_kernel<256><<<grid, THREADS, Cfg<256>::SMEM, st>>>(g);
-  }
-  return cudaGetLastError();
+  return launch_variant<true>(variant, nullptr, nullptr, nullptr, &g, grid, st);
 }
 
 }  // namespace ozg

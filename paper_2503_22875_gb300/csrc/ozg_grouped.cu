@@ -105,7 +105,7 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   g.calls = gat<GroupCall>(c, P.oCalls);
   g.status = c->dflags;
   g.Rws = gat<double>(c, P.oR);
-  g.defer = (P.variant >> 1) & 1;
+  g.defer = variant_defers(P.variant);
   OZG_CUDA(launch_slice_gemm_grouped(g, P.variant, P.grid, st));
   OZG_CUDA(launch_native_batched(gat<NativeArgs>(c, P.oNative), P.ncalls, gat<const int*>(c, P.oFlagPtrs),
                                  gat<int>(c, P.oNList), gat<int64_t>(c, P.oNPre), gat<int64_t>(c, P.oNTot),
@@ -466,21 +466,26 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
   PhaseScope ps(c, OZG_PHASE_GROUPED);
   if (!reuse) {
     c->plan.reset();
-    // tile variant (width, deferred pushes): autotuned per batch when every call writes C without
-    // reading it (all variants give bit-identical results), else the padding heuristic summed
-    // over the batch, with deferred pushes when the work-weighted mean k is long
+    // tile variant: autotuned per batch when every call writes C without reading it (all
+    // variants give bit-identical results), else the padding heuristic summed over the batch;
+    // bit 1 from the work-weighted means of k (256-wide: deferred pushes for long k) and of s
+    // (128-wide: the deeper pipeline for s >= 10)
     int variant;
-    double pad0 = 0, pad1 = 0, wk = 0, w = 0;
+    double pad0 = 0, pad1 = 0, wk = 0, wsum = 0, w = 0;
     bool all_beta_zero = true;
     for (int64_t i = 0; i < n; ++i) {
       pad0 += (double)((work[i].m + 127) / 128) * ((work[i].n + 255) / 256) * 256 * ws[i] * ws[i];
       pad1 += (double)((work[i].m + 127) / 128) * ((work[i].n + 127) / 128) * 128 * ws[i] * ws[i];
       const double wi = (double)work[i].m * work[i].n * ws[i] * ws[i];
       wk += wi * work[i].k;
+      wsum += wi * ws[i];
       w += wi;
       all_beta_zero = all_beta_zero && work[i].beta == 0.0;
     }
-    variant = (pad1 < pad0 ? 1 : 0) | (w > 0 && wk >= 2048.0 * w ? 2 : 0);
+    if (pad1 < pad0)
+      variant = 1 | (w > 0 && wsum >= 10.0 * w ? 2 : 0);
+    else
+      variant = (w > 0 && wk >= 2048.0 * w) ? 2 : 0;
     auto tuned = c->tune.find(key);
     if (c->force_variant >= 0) {
       variant = c->force_variant;

@@ -114,13 +114,16 @@ void tune_store(ozg_ctx* c, uint64_t bucket, int variant) {
   out << std::hex << bucket << std::dec << " " << variant << "\n";
 }
 
-// Heuristic variant: the tile width that wastes the least output area (ties -> BN = 256), and
-// deferred epilogue pushes for long k (their pushes then overlap the next chains' MMAs; for
-// short k the epilogue is the bottleneck and immediate pushes measured faster).
-static int heuristic_variant(int64_t rows, int64_t cols, int64_t k) {
+// Heuristic variant: the tile width that wastes the least output area (ties -> 256 wide); for
+// 256-wide tiles deferred epilogue pushes when k >= 2048 (they then overlap the next chains'
+// MMAs; for short k the epilogue is the bottleneck and immediate pushes measured faster); for
+// 128-wide tiles the deeper pipeline (one 64-wide k sub-tile per stage) when s >= 10, whose
+// larger slice panels make load latency matter more than MMA issue overhead.
+static int heuristic_variant(int64_t rows, int64_t cols, int64_t k, int s) {
   (void)rows;
   const int64_t p256 = (cols + 255) / 256 * 256, p128 = (cols + 127) / 128 * 128;
-  return (p128 < p256 ? 1 : 0) | (k >= 2048 ? 2 : 0);
+  if (p128 < p256) return 1 | (s >= 10 ? 2 : 0);
+  return k >= 2048 ? 2 : 0;
 }
 
 int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s) {
@@ -128,7 +131,7 @@ int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s) {
   tune_load(c);
   auto it = c->tune.find(shape_bucket(rows, cols, k, s));
   if (it != c->tune.end()) return it->second;
-  return heuristic_variant(rows, cols, k);
+  return heuristic_variant(rows, cols, k, s);
 }
 
 }  // namespace host

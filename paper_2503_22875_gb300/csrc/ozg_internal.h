@@ -51,7 +51,8 @@ struct GemmArgs {
   int* status = nullptr;        // device status word (0 ok, 3 timeout)
   const int* nonfinite = nullptr;  // if non-null and set, the kernel exits (native path takes over)
   int grid = 0;                 // CTAs to launch (<= tiles); Rws must hold grid tiles
-  int variant = 0;              // bit 0: tile width (0 -> BN = 256, 1 -> BN = 128); bit 1: defer
+  int variant = 0;              // bit 0: 128-wide tiles; bit 1: deferred pushes (256-wide) or
+                                // one 64-wide k sub-tile per stage, 6 stages (128-wide)
   int defer = 0;                // 1: spread intermediate epilogue pushes over the next drains
   const int* s_dev = nullptr;   // if set, the slice count is read here (device-chosen); s = plane count
   int exact = 0;                // 1: exact 128-bit Horner sum and one rounding (s <= 13)
@@ -82,6 +83,8 @@ struct GroupArgs {
   int defer = 0;  // as GemmArgs::defer
 };
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st);
+// deferred epilogue pushes apply to 256-wide tiles only (128-wide tiles keep R in TMEM)
+inline int variant_defers(int variant) { return (variant & 3) == 2 ? 1 : 0; }
 // set the kernels' dynamic shared-memory limits (once per process, before any stream capture)
 cudaError_t prepare_kernels();
 int slice_gemm_tile_n_of(int variant);
