@@ -1,19 +1,28 @@
 #!/usr/bin/env python
-"""Benchmark: FP64-equivalent GEMM TFLOP/s of the INT8-slice emulated DGEMM at <= 1e-12
-componentwise error (relative to |A||B|) on one GB300, on the wide-exponent 8192^3 DGEMM
-workload (a = (u - 0.5) exp(phi g), phi = 0.5).
+"""Benchmark: FP64-equivalent GEMM TFLOP/s at <= 1e-12 componentwise error (relative to |A||B|)
+of learned-slice batched emulation against fixed-slice emulation, on one GB300.
 
-A step is one emulated DGEMM through the C ABI: split(A), split(B), the fused tensor-core
-slice GEMM + FP64 epilogue, and the sampled double-double error check of the result.  The
-slice count is the smallest s in 5..10 whose sampled error (GPU double-double check) is
-<= 1e-12; it is chosen once before timing.
+A step (the headline) is one ozg_dgemm_grouped call over a batch of 2048 uneven DGEMMs (m, n, k
+log-uniform in [32, 2048], entries (u - 0.5) exp(phi g), phi ~ U(0, 4) per call) with slices = 0:
+the learned selector (Sec. 4's adaptive split number) picks s per call for the 1e-12 target,
+the split, the tensor-core slice products with the fused epilogue and the sampled double-double
+check of every call run as one graph-replayed sequence of batched launches, and calls the
+check rejects are re-run at the fallback count.  value = sum of 2 m n k over the batch / the
+step time.
+
+Beside it, in the same JSON line: the fixed-slice baselines on the same batch (s = 7 issued one
+ozg_dgemm call at a time, and fixed counts in one grouped call, with the fraction of calls each
+meets 1e-12 on), the native FP64 kernel, the 8192^3 DGEMM slice sweep (phi in {0.5, 2, 4},
+s = 3..10, error and TFLOP/s per s), the KKR-like ZGEMM (n = 3616, s = 4..10), the roofline of
+the grouped slice-product kernel, the CPU oracle on a bounded sample, and an end-to-end number
+with the whole batch copied host -> device and the results device -> host in every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ozg|reference]
 
-Under torchrun each rank runs its own independent GEMM of the same size (independent problems,
-no data-path collective: weak scaling); value = total FP64-equivalent flops of all ranks / the
-slowest rank's time.  --impl reference times the CPU oracle's emulated DGEMM on a bounded
-sample of the same workload (rank 0 only).
+Under torchrun every rank runs its own batch of the same distribution (independent problems,
+no data-path collective: weak scaling); value = all ranks' flops / the slowest rank's time.
+--impl reference times the CPU oracle doing the same method (features, selector, emulated
+GEMM at the selected s) on a bounded sample of the batch (rank 0 only).
 """
 from __future__ import annotations
 
@@ -35,10 +44,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FP64-equiv GEMM TFLOP/s at ≤1e-12 rel err: learned+batched vs fixed-slice"
 TARGET_ERR = 1e-12
-M = N = K = 8192
-PHI = 0.5
-SEED = 2
+COUNT = 2048
+BATCH_SEED = 4
 CHECK_SAMPLES = 64
+FIXED_SWEEP = (7, 9, 10, 11, 12)
+SINGLE_PHIS = (0.5, 2.0, 4.0)
+SELECTOR_MODEL = os.path.join(ROOT, "paper_2503_22875_gb300", "data", "selector_v1.ozgsel")
 
 
 def parse():
@@ -47,12 +58,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ozg", choices=["ozg", "reference"])
-    ap.add_argument("--size", type=int, default=M)
-    ap.add_argument("--slices", type=int, default=0, help="0: smallest s meeting 1e-12 on the sampled check")
+    ap.add_argument("--count", type=int, default=COUNT, help="GEMMs in the batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-grouped", action="store_true", help="skip the grouped-batch comparison")
-    ap.add_argument("--grouped-count", type=int, default=2048)
-    ap.add_argument("--no-zgemm", action="store_true", help="skip the complex (KKR-like ZGEMM) section")
+    ap.add_argument("--no-compare", action="store_true", help="skip the fixed-slice and native comparisons")
+    ap.add_argument("--no-single", action="store_true", help="skip the 8192^3 slice sweep")
+    ap.add_argument("--single-size", type=int, default=8192)
+    ap.add_argument("--no-zgemm", action="store_true", help="skip the KKR-like ZGEMM section")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end number")
     return ap.parse_args()
 
 
@@ -70,10 +82,18 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def kernel_traffic(kernel: str, workload_tag: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None when the
-    summary is missing or was taken on a different version of the kernel source."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_tag}.md")
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("ozg_gemm.cu", "ozg_device.cuh", "ozg_internal.h"):
+        with open(os.path.join(ROOT, "paper_2503_22875_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(name: str):
+    """Per-launch DRAM bytes from the committed ncu summary profiles/<name>.md, or None when it is
+    missing or was taken on a different version of the kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -84,12 +104,19 @@ def kernel_traffic(kernel: str, workload_tag: str):
     return float(m.group(1))
 
 
-def source_hash():
-    h = hashlib.sha256()
-    for f in ("ozg_gemm.cu", "ozg_device.cuh", "ozg_internal.h"):
-        with open(os.path.join(ROOT, "paper_2503_22875_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()
+def tensor_roofline(kernel, flops, ms, traffic_name):
+    """Roofline of a slice-product kernel: algorithmic tensor flops (s(s+1)/2 FP16 products of
+    2 m n k each) over its CUDA-event duration, against the measured dense bf16 peak (FP16
+    operands run at the same nominal rate).  The burst peak: each timed launch lasts well under
+    a second and the sampled clocks stay at the maximum."""
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops")
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": kernel_traffic(traffic_name),
+            "peak_src": f"{src} bf16 burst (cuBLAS); sustained {peaks.get('bf16_tflops_sustained')}",
+            "frac_of_sustained": achieved / peaks.get("bf16_tflops_sustained", peak),
+            "tensor_flops_per_launch": flops, "launch_ms": ms}
 
 
 # ------------------------------------------------------------------------------------ clocks
@@ -139,129 +166,195 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------------------------ CPU baseline
-def cpu_baseline(A, B, s, rows=1536, cols=1024):
-    """The oracle's emulated DGEMM (as it stands) on a rows x cols block of the product (full k)."""
-    import numpy as np
+# ------------------------------------------------------------------------------------ CPU oracle
+def oracle_sample(count, budget_s):
+    """Calls of the batch taken in batch order while their estimated oracle time still fits
+    budget_s (same shapes, spreads and per-call seeds; numpy draws), at most 64."""
     import oracle
+    from paper_2503_22875_gb300 import selector, workloads
     oracle.build()
-    As = np.asfortranarray(A[:rows])
-    Bs = np.asfortranarray(B[:, :cols])
+    model = selector.read_model(SELECTOR_MODEL)
+    s_cap = max(model["s_lo"] + 10, model["fallback"])
+    rate = 3.0e9  # int64 MACs per second of the threaded oracle (order of magnitude, for the budget)
+    sample, est = [], 0.0
+    for c in workloads.grouped_batch(count, seed=BATCH_SEED):
+        cost = 60.0 * c.m * c.n * c.k / rate
+        if est + cost > budget_s:
+            continue
+        A, B = workloads.call_matrices(c)
+        sample.append((c, A, B))
+        est += cost
+        if len(sample) == 64:
+            break
+    return sample, model, s_cap
+
+
+def oracle_step(sample, model, s_cap):
+    """One pass of the method on the CPU oracle: features -> selector -> emulated GEMM."""
+    import oracle
     t0 = time.perf_counter()
-    oracle.dgemm_emu(As, Bs, s)
-    dt = time.perf_counter() - t0
-    k = A.shape[1]
-    return {"value": 2.0 * rows * cols * k / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(),
-            "kind": "oracle",
-            "sample": f"oracle emulated DGEMM (s={s}) of rows 0..{rows - 1} x cols 0..{cols - 1} of the "
-                      f"{A.shape[0]}x{B.shape[1]}x{k} product, full k; {dt:.2f} s",
-            "seconds": dt}
+    flops = 0.0
+    chosen = []
+    for c, A, B in sample:
+        f = oracle.features(A, B, TARGET_ERR)
+        s, _ = oracle.mlp_select(model, f, s_cap)
+        oracle.dgemm_emu(A, B, s)
+        flops += 2.0 * c.m * c.n * c.k
+        chosen.append(s)
+    return time.perf_counter() - t0, flops, chosen
+
+
+def cpu_baseline(count, budget_s=12.0):
+    import oracle
+    sample, model, s_cap = oracle_sample(count, budget_s)
+    dt, flops, chosen = oracle_step(sample, model, s_cap)
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"{len(sample)} GEMMs of the {count}-GEMM batch (taken in batch order while the estimated "
+                       f"time fits {budget_s:g} s; numpy draws of the same shapes and spreads, "
+                       f"{sum(2.0 * c.m * c.n * c.k for c, _, _ in sample) / 1e9:.1f} GFLOP): oracle features, "
+                       f"oracle selector (FP32 emulation of the same model), oracle emulated DGEMM at the selected s "
+                       f"(chosen {sorted(set(chosen))}); {dt:.1f} s")}
 
 
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    import numpy as np
-    from paper_2503_22875_gb300 import workloads
-    n = args.size
-    g = workloads.rng(SEED)
-    # the same distribution as the GPU arm; each step times a 96 x 96 block with full k = n
-    A = workloads.wide_exponent((96, n), PHI, g)
-    B = workloads.wide_exponent((n, 96), PHI, g)
-    s = args.slices or 7
+    import oracle
+    sample, model, s_cap = oracle_sample(args.count, 6.0)
     for _ in range(args.warmup):
-        cpu_baseline(A, B, s, 96, 96)
-    times = []
+        oracle_step(sample, model, s_cap)
+    tot_t, tot_f = 0.0, 0.0
     for _ in range(args.steps):
-        r = cpu_baseline(A, B, s, 96, 96)
-        times.append(r["seconds"])
-    ms = 1e3 * sum(times) / len(times)
-    val = 2.0 * 96 * 96 * n / (ms / 1e3) / 1e12
+        dt, fl, chosen = oracle_step(sample, model, s_cap)
+        tot_t += dt
+        tot_f += fl
+    val = tot_f / tot_t / 1e12
+    ms = 1e3 * tot_t / args.steps
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"emulated DGEMM {n}^3, wide-exponent phi={PHI}, s={s}; each step a 96x96 "
-                                   f"block of the product with full k (CPU oracle)", "m": n, "n": n, "k": n,
-                       "phi": PHI, "slices": s},
-            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": "96x96 block, full k, per step"},
+            "config": {"workload": f"learned-slice emulated DGEMM on {len(sample)} GEMMs of the "
+                                   f"{args.count}-GEMM batch (m,n,k log-uniform [32,2048], phi~U(0,4)), target "
+                                   f"{TARGET_ERR:g}; CPU oracle", "calls": len(sample), "target": TARGET_ERR},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": (f"{len(sample)} GEMMs of the batch per step (batch order, within a 6 s "
+                                        f"estimate), features + selector + emulated DGEMM")},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-# ------------------------------------------------------------------------------------ grouped batch
-SELECTOR_MODEL = os.path.join(ROOT, "paper_2503_22875_gb300", "data", "selector_v1.ozgsel")
-
-
-def grouped_section(ozg, torch, count, steps):
-    """2048 uneven GEMMs (m, n, k log-uniform in [32, 2048], phi ~ U(0, 4)) with target 1e-12:
-    fixed s = 7 one ozg_dgemm call at a time (the fixed-slice baseline), fixed counts in one grouped
-    graph-replayed ozg_dgemm_grouped call, and the learned selector (slices = 0) grouped.  The
-    error of every call is the GPU double-double check's estimate (64 samples)."""
-    from paper_2503_22875_gb300 import workloads
-    batch = workloads.grouped_batch_device(count)
-    st = torch.cuda.Stream()
-    Cs = [torch.empty((n, m), dtype=torch.float64, device="cuda") for m, n, k, _, _, _ in batch]
-    calls = [("N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m) for (m, n, k, _, A, B), C in zip(batch, Cs)]
-    flops = sum(2.0 * m * n * k for m, n, k, _, _, _ in batch)
+# ------------------------------------------------------------------------------------ helpers
+def timed(torch, st, fn, steps, warm=1):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(steps):
+            fn()
+        e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
 
-    def timed(fn):
-        with torch.cuda.stream(st):
-            fn()  # warm-up (and graph capture for grouped calls)
-            torch.cuda.synchronize()
-            e0.record(st)
-            for _ in range(steps):
-                fn()
-            e1.record(st)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        return {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
 
-    def errors(ctx, slices):
-        with torch.cuda.stream(st):
-            reps = ctx.dgemm_grouped(calls, slices, report=True)
-        return reps
+def report_stats(reps):
+    errs = np.array([r.est_err for r in reps], dtype=float)
+    used = [r.slices_used for r in reps]
+    return {"frac_le_target": float(np.mean(errs <= TARGET_ERR)), "max_err_sampled_dd": float(np.nanmax(errs)),
+            "slices_hist": {int(v): int(c) for v, c in zip(*np.unique(used, return_counts=True))}}
 
-    out = {"workload": (f"{count} DGEMMs, m,n,k log-uniform in [32, 2048], a=(u-0.5)exp(phi g), phi~U(0,4) per call, "
-                        f"beta=0; generated on the GPU (seeded torch generator); target 1e-12"),
-           "calls": count, "fp64_equiv_flops": flops}
+
+def tensor_flops(batch, slices):
+    return sum(s * (s + 1) / 2 * 2.0 * c.m * c.n * c.k for c, s in zip(batch.calls, slices))
+
+
+# ------------------------------------------------------------------------------------ comparisons
+def compare_section(ozg, torch, batch, calls, flops, st, steps):
+    """Fixed-slice baselines and the native FP64 kernel on the same batch."""
+    out = {}
+    n = len(calls)
     ctx = ozg.Context(stream=st)
-    out["fixed_s7_one_at_a_time"] = timed(lambda: [ctx.dgemm(*c, 7) for c in calls])
+    ms = timed(torch, st, lambda: [ctx.dgemm(*c, 7) for c in calls], max(1, min(steps, 2)))
+    ctx.set_check_samples(CHECK_SAMPLES)
+    with torch.cuda.stream(st):
+        reps = [ctx.dgemm(*c, 7, report=True) for c in calls]
+    out["fixed_s7_one_at_a_time"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, **report_stats(reps)}
     ctx.close()
     fixed = {}
-    for s in (7, 9, 11, 12, 14):
+    for s in FIXED_SWEEP:
         ctx = ozg.Context(stream=st)
-        r = timed(lambda: ctx.dgemm_grouped(calls, [s] * count))
-        ctx.set_check_samples(64)
-        reps = errors(ctx, [s] * count)
-        r["frac_le_target"] = sum(x.est_err <= TARGET_ERR for x in reps) / count
-        fixed[s] = r
+        ms = timed(torch, st, lambda: ctx.dgemm_grouped(calls, [s] * n), max(1, min(steps, 5)))
+        ctx.set_check_samples(CHECK_SAMPLES)
+        with torch.cuda.stream(st):
+            reps = ctx.dgemm_grouped(calls, [s] * n, report=True)
+        fixed[s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, **report_stats(reps)}
         ctx.close()
     out["fixed_grouped"] = fixed
-    ok = [s for s in fixed if fixed[s]["frac_le_target"] >= 0.99]
-    out["smallest_fixed_s_meeting_target_on_99pct"] = min(ok) if ok else None
-    if os.path.exists(SELECTOR_MODEL):
+    ok_all = [s for s in FIXED_SWEEP if fixed[s]["frac_le_target"] >= 1.0]
+    ok_99 = [s for s in FIXED_SWEEP if fixed[s]["frac_le_target"] >= 0.99]
+    out["smallest_fixed_s_meeting_target_on_all_calls"] = min(ok_all) if ok_all else None
+    out["smallest_fixed_s_meeting_target_on_99pct"] = min(ok_99) if ok_99 else None
+    ctx = ozg.Context(stream=st)
+    ms = timed(torch, st, lambda: [ctx.native_dgemm(*c) for c in calls], 1, warm=0)
+    out["native_fp64_one_at_a_time"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
+    ctx.close()
+    return out
+
+
+def single_section(ozg, torch, size, steps):
+    """Config 2: emulated DGEMM size^3, a = (u - 0.5) exp(phi g), phi in {0.5, 2, 4}, s = 3..10:
+    TFLOP/s and sampled double-double error per s, the native FP64 kernel, and the roofline of the
+    slice-product kernel at phi = 0.5 with the smallest s meeting 1e-12."""
+    n = size
+    st = torch.cuda.Stream()
+    gen = torch.Generator(device="cuda")
+    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    flops = 2.0 * n ** 3
+    out = {"workload": f"emulated DGEMM {n}^3, a=(u-0.5)exp(phi g), u~U(0,1), g~N(0,1); GPU-drawn (seeded)",
+           "by_phi": {}}
+    roof = None
+    for phi in SINGLE_PHIS:
+        gen.manual_seed(int(1000 * phi) + 2)
+
+        def draw():
+            u = torch.rand((n, n), generator=gen, device="cuda", dtype=torch.float64)
+            z = torch.randn((n, n), generator=gen, device="cuda", dtype=torch.float64)
+            return (u - 0.5) * torch.exp(phi * z)
+        dA, dB = draw(), draw()
         ctx = ozg.Context(stream=st)
-        ctx.load_selector(SELECTOR_MODEL)
-        ctx.set_target_error(TARGET_ERR)
-        r = timed(lambda: ctx.dgemm_grouped(calls, [0] * count))
-        reps = errors(ctx, [0] * count)
-        r["frac_le_target"] = sum(x.est_err <= TARGET_ERR for x in reps) / count
-        r["repaired"] = sum(x.repaired for x in reps)
-        r["selected_hist"] = {int(v): int(c) for v, c in zip(*np.unique([x.selected for x in reps], return_counts=True))}
-        r["fallback"] = max(x.slices_used for x in reps)
-        out["learned_grouped"] = r
-        base = out["fixed_s7_one_at_a_time"]["tflops"]
-        out["learned_vs_fixed_s7_one_at_a_time"] = r["tflops"] / base
-        if out["smallest_fixed_s_meeting_target_on_99pct"]:
-            out["learned_vs_smallest_sufficient_fixed_grouped"] = (
-                r["tflops"] / fixed[out["smallest_fixed_s_meeting_target_on_99pct"]]["tflops"])
+        res = {}
+        for s in range(3, 11):
+            ctx.set_check_samples(0)
+            ms = timed(torch, st, lambda: ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s),
+                       max(1, min(steps, 3)))
+            ctx.set_check_samples(CHECK_SAMPLES)
+            with torch.cuda.stream(st):
+                rep = ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s, report=True)
+            res[s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "err_sampled_dd": rep.est_err}
+        ok = [s for s in res if res[s]["err_sampled_dd"] <= TARGET_ERR]
+        entry = {"by_slices": res, "smallest_s_meeting_target": min(ok) if ok else None}
+        if phi == SINGLE_PHIS[0]:
+            s = entry["smallest_s_meeting_target"] or 7
+            ctx.set_check_samples(0)
+            ctx.set_profiling(True)
+            with torch.cuda.stream(st):
+                for _ in range(max(3, min(steps, 5))):
+                    ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s)
+            ph = ctx.phase_times()
+            ctx.set_profiling(False)
+            gemm_ms = ph["gemm"][0] / max(ph["gemm"][1], 1)
+            roof = tensor_roofline("slice_gemm_kernel", s * (s + 1) / 2 * flops, gemm_ms, f"slice_gemm_{n}_s{s}")
+            roof["slices"] = s
+            ms_nat = timed(torch, st, lambda: ctx.native_dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n), 1,
+                           warm=0)
+            entry["native_fp64_tflops"] = flops / (ms_nat / 1e3) / 1e12
+        out["by_phi"][phi] = entry
         ctx.close()
-    else:
-        out["learned_grouped"] = None
+        del dA, dB
+    out["roofline_phi0.5"] = roof
     return out
 
 
@@ -276,40 +369,27 @@ def zgemm_section(ozg, torch, steps):
     dC = torch.empty((n, n), dtype=torch.complex128, device="cuda")
     st = torch.cuda.Stream()
     ctx = ozg.Context(stream=st)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flops = 8.0 * n ** 3
     out = {"workload": f"KKR-like ZGEMM n={n} (113 blocks of 32), complex normal x exp(-|r_i - r_j|) + (1+0.1i) diag",
            "by_slices": {}}
     for s in range(4, 11):
+        ctx.set_check_samples(0)
+        ms = timed(torch, st, lambda: ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s), steps)
+        ctx.set_check_samples(CHECK_SAMPLES)
         with torch.cuda.stream(st):
-            ctx.set_check_samples(0)
-            ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s)
-            torch.cuda.synchronize()
-            e0.record(st)
-            for _ in range(steps):
-                ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s)
-            e1.record(st)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / steps
-            ctx.set_check_samples(64)
             rep = ctx.zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s, report=True)
         out["by_slices"][s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "err_sampled_dd": rep.est_err,
                                "max_real": rep.max_real, "max_imag": rep.max_imag}
     ok = [s for s, v in out["by_slices"].items() if v["err_sampled_dd"] <= TARGET_ERR]
     out["smallest_s_meeting_target"] = min(ok) if ok else None
-    with torch.cuda.stream(st):
-        e0.record(st)
-        ctx.native_zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n)
-        e1.record(st)
-        e1.synchronize()
-    out["native_fp64_tflops"] = flops / (e0.elapsed_time(e1) / 1e3) / 1e12
+    ms = timed(torch, st, lambda: ctx.native_zgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n), 1, warm=0)
+    out["native_fp64_tflops"] = flops / (ms / 1e3) / 1e12
     ctx.close()
     return out
 
 
 # ------------------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
-    import numpy as np
     import torch
 
     from paper_2503_22875_gb300 import build, ozg, workloads
@@ -323,149 +403,159 @@ def run_gpu(args):
         pg = dist
     build.build()
     ozg.load()
-    n = args.size
-    A, B = workloads.wide_exponent_pair(n, n, n, PHI, seed=SEED + rank)
+    batch = workloads.grouped_batch_flat(args.count, seed=BATCH_SEED + rank)
+    calls = batch.gemm_calls()
+    n = len(calls)
+    flops = sum(2.0 * c.m * c.n * c.k for c in batch.calls)
+    in_bytes = 8 * (batch.A.numel() + batch.B.numel())
     st = torch.cuda.Stream()
-    dA, dB = ozg.to_device(A), ozg.to_device(B)
-    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
-    ctx = ozg.Context(stream=st)
-    ctx.set_check_samples(CHECK_SAMPLES)
 
-    def step(s, report=False):
-        return ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s, report=report)
+    def learned_ctx():
+        c = ozg.Context(stream=st)
+        c.load_selector(SELECTOR_MODEL)
+        c.set_target_error(TARGET_ERR)
+        c.set_check_samples(CHECK_SAMPLES)
+        return c
 
-    # slice count for <= 1e-12 from the GPU's own sampled double-double check
-    chosen, errs = None, {}
-    for s in ([args.slices] if args.slices else range(5, 11)):
-        rep = step(s, report=True)
-        errs[s] = rep.est_err
-        if rep.est_err <= TARGET_ERR:
-            chosen = s
-            break
-    if chosen is None:
-        chosen = max(errs)
-    s = chosen
-    if pg is not None:  # every rank uses the largest s any rank needed
-        t = torch.tensor([s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        s = int(t.item())
-
-    for _ in range(args.warmup):
-        step(s)
-    ctx.sync()
-    ctx.set_profiling(True)
-    ctx.phase_times()  # reset
+    ctx = learned_ctx()
+    auto = [0] * n
+    with torch.cuda.stream(st):
+        ctx.dgemm_grouped(calls, auto)  # plan, digit workspace, graph capture
+        for _ in range(args.warmup):
+            ctx.dgemm_grouped(calls, auto)
+    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     if pg is not None:
         pg.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    l0 = ozg.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.steps):
-        step(s)
-    e1.record(st)
+    with torch.cuda.stream(st):
+        e0.record(st)
+        for _ in range(args.steps):
+            ctx.dgemm_grouped(calls, auto)
+        e1.record(st)
     e1.synchronize()
+    launches = ozg.kernel_launches() - l0
     clk = clocks.stop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    phases = ctx.phase_times()
-    ctx.set_profiling(False)
-    rep = step(s, report=True)
     ms_max = ms
     if pg is not None:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms_max = float(t.item())
-        pg.barrier()
-    flops = 2.0 * n * n * n
     value = flops * world / (ms_max / 1e3) / 1e12
-
-    # end-to-end through the C ABI with host buffers: H2D of A, B, the call, D2H of C
-    hA = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(A).T)).pin_memory()
-    hB = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(B).T)).pin_memory()
-    hC = torch.empty((n, n), dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, args.steps // 2)
     with torch.cuda.stream(st):
-        for it in range(1 + e2e_steps):
-            if it == 1:
-                torch.cuda.synchronize()
-                e0.record(st)
-            dA.copy_(hA, non_blocking=True)
-            dB.copy_(hB, non_blocking=True)
-            step(s)
-            hC.copy_(dC, non_blocking=True)
-        e1.record(st)
-    e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        reps = ctx.dgemm_grouped(calls, auto, report=True)
+    stats = report_stats(reps)
+    used = [r.slices_used for r in reps]
+    stats["selected_hist"] = {int(v): int(c) for v, c in zip(*np.unique([r.selected for r in reps],
+                                                                           return_counts=True))}
+    stats["repaired"] = int(sum(r.repaired for r in reps))
+    # tensor work of the step: every call at its selected count, plus the fallback re-runs
+    tflops_step = tensor_flops(batch, [r.selected for r in reps])
+    tflops_step += tensor_flops(batch, [u if r.repaired else 0 for r, u in zip(reps, used)])
+
+    # the slice-product kernel's own duration: the same step without the graph, CUDA events
+    # around each grouped GEMM launch on the launch stream
+    pctx = learned_ctx()
+    pctx.set_graphs(False)
+    with torch.cuda.stream(st):
+        pctx.dgemm_grouped(calls, auto)
+    pctx.set_profiling(True)
+    pctx.phase_times()
+    rsteps = max(3, min(args.steps, 5))
+    with torch.cuda.stream(st):
+        for _ in range(rsteps):
+            pctx.dgemm_grouped(calls, auto)
+    ph = pctx.phase_times()
+    pctx.close()
+    gemm_ms = ph["gemm"][0] / rsteps
+    grouped_ms_nograph = ph["grouped"][0] / max(ph["grouped"][1], 1)
+    roof = tensor_roofline("slice_gemm_grouped_kernel", tflops_step, gemm_ms, f"slice_gemm_grouped_learned_{n}")
+    roof["note"] = ("tensor flops = sum over calls of s(s+1)/2 * 2mnk at the selected s (plus fallback re-runs); "
+                    "launch_ms = the step's grouped GEMM launches, CUDA events, without the graph")
+
+    # end to end through the C ABI: the whole batch host -> device, the call, results -> host
+    e2e = None
+    if not args.no_e2e:
+        hA = torch.empty(batch.A.numel(), dtype=torch.float64, pin_memory=True)
+        hB = torch.empty(batch.B.numel(), dtype=torch.float64, pin_memory=True)
+        hC = torch.empty(batch.C.numel(), dtype=torch.float64, pin_memory=True)
+        hA.copy_(batch.A)
+        hB.copy_(batch.B)
+        e2e_steps = max(2, args.steps // 2)
+        with torch.cuda.stream(st):
+            for it in range(1 + e2e_steps):
+                if it == 1:
+                    torch.cuda.synchronize()
+                    e0.record(st)
+                batch.A.copy_(hA, non_blocking=True)
+                batch.B.copy_(hB, non_blocking=True)
+                ctx.dgemm_grouped(calls, auto)
+                hC.copy_(batch.C, non_blocking=True)
+            e1.record(st)
+        e1.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        if pg is not None:
+            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": flops * world / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * (batch.A.numel() + batch.B.numel()),
+               "d2h_bytes_per_step": 8 * batch.C.numel(), "ms_per_step": e2e_ms}
+        del hA, hB, hC
+    ctx.close()
     if pg is not None:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        pg.barrier()
 
     if rank != 0:
-        ctx.close()
         if pg is not None:
             pg.destroy_process_group()
         return 0
 
-    # native FP64 kernel on the same problem (one call, for the comparison)
-    ctx.set_check_samples(0)
-    tn0, tn1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tn0.record(st)
-    ctx.native_dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n)
-    tn1.record(st)
-    tn1.synchronize()
-    native_tflops = flops / (tn0.elapsed_time(tn1) / 1e3) / 1e12
+    compare = None
+    if not args.no_compare:
+        compare = compare_section(ozg, torch, batch, calls, flops, st, args.steps)
+        learned = value / world
+        compare["learned_vs_fixed_s7_one_at_a_time"] = learned / compare["fixed_s7_one_at_a_time"]["tflops"]
+        best = compare["smallest_fixed_s_meeting_target_on_all_calls"]
+        if best:
+            compare["learned_vs_smallest_sufficient_fixed_grouped"] = learned / compare["fixed_grouped"][best]["tflops"]
+        compare["learned_vs_native_fp64"] = learned / compare["native_fp64_one_at_a_time"]["tflops"]
+    del batch, calls
+    torch.cuda.empty_cache()
+    single = None if args.no_single else single_section(ozg, torch, args.single_size, args.steps)
+    zgemm = None if args.no_zgemm else zgemm_section(ozg, torch, max(1, min(args.steps, 3)))
+    cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(args.count)
 
-    zgemm = None
-    if not args.no_zgemm:
-        zgemm = zgemm_section(ozg, torch, max(1, min(args.steps, 3)))
-    grouped = None
-    if not args.no_grouped:
-        grouped = grouped_section(ozg, torch, args.grouped_count, max(1, min(args.steps, 5)))
-
-    peaks, peak_src = measured_peaks()
-    gemm_ms, gemm_n = phases["gemm"]
-    split_ms, split_n = phases["split"]
-    gemm_avg = gemm_ms / max(gemm_n, 1)
-    int_flops = s * (s + 1) / 2 * 2.0 * n * n * n  # slice-product tensor flops per launch
-    achieved = int_flops / (gemm_avg / 1e3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    traffic = kernel_traffic("slice_gemm", f"{n}_s{s}")
-    launches_per_step = 6 + 1  # rowmax x2, digits x2, slice GEMM, gated native, check
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(A, B, s)
-        cpu.pop("seconds", None)
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 (int8-range digits in fp16 on tcgen05, exact fp32 accumulation)",
+        "vs_baseline": None, "dtype": "f64 (int8-range digits in fp16 on tcgen05, exact integer accumulation)",
         "data": "synthetic",
-        "config": {"workload": f"emulated DGEMM {n}^3, wide-exponent a=(u-0.5)exp({PHI} g), fixed s={s} "
-                               f"(smallest s meeting 1e-12 on the sampled dd check), one call per step",
-                   "m": n, "n": n, "k": n, "phi": PHI, "slices": s, "check_samples": CHECK_SAMPLES,
-                   "l2": "inputs larger than L2 (537 MB per operand), no flush"},
-        "err_sampled_dd": rep.est_err, "err_by_slices": errs,
-        "phase_ms": {k: (v[0] / max(v[1], 1)) for k, v in phases.items() if v[1]},
-        "native_fp64_tflops": native_tflops,
-        "roofline": {"bound": "tensor", "kernel": "slice_gemm_kernel", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_src": f"{peak_src} bf16 sustained (fp16 operands, same nominal rate)",
-                     "flops_per_launch": int_flops},
+        "config": {"workload": (f"learned+batched: {n} DGEMMs (m,n,k log-uniform [32,2048], a=(u-0.5)exp(phi g), "
+                                f"phi~U(0,4) per call, beta=0), slices chosen per call by the selector MLP for "
+                                f"{TARGET_ERR:g}, one graph-replayed ozg_dgemm_grouped call per step"),
+                   "calls": n, "target": TARGET_ERR, "check_samples": CHECK_SAMPLES,
+                   "selector": os.path.relpath(SELECTOR_MODEL, ROOT),
+                   "l2": f"inputs larger than L2 ({in_bytes / 1e9:.1f} GB of A and B per batch), no flush"},
+        "accuracy": stats,
+        "grouped_ms_without_graph": grouped_ms_nograph,
+        "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": flops * world / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
-                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n},
-        "grouped_batch": grouped,
+        "e2e": e2e,
+        "compare": compare,
+        "single_dgemm": single,
         "zgemm_kkr": zgemm,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": launches,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
     if pg is not None:
         pg.destroy_process_group()
     return 0

@@ -228,6 +228,10 @@ int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
  * autotuned / heuristic choice.  Returns OZG_ERR_INVALID for other values. */
 int ozg_set_tile_variant(ozg_ctx* ctx, int variant);
 
+/* Kernel launches this library has issued in this process, written to *out (a replay of a
+ * captured grouped call counts every kernel it replays).  For launch accounting in benchmarks. */
+int ozg_kernel_launches(long long* out);
+
 /* ---- inspection entry points (used by the parity tests; same kernels as the GEMM path) ---- */
 
 /* Split the rows of op(X) (rows x k, real FP64, device) into exponents and digit planes, the
@@ -278,7 +282,8 @@ int ozg_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k,
 
 /* ---- per-phase device timing (CUDA events on the context's stream) ---- */
 #define OZG_PHASE_SPLIT 0    /* exponent + digit extraction of both operands */
-#define OZG_PHASE_GEMM 1     /* fused slice-product GEMM + epilogue */
+#define OZG_PHASE_GEMM 1     /* fused slice-product GEMM + epilogue (also each grouped GEMM launch
+                                of a grouped call issued without a graph) */
 #define OZG_PHASE_NATIVE 2   /* native FP64 kernel (native mode, or the gated non-finite path) */
 #define OZG_PHASE_CHECK 3    /* sampled double-double error check */
 #define OZG_PHASE_SELECT 4   /* learned slice selector */

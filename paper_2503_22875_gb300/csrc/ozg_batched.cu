@@ -104,46 +104,71 @@ __global__ void __launch_bounds__(256) rowmax_batched(const SplitArgs* jobs, con
   }
 }
 
-// Digits (real jobs: the grouped GEMM is real).  A unit is 32 rows x 64 k.  Thread t computes
-// row t/8 and the 8 consecutive k at (t%8)*8; strided jobs are staged (transposed) through
-// shared memory so that the global loads stay coalesced.
+// Digits (real jobs: the grouped GEMM is real).  A unit is 32 rows x kDgK k, walked as 64-wide
+// sub-tiles.  Thread t computes row t/8 and the 8 consecutive k at (t%8)*8 of a sub-tile;
+// strided jobs are staged (transposed) through shared memory so that global loads stay
+// coalesced.  The loads of the next sub-tile are issued before the current one is processed.
 __global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, const int2* units) {
   __shared__ uint64_t tile[64][33];
   const int2 ur = units[blockIdx.x];
+  {
+    const int* gate = jobs[ur.x].gate;
+    if (gate != nullptr && *gate) return;
+  }
   const SplitArgs J = jobs[ur.x];
+  const int t_lo = J.plane_from != nullptr ? *J.plane_from + 1 : 1;
+  const int t_hi = J.plane_to != nullptr ? *J.plane_to : J.s;
+  if (t_lo > t_hi) return;
   const int64_t u = ur.y;
-  const int64_t ltiles = (J.k + 63) / 64;
-  const int64_t r0 = (u / ltiles) * 32, l0 = (u % ltiles) * 64;
+  const int64_t ktiles = (J.k + kDgK - 1) / kDgK;
+  const int64_t r0 = (u / ktiles) * 32, lbase = (u % ktiles) * kDgK;
   const int tid = threadIdx.x;
   const int r = tid / 8, lg = (tid % 8) * 8;
   const int64_t row = r0 + r;
+  const bool row_ok = row < J.rows;
   const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
-  uint64_t b[8];
-  if (J.strided) {
-    const int rr = tid % 32;
-    const bool rok = r0 + rr < J.rows;
+  const int e = row_ok ? exponent_from_maxbits(J.maxbits[row]) : 0;
+  if (row_ok && lbase == 0 && lg == 0 && t_lo == 1) J.exps[row] = e;
+  const int64_t plane = J.plane_rows * J.Kp;
+  const int rr = tid % 32;
+  const bool rrok = r0 + rr < J.rows;
+  uint64_t nx[8];
+  auto load = [&](int64_t l0) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int li = tid / 32 + 8 * q;
-      tile[li][rr] = (rok && l0 + li < J.k) ? __ldg(X + (r0 + rr) + (l0 + li) * J.ld) : 0ull;
+      if (J.strided) {
+        const int64_t l = l0 + tid / 32 + 8 * q;
+        nx[q] = (rrok && l < J.k) ? __ldg(X + (r0 + rr) + l * J.ld) : 0ull;
+      } else {
+        const int64_t l = l0 + lg + q;
+        nx[q] = (row_ok && l < J.k) ? __ldg(X + row * J.ld + l) : 0ull;
+      }
     }
-    __syncthreads();
+  };
+  load(lbase);
+  for (int sub = 0; sub < kDgK / 64; ++sub) {
+    const int64_t l0 = lbase + 64 * sub;
+    if (l0 >= J.k) break;
+    uint64_t b[8];
+    if (J.strided) {
+      __syncthreads();  // the previous sub-tile's reads of the tile are done
 #pragma unroll
-    for (int q = 0; q < 8; ++q) b[q] = tile[lg + q][r];
-  } else {
-    const bool rok = row < J.rows;
+      for (int q = 0; q < 8; ++q) tile[tid / 32 + 8 * q][rr] = nx[q];
+      __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 8; ++q) b[q] = (rok && l0 + lg + q < J.k) ? __ldg(X + row * J.ld + l0 + lg + q) : 0ull;
+      for (int q = 0; q < 8; ++q) b[q] = tile[lg + q][r];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) b[q] = nx[q];
+    }
+    if (sub + 1 < kDgK / 64 && l0 + 64 < J.k) load(l0 + 64);
+    if (!row_ok || l0 + lg >= J.k) continue;
+    DigitSrc ds[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ds[q] = digit_src(b[q], e);
+    __half* out = J.D + row * J.Kp + l0 + lg;
+    for (int t = t_lo; t <= t_hi; ++t) *reinterpret_cast<uint4*>(out + (int64_t)(t - 1) * plane) = digits8(ds, t);
   }
-  if (row >= J.rows || l0 + lg >= J.k) return;
-  const int e = exponent_from_maxbits(J.maxbits[row]);
-  if (l0 + lg == 0) J.exps[row] = e;
-  DigitSrc ds[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) ds[q] = digit_src(b[q], e);
-  __half* out = J.D + row * J.Kp + l0 + lg;
-  const int64_t plane = J.plane_rows * J.Kp;
-  for (int t = 1; t <= J.s; ++t) *reinterpret_cast<uint4*>(out + (int64_t)(t - 1) * plane) = digits8(ds, t);
 }
 
 // ---------------------------------------------------------------------------- native fallback
@@ -241,31 +266,41 @@ __global__ void save_restore_batched(const RepairJob* jobs, const int64_t* prefi
 
 cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  repair_prep_batched<<<(njobs + 127) / 128, 128, 0, st>>>(jobs_dev, njobs, target);
+  { repair_prep_batched<<<(njobs + 127) / 128, 128, 0, st>>>(jobs_dev, njobs, target); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_save_restore_batched(const RepairJob* jobs_dev, const int64_t* prefix_dev, int64_t units,
                                         int njobs, int restore, cudaStream_t st) {
   if (units <= 0 || njobs <= 0) return cudaSuccess;
-  save_restore_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, prefix_dev, njobs, restore);
+  { save_restore_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, prefix_dev, njobs, restore); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rowmax_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st) {
+  if (units > 0) { rowmax_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, units_dev); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st) {
+  if (units > 0) { digits_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, units_dev); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t rowmax_units,
                                  const int2* digit_units_dev, int64_t digit_units, cudaStream_t st) {
-  if (rowmax_units > 0) rowmax_batched<<<(unsigned)rowmax_units, 256, 0, st>>>(jobs_dev, rowmax_units_dev);
+  if (rowmax_units > 0) { rowmax_batched<<<(unsigned)rowmax_units, 256, 0, st>>>(jobs_dev, rowmax_units_dev); note_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (digit_units > 0) digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_units_dev);
+  if (digit_units > 0) { digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_units_dev); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_native_batched(const NativeArgs* calls_dev, int ncalls, const int* const* flags_dev, int* list_dev,
                                   int64_t* prefix_dev, int64_t* total_dev, int grid, cudaStream_t st) {
   if (ncalls <= 0) return cudaSuccess;
-  native_compact<<<1, 32, 0, st>>>(calls_dev, ncalls, flags_dev, list_dev, prefix_dev, total_dev);
-  native_batched<<<grid, 256, 0, st>>>(calls_dev, list_dev, prefix_dev, total_dev);
+  { native_compact<<<1, 32, 0, st>>>(calls_dev, ncalls, flags_dev, list_dev, prefix_dev, total_dev); note_launch(); }
+  { native_batched<<<grid, 256, 0, st>>>(calls_dev, list_dev, prefix_dev, total_dev); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -82,29 +82,66 @@ __global__ void check_pre(CheckArgs P) {
   }
 }
 
+// Compensated dot product (Dot2 of Ogita, Rump and Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26, 2005): the running sum s is updated by TwoSum with the exact product
+// error from TwoProd, and both rounding errors go into one plain-double correction c.  The result
+// s + c is as accurate as the dot product computed in twice the working precision and then
+// rounded, at about half the FP64 operations of a full double-double accumulation.
+struct dot2 {
+  double s, c;
+};
+__device__ __forceinline__ void dot2_add(dot2& a, double x, double y) {
+  const double p = x * y;
+  const double pe = fma(x, y, -p);
+  const double t = a.s + p;
+  const double z = t - a.s;
+  const double se = (a.s - (t - z)) + (p - z);
+  a.s = t;
+  a.c += se + pe;
+}
+__device__ __forceinline__ dd dot2_reduce_warp(dot2 a) {
+  // pairwise: TwoSum of the partial sums, the corrections added plainly
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double os = __shfl_xor_sync(0xffffffffu, a.s, o), oc = __shfl_xor_sync(0xffffffffu, a.c, o);
+    const dd t = two_sum(a.s, os);
+    a.s = t.hi;
+    a.c = a.c + oc + t.lo;
+  }
+  return fast_two_sum(a.s, a.c);
+}
+
 __device__ void check_one(const CheckArgs& P, int sample, int lane, double* err_slot) {
   int64_t i, j;
   sample_ij(P, sample, i, j);
   dd re = {0, 0}, im = {0, 0};
   double sabs = 0.0;
-  for (int64_t l = lane; l < P.k; l += 32) {
+  if (!P.cplx) {
+    dot2 acc = {0.0, 0.0};
+    for (int64_t l = lane; l < P.k; l += 32) {
+      const double ar = (P.ta == 'N') ? P.A[i + l * P.lda] : P.A[l + i * P.lda];
+      const double br = (P.tb == 'N') ? P.B[l + j * P.ldb] : P.B[j + l * P.ldb];
+      dot2_add(acc, ar, br);
+      sabs = fma(fabs(ar), fabs(br), sabs);
+    }
+    re = dot2_reduce_warp(acc);
+  }
+  for (int64_t l = lane; P.cplx && l < P.k; l += 32) {
     double ai = 0, bi = 0;
     const double ar = ld_op(P.A, P.lda, P.ta, i, l, P.cplx, &ai);
     const double br = ld_op(P.B, P.ldb, P.tb, l, j, P.cplx, &bi);
     re = dd_add_prod(re, ar, br);
-    if (P.cplx) {
-      re = dd_add_prod(re, -ai, bi);
-      im = dd_add_prod(im, ar, bi);
-      im = dd_add_prod(im, ai, br);
-      sabs += (fabs(ar) + fabs(ai)) * (fabs(br) + fabs(bi));
-    } else {
-      sabs += fabs(ar) * fabs(br);
-    }
+    re = dd_add_prod(re, -ai, bi);
+    im = dd_add_prod(im, ar, bi);
+    im = dd_add_prod(im, ai, br);
+    sabs += (fabs(ar) + fabs(ai)) * (fabs(br) + fabs(bi));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    re = dd_add(re, dd_shfl_xor(re, o));
-    im = dd_add(im, dd_shfl_xor(im, o));
+    if (P.cplx) {
+      re = dd_add(re, dd_shfl_xor(re, o));
+      im = dd_add(im, dd_shfl_xor(im, o));
+    }
     sabs += __shfl_xor_sync(0xffffffffu, sabs, o);
   }
   if (lane != 0) return;
@@ -162,9 +199,12 @@ __global__ void check_post(CheckArgs P) {
 __global__ void check_pre_batched(const CheckArgs* calls, int ncalls, int nsamp) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)ncalls * nsamp) return;
-  const CheckArgs P = calls[idx / nsamp];
+  const CheckArgs* Pp = calls + idx / nsamp;
+  if (Pp->beta_zero) return;
+  const int* gate = Pp->gate;
+  if (gate != nullptr && *gate) return;
+  const CheckArgs P = *Pp;
   const int smp = (int)(idx % nsamp);
-  if (P.beta_zero || (P.gate != nullptr && *P.gate)) return;
   int64_t i, j;
   sample_ij(P, smp, i, j);
   P.cold[2 * smp] = P.C[i + j * P.ldc];
@@ -175,8 +215,10 @@ __global__ void check_post_batched(const CheckArgs* calls, int ncalls, int nsamp
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= (int64_t)ncalls * nsamp) return;
-  const CheckArgs P = calls[warp / nsamp];
-  if (P.gate != nullptr && *P.gate) return;
+  const CheckArgs* Pp = calls + warp / nsamp;
+  const int* gate = Pp->gate;  // read the gate before anything else (most re-run checks skip)
+  if (gate != nullptr && *gate) return;
+  const CheckArgs P = *Pp;
   check_one(P, (int)(warp % nsamp), lane, P.err_out);
 }
 
@@ -184,14 +226,14 @@ __global__ void check_post_batched(const CheckArgs* calls, int ncalls, int nsamp
 
 cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st) {
   if (a.nsamp <= 0 || a.beta_zero) return cudaSuccess;
-  check_pre<<<(a.nsamp + 127) / 128, 128, 0, st>>>(a);
+  { check_pre<<<(a.nsamp + 127) / 128, 128, 0, st>>>(a); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_check_batched_pre(const CheckArgs* calls_dev, int ncalls, int nsamp, cudaStream_t st) {
   const int64_t total = (int64_t)ncalls * nsamp;
   if (total <= 0) return cudaSuccess;
-  check_pre_batched<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(calls_dev, ncalls, nsamp);
+  { check_pre_batched<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(calls_dev, ncalls, nsamp); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -201,7 +243,7 @@ cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, in
   if (total <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(errs_dev, 0, sizeof(double) * ncalls, st);
   if (e != cudaSuccess) return e;
-  check_post_batched<<<(unsigned)((total + 3) / 4), 128, 0, st>>>(calls_dev, ncalls, nsamp);
+  { check_post_batched<<<(unsigned)((total + 3) / 4), 128, 0, st>>>(calls_dev, ncalls, nsamp); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -211,7 +253,7 @@ cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st) {
   if (e == cudaSuccess && a.part_err != nullptr) e = cudaMemsetAsync(a.part_err, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int warps_per_block = 4;
-  check_post<<<(a.nsamp + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(a);
+  { check_post<<<(a.nsamp + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(a); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -261,10 +261,11 @@ __device__ __forceinline__ void i128_shl_add(long long a, int sh, long long b, l
 
 __device__ __noinline__ double round_i128_slow(long long hi, unsigned long long lo, int E) { return round_i128(hi, lo, E); }
 
-// RN(N 2^E) for the 128-bit integer N = (hi, lo), built with integer instructions: normalise the
-// magnitude so its leading one is bit 127, keep 53 bits, round to nearest (ties to even) on the
-// guard bit and the sticky OR of the rest, and assemble sign, biased exponent and fraction.
-// Results outside the normal range take the conversion-based path.
+// RN(N 2^E) for the 128-bit integer N = (hi, lo), |N| < 2^126: the magnitude's top 64 bits with
+// a sticky bit for everything below are converted with one correctly rounded conversion (the
+// sticky bit sits below the guard bit, so the rounding is that of N itself), and the power of
+// two is applied by adding to the exponent field.  Results outside the normal range take the
+// general path.
 __device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long lo, int E) {
   const bool neg = hi < 0;
   unsigned long long mh = (unsigned long long)hi, ml = lo;
@@ -272,32 +273,23 @@ __device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long 
     ml = ~ml + 1;
     mh = ~mh + (ml == 0 ? 1 : 0);
   }
-  if ((mh | ml) == 0) return 0.0;
-  const int lz = mh != 0 ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
-  unsigned long long nh, nl;
-  if (lz == 0) {
-    nh = mh;
-    nl = ml;
-  } else if (lz < 64) {
-    nh = (mh << lz) | (ml >> (64 - lz));
-    nl = ml << lz;
+  double mag;
+  int sh = 0;
+  if (mh == 0) {
+    if (ml == 0) return 0.0;
+    mag = __ull2double_rn(ml);
   } else {
-    nh = ml << (lz - 64);
-    nl = 0;
+    sh = 64 - __clzll((long long)mh);  // 1 .. 62 for |N| < 2^126
+    if (sh >= 64) return round_i128_slow(hi, lo, E);
+    const unsigned long long top = (mh << (64 - sh)) | (ml >> sh);
+    const unsigned long long sticky = (ml << (64 - sh)) != 0 ? 1ull : 0ull;
+    mag = __ull2double_rn(top | sticky);
   }
-  unsigned long long m = nh >> 11;  // 53 bits, leading one at bit 52
-  const unsigned long long guard = (nh >> 10) & 1ull;
-  const bool sticky = (nh & 0x3FFull) != 0 || nl != 0;
-  int x = (127 - lz) + E;  // N 2^E lies in [2^x, 2^(x+1))
-  m += (guard != 0 && (sticky || (m & 1ull))) ? 1ull : 0ull;
-  if (m == (1ull << 53)) {
-    m >>= 1;
-    ++x;
-  }
-  if (x < -1022 || x > 1023) return round_i128_slow(hi, lo, E);
-  const unsigned long long bits =
-      (neg ? (1ull << 63) : 0ull) | ((unsigned long long)(x + 1023) << 52) | (m & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
+  const long long bits = __double_as_longlong(mag);
+  const int ex = (int)(bits >> 52) + E + sh;  // biased exponent of the result
+  if (ex < 1 || ex > 2046) return round_i128_slow(hi, lo, E);
+  const long long r = bits + ((long long)(E + sh) << 52);
+  return __longlong_as_double(neg ? (r | (long long)0x8000000000000000ull) : r);
 }
 
 // Window-closing or final step of one output, given the first slot's word s0 (int64 W0 while
@@ -901,10 +893,10 @@ cudaError_t launch_one(const CUtensorMap* tmA, const CUtensorMap* tmB, const Gem
   cudaError_t e;
   if (GROUPED) {
     if ((e = set_smem_once(slice_gemm_grouped_kernel<BN_, SUB_>, K::SMEM, done)) != cudaSuccess) return e;
-    slice_gemm_grouped_kernel<BN_, SUB_><<<grid, THREADS, K::SMEM, st>>>(*g);
+    { slice_gemm_grouped_kernel<BN_, SUB_><<<grid, THREADS, K::SMEM, st>>>(*g); note_launch(); }
   } else {
     if ((e = set_smem_once(slice_gemm_kernel<BN_, SUB_>, K::SMEM, done)) != cudaSuccess) return e;
-    slice_gemm_kernel<BN_, SUB_><<<grid, THREADS, K::SMEM, st>>>(*tmA, *tmB, *a);
+    { slice_gemm_kernel<BN_, SUB_><<<grid, THREADS, K::SMEM, st>>>(*tmA, *tmB, *a); note_launch(); }
   }
   return cudaGetLastError();
 }

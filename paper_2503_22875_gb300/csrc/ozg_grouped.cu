@@ -20,6 +20,7 @@ namespace host {
 struct GroupPlan {
   uint64_t key = 0, epoch = 0;
   int ncalls = 0, nsamp = 0, variant = 0, grid = 0, njobs = 0, ntiles = 0;
+  long long nkernels = 0;  // kernels one replay of the captured graph launches
   int64_t rowmax_units = 0, digit_units = 0;
   cudaGraphExec_t exec = nullptr;
   size_t oFlags = 0, flags_bytes = 0, oMax = 0, max_bytes = 0;
@@ -30,7 +31,7 @@ struct GroupPlan {
   int any_auto = 0, s_fb = 0;
   int64_t save_units = 0;
   size_t oHist = 0, hist_bytes = 0, oSel = 0, oSused = 0, oRep = 0, oSavePre = 0, oSaved = 0;
-  size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0;
+  size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0, oJobs2 = 0;
   std::vector<char> autom;
 };
 
@@ -89,12 +90,16 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oFlags), 0, P.flags_bytes, st));
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
-  OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units,
-                                gat<int2>(c, P.oDgTab), P.digit_units, st));
-  if (P.any_auto) {
+  if (!P.any_auto) {
+    OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units,
+                                  gat<int2>(c, P.oDgTab), P.digit_units, st));
+  } else {
+    // row maxima -> features -> selection -> digits up to each call's selected count
+    OZG_CUDA(launch_rowmax_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units, st));
     OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
     OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, st));
     OZG_CUDA(launch_select_batched(c->dsel, gat<SelectJob>(c, P.oSel), P.ncalls, (float)std::log10(c->target), st));
+    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, st));
     OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
                                          P.ncalls, 0, st));
   }
@@ -106,7 +111,10 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   g.status = c->dflags;
   g.Rws = gat<double>(c, P.oR);
   g.defer = variant_defers(P.variant);
-  OZG_CUDA(launch_slice_gemm_grouped(g, P.variant, P.grid, st));
+  {
+    PhaseScope ps(c, OZG_PHASE_GEMM);
+    OZG_CUDA(launch_slice_gemm_grouped(g, P.variant, P.grid, st));
+  }
   OZG_CUDA(launch_native_batched(gat<NativeArgs>(c, P.oNative), P.ncalls, gat<const int*>(c, P.oFlagPtrs),
                                  gat<int>(c, P.oNList), gat<int64_t>(c, P.oNPre), gat<int64_t>(c, P.oNTot),
                                  2 * c->num_sms, st));
@@ -116,9 +124,13 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
     OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, P.oRep), P.ncalls, c->target, st));
     OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
                                          P.ncalls, 1, st));
+    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs2), gat<int2>(c, P.oDgTab), P.digit_units, st));
     GroupArgs g2 = g;
     g2.calls = gat<GroupCall>(c, P.oCalls2);
-    OZG_CUDA(launch_slice_gemm_grouped(g2, P.variant, P.grid, st));
+    {
+      PhaseScope ps(c, OZG_PHASE_GEMM);
+      OZG_CUDA(launch_slice_gemm_grouped(g2, P.variant, P.grid, st));
+    }
     OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, P.oChecks2), P.ncalls, P.nsamp, gat<double>(c, P.oErrs2),
                                        st));
   }
@@ -226,6 +238,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     P->oChecks2 = cv.take(sizeof(CheckArgs) * count);
     P->oErrs2 = cv.take(sizeof(double) * count);
     P->oSkip2 = cv.take(sizeof(int) * count);
+    P->oJobs2 = cv.take(sizeof(SplitArgs) * 2 * count);
     for (int64_t i = 0; i < count; ++i) {
       const bool sv = autom[i] && d[i].beta != 0.0;
       sp[i + 1] = sp[i] + (sv ? (d[i].m * d[i].n + 255) / 256 : 0);
@@ -269,9 +282,13 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     b.maxbits = gat<unsigned long long>(c, oMB[i]);
     b.exps = gat<int32_t>(c, oEB[i]);
     b.hist = autom[i] ? gat<unsigned long long>(c, P->oHist) + 20 * i + 10 : nullptr;
+    if (autom[i]) {  // digits only up to the count the selector writes into the call's slot
+      const int* sel = &gat<GroupCall>(c, P->oCalls)[i].s;
+      a.plane_to = sel;
+      b.plane_to = sel;
+    }
     jobs[2 * i] = a;
     jobs[2 * i + 1] = b;
-    // units: rows per rowmax unit 256 (strided) / 8 (contiguous); digit tiles 32 x 64
 
     GroupCall& g = calls[i];
     OZG_CUDA(make_digit_tmap(&g.tmA, a.D, d[i].k, d[i].m, Kp, planes[i], 128));
@@ -373,6 +390,21 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->digit_units = (int64_t)dgtab.size();
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs), jobs.data(), sizeof(SplitArgs) * jobs.size(), cudaMemcpyHostToDevice, st));
+  std::vector<SplitArgs> jobs2;
+  if (any_auto) {
+    // completion of the digit planes for calls the check rejects: planes (selected, fallback]
+    jobs2 = jobs;
+    for (int64_t i = 0; i < count; ++i)
+      for (int side = 0; side < 2; ++side) {
+        SplitArgs& x = jobs2[2 * i + side];
+        x.plane_from = &gat<GroupCall>(c, P->oCalls)[i].s;
+        x.plane_to = &gat<GroupCall>(c, P->oCalls2)[i].s;
+        x.gate = gat<int>(c, P->oSkip2) + i;  // 1 unless the call is re-run
+        x.hist = nullptr;
+      }
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs2), jobs2.data(), sizeof(SplitArgs) * jobs2.size(),
+                             cudaMemcpyHostToDevice, st));
+  }
   if (!rmtab.empty())
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oRmTab), rmtab.data(), sizeof(int2) * rmtab.size(), cudaMemcpyHostToDevice,
                              st));
@@ -524,7 +556,10 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     if (c->graphs && c->stream != nullptr) {
       cudaGraph_t graph = nullptr;
       OZG_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      const long long before = ozg::launch_counter();
       rc = enqueue(c, *NP);
+      NP->nkernels = ozg::launch_counter() - before;
+      __atomic_fetch_sub(&ozg::launch_counter(), NP->nkernels, __ATOMIC_RELAXED);  // counted per replay
       cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
       if (rc) {
         if (graph) cudaGraphDestroy(graph);
@@ -540,6 +575,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
   }
   if (P->exec) {
     OZG_CUDA(cudaGraphLaunch(P->exec, c->stream));
+    __atomic_fetch_add(&ozg::launch_counter(), P->nkernels, __ATOMIC_RELAXED);
   } else {
     int rc = enqueue(c, *P);
     if (rc) return rc;

@@ -10,6 +10,11 @@ namespace ozg {
 // ---------------------------------------------------------------------------------- split
 // Rows of op(X): element (i, l) at X[i + l*ld] when `strided`, at X[l + i*ld] otherwise
 // (complex: interleaved pairs, same indexing in complex elements; `conj` negates Im).
+// Kernel launches issued by this library in this process (graph replays add the kernels they
+// replay); every launch site calls note_launch() right after its launch.
+long long& launch_counter();
+inline void note_launch() { __atomic_fetch_add(&launch_counter(), 1LL, __ATOMIC_RELAXED); }
+
 struct SplitArgs {
   const double* X = nullptr;
   int64_t ld = 0;
@@ -26,6 +31,11 @@ struct SplitArgs {
   int32_t* exps = nullptr;        // [rows] output exponents
   int* nonfinite = nullptr;       // set to 1 if any entry is Inf/NaN
   unsigned long long* hist = nullptr;  // selector features: 10 gap-histogram counters (nullable)
+  // batched split only: digit planes t_lo .. t_hi are written, t_lo = (plane_from ? *plane_from + 1
+  // : 1), t_hi = (plane_to ? *plane_to : s); a job whose *gate is non-zero writes nothing
+  const int* plane_from = nullptr;
+  const int* plane_to = nullptr;
+  const int* gate = nullptr;
 };
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
 
@@ -144,15 +154,20 @@ cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, in
 // prefix arrays: njobs + 1 entries, prefix[0] = 0, prefix[njobs] = units
 // Batched split: one launch per pass over every job of a batch.  Work units come from device
 // tables of (job, unit within the job): row-max units are 32 rows x kRmStridedK k of a strided
-// job or 8 rows x kRmContigK k of a contiguous one; digit units are 32 rows x 64 k.
-constexpr int kRmStridedK = 128, kRmContigK = 1024;
+// job or 8 rows x kRmContigK k of a contiguous one; digit (and feature) units are 32 rows x
+// kDgK k, processed as 64-wide sub-tiles.
+constexpr int kRmStridedK = 128, kRmContigK = 1024, kDgK = 64;
 inline int64_t rowmax_units_of(const SplitArgs& x) {
   return x.strided ? ((x.rows + 31) / 32) * ((x.k + kRmStridedK - 1) / kRmStridedK)
                    : ((x.rows + 7) / 8) * ((x.k + kRmContigK - 1) / kRmContigK);
 }
-inline int64_t digit_units_of(const SplitArgs& x) { return ((x.rows + 31) / 32) * ((x.k + 63) / 64); }
+inline int64_t digit_units_of(const SplitArgs& x) { return ((x.rows + 31) / 32) * ((x.k + kDgK - 1) / kDgK); }
 cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t rowmax_units,
                                  const int2* digit_units_dev, int64_t digit_units, cudaStream_t st);
+// the two passes separately (row maxima; digits) for batches whose slice counts are chosen
+// between them
+cudaError_t launch_rowmax_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st);
+cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st);
 // grouped automatic calls: after the check, skip2[c] = 0 for the calls to re-run (automatic,
 // finite, sampled error above the target), 1 otherwise; save / restore C of automatic calls
 // with beta != 0 (restore only for the calls being re-run)

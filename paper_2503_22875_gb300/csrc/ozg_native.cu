@@ -150,9 +150,9 @@ cudaError_t launch_native_gemm(const NativeArgs& a, cudaStream_t st) {
   dim3 grid((unsigned)((a.n + TN - 1) / TN), (unsigned)((a.m + TM - 1) / TM));
   if (grid.y > 65535) return cudaErrorInvalidValue;
   if (a.cplx)
-    native_gemm_kernel<1><<<grid, 256, 0, st>>>(a);
+    { native_gemm_kernel<1><<<grid, 256, 0, st>>>(a); note_launch(); }
   else
-    native_gemm_kernel<0><<<grid, 256, 0, st>>>(a);
+    { native_gemm_kernel<0><<<grid, 256, 0, st>>>(a); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -161,8 +161,8 @@ cudaError_t launch_scale_c(double* C, int64_t m, int64_t n, int64_t ldc, const d
   int64_t total = m * n;
   if (total <= 0) return cudaSuccess;
   int zero = (beta[0] == 0.0 && (!cplx || beta[1] == 0.0));
-  scale_c_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(C, m, n, ldc, beta[0], cplx ? beta[1] : 0.0, cplx,
-                                                                 zero);
+  { scale_c_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(C, m, n, ldc, beta[0], cplx ? beta[1] : 0.0, cplx,
+                                                                 zero); note_launch(); }
   return cudaGetLastError();
 }
 

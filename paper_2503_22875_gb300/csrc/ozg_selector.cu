@@ -21,6 +21,7 @@
 #include <cuda_bf16.h>
 
 #include "ozg_context.h"
+#include "ozg_split_dev.cuh"
 
 namespace ozg {
 namespace {
@@ -59,7 +60,7 @@ __device__ void hist_tile(const SplitArgs& J, int64_t u, unsigned int* sh) {
     }
     int bin = 9;
     if (b != 0) {
-      const int gap = J.exps[row] - exp_of_bits(b);
+      const int gap = exponent_from_maxbits(J.maxbits[row]) - exp_of_bits(b);  // e_i from the row maximum
       bin = gap < 36 ? (gap < 0 ? 0 : gap / 4) : 9;
     }
     atomicAdd(&sh[bin], 1u);
@@ -78,13 +79,52 @@ __global__ void __launch_bounds__(256) gap_hist_pair(SplitArgs a, SplitArgs b, i
 }
 
 
+// Batched features: a unit is 32 rows x kDgK k of a job (the digit units).  Each thread bins
+// its elements into ten 6-bit counters packed in one 64-bit word (at most 32 elements per
+// thread), the warp sums them with integer reductions, and one shared-memory add per bin and
+// warp precedes one global add per bin and CTA.
 __global__ void __launch_bounds__(256) gap_hist_batched(const SplitArgs* jobs, const int2* units) {
   __shared__ unsigned int sh[10];
   if (threadIdx.x < 10) sh[threadIdx.x] = 0;
   __syncthreads();
   const int2 ur = units[blockIdx.x];
   const SplitArgs J = jobs[ur.x];
-  if (J.hist != nullptr) hist_tile(J, (int64_t)ur.y, sh);
+  if (J.hist != nullptr) {
+    const int64_t ktiles = (J.k + kDgK - 1) / kDgK;
+    const int64_t r0 = (ur.y / ktiles) * 32, lbase = (ur.y % ktiles) * kDgK;
+    const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
+    unsigned long long packed = 0;
+    int e_row = 0;
+    int64_t cached = -1;
+    for (int q = 0; q < kDgK / 8; ++q) {  // 32 elements per thread
+      const int idx = q * 256 + threadIdx.x;
+      int64_t row, l;
+      if (J.strided) {
+        row = r0 + idx % 32;
+        l = lbase + idx / 32;
+      } else {
+        row = r0 + idx / kDgK;
+        l = lbase + idx % kDgK;
+      }
+      if (row >= J.rows || l >= J.k) continue;
+      const uint64_t b = __ldg(J.strided ? X + row + l * J.ld : X + l + row * J.ld) & kAbsMask;
+      if (row != cached) {
+        e_row = exponent_from_maxbits(J.maxbits[row]);
+        cached = row;
+      }
+      int bin = 9;
+      if (b != 0) {
+        const int gap = e_row - exp_of_bits(b);
+        bin = gap < 36 ? (gap < 0 ? 0 : gap / 4) : 9;
+      }
+      packed += 1ull << (6 * bin);
+    }
+#pragma unroll
+    for (int bin = 0; bin < 10; ++bin) {
+      const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (6 * bin)) & 63ull));
+      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sh[bin], v);
+    }
+  }
   __syncthreads();
   if (J.hist != nullptr && threadIdx.x < 10 && sh[threadIdx.x])
     atomicAdd(&J.hist[threadIdx.x], (unsigned long long)sh[threadIdx.x]);
@@ -271,8 +311,8 @@ __global__ void repair_prep_kernel(const double* err, double target, int* not_re
 cudaError_t launch_repair_prep(const double* err, double target, int* not_repaired, const double* saved, double* C,
                                int64_t m, int64_t n, int64_t ldc, int w, int restore, cudaStream_t st) {
   const int64_t total = restore ? m * n * w : 1;
-  repair_prep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(err, target, not_repaired, saved, C, m, n, ldc, w,
-                                                                     restore);
+  { repair_prep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(err, target, not_repaired, saved, C, m, n, ldc, w,
+                                                                     restore); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -282,42 +322,42 @@ cudaError_t launch_mlp_grads(const float* theta, const float* X, const int* y, i
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * kSelParams, st);
   if (e == cudaSuccess && loss) e = cudaMemsetAsync(loss, 0, sizeof(float), st);
   if (e != cudaSuccess) return e;
-  mlp_grads_kernel<<<(B + kSamplesPerBlock - 1) / kSamplesPerBlock, 64, 0, st>>>(theta, X, y, B, grad, loss);
+  { mlp_grads_kernel<<<(B + kSamplesPerBlock - 1) / kSamplesPerBlock, 64, 0, st>>>(theta, X, y, B, grad, loss); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_adam(float* theta, const float* grad, float* m1, float* m2, int step, float lr, float b1, float b2,
                         float eps, float scale, cudaStream_t st) {
   const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
-  adam_kernel<<<(kSelParams + 255) / 256, 256, 0, st>>>(theta, grad, m1, m2, lr, b1, b2, eps, c1, c2, scale);
+  { adam_kernel<<<(kSelParams + 255) / 256, 256, 0, st>>>(theta, grad, m1, m2, lr, b1, b2, eps, c1, c2, scale); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gap_hist_pair(const SplitArgs& a, const SplitArgs& b, cudaStream_t st) {
   const int64_t ua = ((a.rows + 31) / 32) * ((a.k + 63) / 64), ub = ((b.rows + 31) / 32) * ((b.k + 63) / 64);
   if (ua + ub <= 0) return cudaSuccess;
-  gap_hist_pair<<<(unsigned)(ua + ub), 256, 0, st>>>(a, b, ua);
+  { gap_hist_pair<<<(unsigned)(ua + ub), 256, 0, st>>>(a, b, ua); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* digit_units_dev, int64_t units,
                                     cudaStream_t st) {
   if (units <= 0) return cudaSuccess;
-  gap_hist_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, digit_units_dev);
+  { gap_hist_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, digit_units_dev); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_select_single(const SelectorDev* M, const unsigned long long* hA, const unsigned long long* hB,
                                  int64_t m, int64_t n, int64_t k, float log10_target, int s_cap, int* s_out,
                                  float* feat_out, float* prob_out, cudaStream_t st) {
-  select_single<<<1, 32, 0, st>>>(M, hA, hB, m, n, k, log10_target, s_cap, s_out, feat_out, prob_out);
+  { select_single<<<1, 32, 0, st>>>(M, hA, hB, m, n, k, log10_target, s_cap, s_out, feat_out, prob_out); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_select_batched(const SelectorDev* M, const SelectJob* jobs_dev, int njobs, float log10_target,
                                   cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  select_batched<<<(njobs + 3) / 4, 128, 0, st>>>(M, jobs_dev, njobs, log10_target);
+  { select_batched<<<(njobs + 3) / 4, 128, 0, st>>>(M, jobs_dev, njobs, log10_target); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -180,7 +180,7 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
     if (!a.strided) {
       int wpb = 8;
       unsigned grid = (unsigned)((a.rows + wpb - 1) / wpb);
-      rowmax_contig<<<grid, 32 * wpb, 0, st>>>(a.X, a.ld, a.rows, a.k, a.cplx, a.maxbits, a.nonfinite);
+      { rowmax_contig<<<grid, 32 * wpb, 0, st>>>(a.X, a.ld, a.rows, a.k, a.cplx, a.maxbits, a.nonfinite); note_launch(); }
     } else {
       int64_t rb = (a.rows + 255) / 256;
       int64_t ksplit = (608 + rb - 1) / rb;  // ~4 CTAs per SM in total
@@ -189,8 +189,8 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
       if (ksplit < 1) ksplit = 1;
       int64_t kchunk = (a.k + ksplit - 1) / ksplit;
       ksplit = (a.k + kchunk - 1) / kchunk;
-      rowmax_strided<<<dim3((unsigned)rb, (unsigned)ksplit), 256, 0, st>>>(a.X, a.ld, a.rows, a.k, kchunk, a.cplx,
-                                                                           a.maxbits, a.nonfinite);
+      { rowmax_strided<<<dim3((unsigned)rb, (unsigned)ksplit), 256, 0, st>>>(a.X, a.ld, a.rows, a.k, kchunk, a.cplx,
+                                                                           a.maxbits, a.nonfinite); note_launch(); }
     }
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -201,19 +201,19 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
     int64_t total = a.rows * groups;
     unsigned grid = (unsigned)((total + 255) / 256);
     if (a.cplx)
-      digits_contig<1><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                             a.exps, a.D);
+      { digits_contig<1><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
+                                             a.exps, a.D); note_launch(); }
     else
-      digits_contig<0><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                             a.exps, a.D);
+      { digits_contig<0><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
+                                             a.exps, a.D); note_launch(); }
   } else {
     dim3 grid((unsigned)((a.rows + 31) / 32), (unsigned)((a.k + 63) / 64));
     if (a.cplx)
-      digits_strided<1><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                              a.exps, a.D);
+      { digits_strided<1><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
+                                              a.exps, a.D); note_launch(); }
     else
-      digits_strided<0><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                              a.exps, a.D);
+      { digits_strided<0><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
+                                              a.exps, a.D); note_launch(); }
   }
   return cudaGetLastError();
 }
@@ -222,7 +222,7 @@ cudaError_t launch_digits_to_i8(const __half* D, int64_t planes, int64_t plane_r
                                 int8_t* out, cudaStream_t st) {
   int64_t total = planes * plane_rows * k;
   if (total <= 0) return cudaSuccess;
-  digits_to_i8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, planes * plane_rows, k, Kp, out);
+  { digits_to_i8<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(D, planes * plane_rows, k, Kp, out); note_launch(); }
   return cudaGetLastError();
 }
 

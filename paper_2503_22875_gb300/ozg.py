@@ -89,9 +89,17 @@ def load():
     L.ozg_set_fallback_slices.argtypes = [vp, i32]
     L.ozg_set_autotune.argtypes = [vp, i32, ctypes.c_char_p]
     L.ozg_set_tile_variant.argtypes = [vp, i32]
+    L.ozg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
     L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
     _lib = L
     return L
+
+
+def kernel_launches() -> int:
+    """Kernel launches the library has issued in this process (graph replays included)."""
+    n = ctypes.c_longlong(0)
+    _check(load().ozg_kernel_launches(ctypes.byref(n)), "ozg_kernel_launches")
+    return int(n.value)
 
 
 def strerror(code: int) -> str:

@@ -9,6 +9,7 @@ can feed both the CUDA path and the CPU oracle.  numpy PCG64 generators with fix
                         with atom sites r ~ U(cube of unit density) plus (1 + 0.1i) on the
                         diagonal -- stands in for the MuST "MT u56" ZGEMMs of Sec. 3.2
   grouped_batch         2048 GEMMs, m, n, k log-uniform in [32, 2048], phi ~ U(0, 4) per call
+                        (grouped_batch_flat: the same batch drawn on the GPU into flat buffers)
 """
 from __future__ import annotations
 
@@ -98,3 +99,62 @@ def grouped_batch_device(count: int = 2048, lo: int = 32, hi: int = 2048, phi_hi
             return (u - 0.5) * torch.exp(c.phi * z)  # shape (cols, rows): column-major rows x cols
         out.append((c.m, c.n, c.k, c.phi, draw(c.m, c.k), draw(c.k, c.n)))
     return out
+
+
+@dataclass
+class FlatBatch:
+    """A grouped batch in three flat device buffers (A's, B's, C's back to back, 256-byte aligned
+    offsets), so the whole batch moves between host and device in three copies."""
+    calls: list          # GemmCall per problem
+    A: object            # torch float64 flat buffers on the device
+    B: object
+    C: object
+    offA: list           # element offsets of each problem's A, B, C
+    offB: list
+    offC: list
+
+    def views(self, i):
+        """(A_i, B_i, C_i) as column-major torch views: shapes (k, m), (n, k), (n, m)."""
+        c = self.calls[i]
+        a = self.A[self.offA[i]:self.offA[i] + c.m * c.k].view(c.k, c.m)
+        b = self.B[self.offB[i]:self.offB[i] + c.k * c.n].view(c.n, c.k)
+        cc = self.C[self.offC[i]:self.offC[i] + c.m * c.n].view(c.n, c.m)
+        return a, b, cc
+
+    def gemm_calls(self, alpha=1.0, beta=0.0):
+        """Descriptor tuples ('N', 'N', m, n, k, alpha, A, lda, B, ldb, beta, C, ldc) for ozg."""
+        out = []
+        for i, c in enumerate(self.calls):
+            a, b, cc = self.views(i)
+            out.append(("N", "N", c.m, c.n, c.k, alpha, a, c.m, b, c.k, beta, cc, c.m))
+        return out
+
+
+def grouped_batch_flat(count: int = 2048, lo: int = 32, hi: int = 2048, phi_hi: float = 4.0, seed: int = 4,
+                       device: str = "cuda") -> FlatBatch:
+    """The grouped batch (shapes and spreads of grouped_batch) drawn on the GPU into flat buffers
+    with a seeded torch generator."""
+    import torch
+    calls = grouped_batch(count, lo, hi, phi_hi, seed)
+
+    def offsets(sizes):
+        offs, o = [], 0
+        for z in sizes:
+            offs.append(o)
+            o += (z + 31) // 32 * 32
+        return offs, max(o, 1)
+
+    offA, nA = offsets([c.m * c.k for c in calls])
+    offB, nB = offsets([c.k * c.n for c in calls])
+    offC, nC = offsets([c.m * c.n for c in calls])
+    A = torch.zeros(nA, dtype=torch.float64, device=device)
+    B = torch.zeros(nB, dtype=torch.float64, device=device)
+    C = torch.zeros(nC, dtype=torch.float64, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    for i, c in enumerate(calls):
+        for buf, off, size in ((A, offA[i], c.m * c.k), (B, offB[i], c.k * c.n)):
+            u = torch.rand(size, generator=gen, device=device, dtype=torch.float64)
+            z = torch.randn(size, generator=gen, device=device, dtype=torch.float64)
+            buf[off:off + size] = (u - 0.5) * torch.exp(c.phi * z)
+    return FlatBatch(calls, A, B, C, offA, offB, offC)
