@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the fixed-slice and native comparisons")
     ap.add_argument("--no-single", action="store_true", help="skip the 8192^3 slice sweep")
     ap.add_argument("--single-size", type=int, default=8192)
+    ap.add_argument("--single-phis", default="0.5,2,4", help="phi values of the single-DGEMM sweep")
+    ap.add_argument("--single-slices", default="3-10", help="slice counts of the single-DGEMM sweep (a-b or list)")
+    ap.add_argument("--only-single", action="store_true", help="run only the single-DGEMM section (profiling)")
     ap.add_argument("--no-zgemm", action="store_true", help="skip the KKR-like ZGEMM section")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end number")
     return ap.parse_args()
@@ -70,6 +73,26 @@ def parse():
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def world_max(pg, x: float, device) -> float:
+    """Maximum of x over all ranks (the slowest rank's time), or x itself without a group."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(flops_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job TFLOP/s: every rank's (equal-sized) batch over the slowest rank's step time."""
+    return flops_per_rank * world / (ms_max / 1e3) / 1e12
+
+
+def rank_batch_seed(rank: int) -> int:
+    """Each rank draws its own batch (independent problems of the same distribution)."""
+    return BATCH_SEED + rank
 
 
 # ------------------------------------------------------------------------------------ peaks
@@ -281,16 +304,22 @@ def compare_section(ozg, torch, batch, calls, flops, st, steps):
     ctx.set_check_samples(CHECK_SAMPLES)
     with torch.cuda.stream(st):
         reps = [ctx.dgemm(*c, 7, report=True) for c in calls]
-    out["fixed_s7_one_at_a_time"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, **report_stats(reps)}
+    out["fixed_s7_one_at_a_time"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "check": "none while timed",
+                                     **report_stats(reps)}
     ctx.close()
     fixed = {}
     for s in FIXED_SWEEP:
+        # timed with the same per-call sampled check the learned step runs (and without it)
         ctx = ozg.Context(stream=st)
-        ms = timed(torch, st, lambda: ctx.dgemm_grouped(calls, [s] * n), max(1, min(steps, 5)))
+        ms_nocheck = timed(torch, st, lambda: ctx.dgemm_grouped(calls, [s] * n), max(1, min(steps, 5)))
+        ctx.close()
+        ctx = ozg.Context(stream=st)
         ctx.set_check_samples(CHECK_SAMPLES)
+        ms = timed(torch, st, lambda: ctx.dgemm_grouped(calls, [s] * n), max(1, min(steps, 5)))
         with torch.cuda.stream(st):
             reps = ctx.dgemm_grouped(calls, [s] * n, report=True)
-        fixed[s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, **report_stats(reps)}
+        fixed[s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "tflops_without_check": flops / (ms_nocheck / 1e3) / 1e12,
+                    **report_stats(reps)}
         ctx.close()
     out["fixed_grouped"] = fixed
     ok_all = [s for s in FIXED_SWEEP if fixed[s]["frac_le_target"] >= 1.0]
@@ -304,7 +333,14 @@ def compare_section(ozg, torch, batch, calls, flops, st, steps):
     return out
 
 
-def single_section(ozg, torch, size, steps):
+def parse_list(spec, cast):
+    if "-" in spec and "," not in spec:
+        a, b = spec.split("-")
+        return list(range(int(a), int(b) + 1))
+    return [cast(x) for x in spec.split(",")]
+
+
+def single_section(ozg, torch, size, steps, phis=SINGLE_PHIS, slice_list=tuple(range(3, 11))):
     """Config 2: emulated DGEMM size^3, a = (u - 0.5) exp(phi g), phi in {0.5, 2, 4}, s = 3..10:
     TFLOP/s and sampled double-double error per s, the native FP64 kernel, and the roofline of the
     slice-product kernel at phi = 0.5 with the smallest s meeting 1e-12."""
@@ -316,7 +352,7 @@ def single_section(ozg, torch, size, steps):
     out = {"workload": f"emulated DGEMM {n}^3, a=(u-0.5)exp(phi g), u~U(0,1), g~N(0,1); GPU-drawn (seeded)",
            "by_phi": {}}
     roof = None
-    for phi in SINGLE_PHIS:
+    for phi in phis:
         gen.manual_seed(int(1000 * phi) + 2)
 
         def draw():
@@ -326,7 +362,7 @@ def single_section(ozg, torch, size, steps):
         dA, dB = draw(), draw()
         ctx = ozg.Context(stream=st)
         res = {}
-        for s in range(3, 11):
+        for s in slice_list:
             ctx.set_check_samples(0)
             ms = timed(torch, st, lambda: ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s),
                        max(1, min(steps, 3)))
@@ -336,7 +372,7 @@ def single_section(ozg, torch, size, steps):
             res[s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "err_sampled_dd": rep.est_err}
         ok = [s for s in res if res[s]["err_sampled_dd"] <= TARGET_ERR]
         entry = {"by_slices": res, "smallest_s_meeting_target": min(ok) if ok else None}
-        if phi == SINGLE_PHIS[0]:
+        if phi == phis[0]:
             s = entry["smallest_s_meeting_target"] or 7
             ctx.set_check_samples(0)
             ctx.set_profiling(True)
@@ -396,6 +432,13 @@ def run_gpu(args):
 
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
+    if args.only_single:
+        build.build()
+        ozg.load()
+        sec = single_section(ozg, torch, args.single_size, args.steps, parse_list(args.single_phis, float),
+                             parse_list(args.single_slices, int))
+        print(json.dumps({"single_dgemm": sec}), flush=True)
+        return 0
     pg = None
     if world > 1:
         import torch.distributed as dist
@@ -403,7 +446,7 @@ def run_gpu(args):
         pg = dist
     build.build()
     ozg.load()
-    batch = workloads.grouped_batch_flat(args.count, seed=BATCH_SEED + rank)
+    batch = workloads.grouped_batch_flat(args.count, seed=rank_batch_seed(rank))
     calls = batch.gemm_calls()
     n = len(calls)
     flops = sum(2.0 * c.m * c.n * c.k for c in batch.calls)
@@ -443,12 +486,8 @@ def run_gpu(args):
     clk = clocks.stop()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = flops * world / (ms_max / 1e3) / 1e12
+    ms_max = world_max(pg, ms, "cuda")
+    value = weak_value(flops, world, ms_max)
     with torch.cuda.stream(st):
         reps = ctx.dgemm_grouped(calls, auto, report=True)
     stats = report_stats(reps)
@@ -500,12 +539,8 @@ def run_gpu(args):
                 hC.copy_(batch.C, non_blocking=True)
             e1.record(st)
         e1.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
-        if pg is not None:
-            t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": flops * world / (e2e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+        e2e_ms = world_max(pg, e0.elapsed_time(e1) / e2e_steps, "cuda")
+        e2e = {"value": weak_value(flops, world, e2e_ms), "unit": "TFLOP/s",
                "h2d_bytes_per_step": 8 * (batch.A.numel() + batch.B.numel()),
                "d2h_bytes_per_step": 8 * batch.C.numel(), "ms_per_step": e2e_ms}
         del hA, hB, hC
@@ -529,7 +564,9 @@ def run_gpu(args):
         compare["learned_vs_native_fp64"] = learned / compare["native_fp64_one_at_a_time"]["tflops"]
     del batch, calls
     torch.cuda.empty_cache()
-    single = None if args.no_single else single_section(ozg, torch, args.single_size, args.steps)
+    single = None if args.no_single else single_section(ozg, torch, args.single_size, args.steps,
+                                                        parse_list(args.single_phis, float),
+                                                        parse_list(args.single_slices, int))
     zgemm = None if args.no_zgemm else zgemm_section(ozg, torch, max(1, min(args.steps, 3)))
     cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(args.count)
 

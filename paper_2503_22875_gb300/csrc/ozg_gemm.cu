@@ -46,6 +46,7 @@ constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 128 + EPI_WARPS * 32;
 constexpr int REG_PRODUCER = 40, REG_EPILOGUE = 232;
 static_assert(128 * REG_PRODUCER + EPI_WARPS * 32 * REG_EPILOGUE <= THREADS * 168, "register split");
+constexpr int TRING = 4;       // tile-index ring depth (grouped launches)
 constexpr int CHAIN_K = 1024;  // products per accumulation chain: 1024 * 127^2 = 16516096 < 2^24
 constexpr int GROUP_M = 8;     // tile raster: GROUP_M row-tiles share a sweep over the column tiles
 static_assert(CHAIN_K * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
@@ -477,6 +478,10 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES], bar_accf[2], bar_acce[2], bar_done;
+  // grouped launches hand out tiles dynamically: the producer claims a tile index (atomic
+  // counter) and passes it to the MMA lane and the epilogue warps through this ring
+  __shared__ __align__(8) uint64_t bar_tfull[TRING], bar_tempty[TRING];
+  __shared__ int tile_ring[TRING];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
 
@@ -496,6 +501,10 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
       mbar_init(&bar_acce[b], EPI_WARPS);
     }
     mbar_init(&bar_done, 1);
+    for (int i = 0; i < TRING; ++i) {
+      mbar_init(&bar_tfull[i], 1);
+      mbar_init(&bar_tempty[i], 1 + EPI_WARPS);
+    }
     abort_flag = 0;
     mbar_fence_init();
   }
@@ -518,7 +527,25 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         uint32_t stage = 0, phase = 0;
         long long issued = 0;
         const CUtensorMap* last_map = nullptr;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t tslot = 0, tphase = 0;
+        int tnext = blockIdx.x;
+        for (;;) {
+          int t;
+          if (GROUPED) {
+            if (!mbar_wait(&bar_tempty[tslot], tphase ^ 1, abort_p, status)) goto producer_done;
+            t = tnext < ntiles ? tnext : -1;
+            tile_ring[tslot] = t;
+            mbar_arrive(&bar_tfull[tslot]);
+            if (++tslot == TRING) {
+              tslot = 0;
+              tphase ^= 1;
+            }
+            if (t >= 0) tnext = (int)gridDim.x + atomicAdd(G->tile_counter, 1);
+          } else {
+            t = tnext < ntiles ? tnext : -1;
+            tnext += gridDim.x;
+          }
+          if (t < 0) break;
           const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
           if (j.skip) continue;
           if (GROUPED && j.tmA != last_map) {
@@ -568,7 +595,23 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         uint32_t stage = 0, phase = 0;
         uint32_t acc_par = 0;  // bit b: parity of the next use of TMEM buffer b
         int buf = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t tslot = 0, tphase = 0;
+        int tnext = blockIdx.x;
+        for (;;) {
+          int t;
+          if (GROUPED) {
+            if (!mbar_wait(&bar_tfull[tslot], tphase, abort_p, status)) goto mma_done;
+            t = tile_ring[tslot];
+            mbar_arrive(&bar_tempty[tslot]);
+            if (++tslot == TRING) {
+              tslot = 0;
+              tphase ^= 1;
+            }
+          } else {
+            t = tnext < ntiles ? tnext : -1;
+            tnext += gridDim.x;
+          }
+          if (t < 0) break;
           const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
           if (j.skip) continue;
           for (int g = 2; g <= j.s + 1; ++g) {
@@ -642,7 +685,24 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     int pend_o = CPT, pend_chunk = CPT, pend_nout = CPT;
     PushArgs pend;
     const bool odd = (lane & 1) != 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    uint32_t tslot = 0, tphase = 0;
+    int tnext = blockIdx.x;
+    for (;;) {
+      int t;
+      if (GROUPED) {
+        if (!mbar_wait(&bar_tfull[tslot], tphase, abort_p, status)) goto epi_done;
+        t = tile_ring[tslot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_tempty[tslot]);
+        if (++tslot == TRING) {
+          tslot = 0;
+          tphase ^= 1;
+        }
+      } else {
+        t = tnext < ntiles ? tnext : -1;
+        tnext += gridDim.x;
+      }
+      if (t < 0) break;
       const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
       if (j.skip) continue;
       const int s = j.s;

@@ -31,7 +31,7 @@ struct GroupPlan {
   int any_auto = 0, s_fb = 0;
   int64_t save_units = 0;
   size_t oHist = 0, hist_bytes = 0, oSel = 0, oSused = 0, oRep = 0, oSavePre = 0, oSaved = 0;
-  size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0, oJobs2 = 0;
+  size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0, oJobs2 = 0, oCounter = 0;
   std::vector<char> autom;
 };
 
@@ -51,10 +51,11 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
 
 int tile_n_of(int variant) { return slice_gemm_tile_n_of(variant); }
 
-// Longest-processing-time assignment of all tiles to `grid` CTAs, interleaved for the
-// persistent kernel's static stride.
-std::vector<GroupTile> balanced_tiles(const ozg_gemm_desc* d, const std::vector<int>& s, int64_t count, int variant,
-                                      int grid) {
+// All tiles in decreasing estimated cost (tiles of one call stay together, so tiles that share
+// digit panels run at about the same time).  The kernel hands them out dynamically -- each CTA
+// claims the next tile when it starts one -- so the order gives the longest-first balance and
+// costs that are only known on the device (selected slice counts) cannot unbalance the launch.
+std::vector<GroupTile> ordered_tiles(const ozg_gemm_desc* d, const std::vector<int>& s, int64_t count, int variant) {
   struct T {
     double cost;
     GroupTile t;
@@ -68,21 +69,9 @@ std::vector<GroupTile> balanced_tiles(const ozg_gemm_desc* d, const std::vector<
       for (int64_t j = 0; j < tn; ++j) all.push_back({cost, {(int)c, (int)i, (int)j, 0}});
   }
   std::stable_sort(all.begin(), all.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
-  typedef std::pair<double, int> L;
-  std::priority_queue<L, std::vector<L>, std::greater<L>> heap;
-  for (int b = 0; b < grid; ++b) heap.push({0.0, b});
-  std::vector<std::vector<GroupTile>> per(grid);
-  for (const T& x : all) {
-    L top = heap.top();
-    heap.pop();
-    per[top.second].push_back(x.t);
-    heap.push({top.first + x.cost, top.second});
-  }
-  size_t depth = 0;
-  for (auto& v : per) depth = std::max(depth, v.size());
-  std::vector<GroupTile> out(depth * grid, GroupTile{-1, 0, 0, 0});
-  for (int b = 0; b < grid; ++b)
-    for (size_t i = 0; i < per[b].size(); ++i) out[i * grid + b] = per[b][i];
+  std::vector<GroupTile> out;
+  out.reserve(all.size());
+  for (const T& x : all) out.push_back(x.t);
   return out;
 }
 
@@ -90,6 +79,7 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oFlags), 0, P.flags_bytes, st));
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
+  OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oCounter), 0, sizeof(int) * 2, st));
   if (!P.any_auto) {
     OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units,
                                   gat<int2>(c, P.oDgTab), P.digit_units, st));
@@ -111,6 +101,7 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   g.status = c->dflags;
   g.Rws = gat<double>(c, P.oR);
   g.defer = variant_defers(P.variant);
+  g.tile_counter = gat<int>(c, P.oCounter);
   {
     PhaseScope ps(c, OZG_PHASE_GEMM);
     OZG_CUDA(launch_slice_gemm_grouped(g, P.variant, P.grid, st));
@@ -127,6 +118,7 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
     OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs2), gat<int2>(c, P.oDgTab), P.digit_units, st));
     GroupArgs g2 = g;
     g2.calls = gat<GroupCall>(c, P.oCalls2);
+    g2.tile_counter = gat<int>(c, P.oCounter) + 1;
     {
       PhaseScope ps(c, OZG_PHASE_GEMM);
       OZG_CUDA(launch_slice_gemm_grouped(g2, P.variant, P.grid, st));
@@ -177,7 +169,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   const int BN = tile_n_of(variant);
   for (int64_t i = 0; i < count; ++i) total_tiles += ((d[i].m + 127) / 128) * ((d[i].n + BN - 1) / BN);
   P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->num_sms, total_tiles));
-  std::vector<GroupTile> tiles = balanced_tiles(d, s, count, variant, P->grid);
+  std::vector<GroupTile> tiles = ordered_tiles(d, s, count, variant);
   P->ntiles = (int)tiles.size();
 
   Carve cv;
@@ -225,6 +217,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->oErrs = cv.take(sizeof(double) * count);
   P->oCold = cv.take(sizeof(double) * 2 * (size_t)std::max(nsamp, 1) * count);
   P->oR = cv.take((size_t)P->grid * 128 * 256 * 16);
+  P->oCounter = cv.take(sizeof(int) * 2);  // tile counters of the main and the re-run launch
   std::vector<int64_t> sp(count + 1, 0);
   std::vector<size_t> oSv(count, 0);
   if (any_auto) {
@@ -500,8 +493,7 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     c->plan.reset();
     // tile variant: autotuned per batch when every call writes C without reading it (all
     // variants give bit-identical results), else the padding heuristic summed over the batch;
-    // bit 1 from the work-weighted means of k (256-wide: deferred pushes for long k) and of s
-    // (128-wide: the deeper pipeline for s >= 10)
+    // for 256-wide tiles, deferred pushes when the work-weighted mean k is long
     int variant;
     double pad0 = 0, pad1 = 0, wk = 0, wsum = 0, w = 0;
     bool all_beta_zero = true;
@@ -514,8 +506,9 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
       w += wi;
       all_beta_zero = all_beta_zero && work[i].beta == 0.0;
     }
+    (void)wsum;
     if (pad1 < pad0)
-      variant = 1 | (w > 0 && wsum >= 10.0 * w ? 2 : 0);
+      variant = 1;
     else
       variant = (w > 0 && wk >= 2048.0 * w) ? 2 : 0;
     auto tuned = c->tune.find(key);

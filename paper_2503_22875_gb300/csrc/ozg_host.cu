@@ -127,12 +127,13 @@ void tune_store(ozg_ctx* c, uint64_t bucket, int variant) {
 // Heuristic variant: the tile width that wastes the least output area (ties -> 256 wide); for
 // 256-wide tiles deferred epilogue pushes when k >= 2048 (they then overlap the next chains'
 // MMAs; for short k the epilogue is the bottleneck and immediate pushes measured faster); for
-// 128-wide tiles the deeper pipeline (one 64-wide k sub-tile per stage) when s >= 10, whose
-// larger slice panels make load latency matter more than MMA issue overhead.
+// 128-wide tiles two 64-wide k sub-tiles per stage (measured faster than the deeper 6-stage
+// pipeline for s = 7..12 once grouped tiles are handed out dynamically).
 static int heuristic_variant(int64_t rows, int64_t cols, int64_t k, int s) {
   (void)rows;
+  (void)s;
   const int64_t p256 = (cols + 255) / 256 * 256, p128 = (cols + 127) / 128 * 128;
-  if (p128 < p256) return 1 | (s >= 10 ? 2 : 0);
+  if (p128 < p256) return 1;
   return k >= 2048 ? 2 : 0;
 }
 

@@ -81,12 +81,13 @@ struct GroupCall {
   const int* nonfinite = nullptr;  // this call's Inf/NaN flag (its tiles are skipped when set)
 };
 struct GroupTile {
-  int call;  // < 0: empty slot (load-balancing padding)
+  int call;  // < 0: empty slot
   int tm, tn, pad;
 };
 struct GroupArgs {
-  const GroupTile* tiles = nullptr;  // CTA b processes tiles b, b + grid, b + 2 grid, ...
-  int ntiles = 0;
+  const GroupTile* tiles = nullptr;  // in decreasing cost; CTA b starts with tile b, then claims
+  int ntiles = 0;                    // grid + atomicAdd(tile_counter, 1) until the list ends
+  int* tile_counter = nullptr;       // zero before the launch
   const GroupCall* calls = nullptr;
   int* status = nullptr;
   double* Rws = nullptr;

@@ -9,7 +9,11 @@ accuracy it needs).
   (s = 12 if none does).  Per-row and per-column scales make the block's emulation identical to
   the full product's on those entries.
 * Training runs on the GPU with the library's forward/backward and Adam kernels
-  (``ozg_selector_train_step``).
+  (``ozg_selector_train_step``) on four fifths of the GEMMs.
+* Decision: the smallest s whose cumulative predicted probability of "s_min <= s" reaches a
+  threshold, chosen on the held-out fifth to minimise the expected tensor work -- s(s+1)/2
+  products at the chosen s plus a re-run at the fallback count when the sampled check rejects
+  the result (s below the GEMM's minimal sufficient count).
 
     python -m paper_2503_22875_gb300.selector --problems 25000 --out model.ozgsel
 """
@@ -190,6 +194,46 @@ def train(ctx, X: np.ndarray, y: np.ndarray, epochs: int = 40, batch: int = 1024
     return ctx.selector_get_params(), mean, std, losses
 
 
+def predict_probs(theta, mean, std, X: np.ndarray) -> np.ndarray:
+    """Class probabilities of the model as the GPU computes them (BF16 weights, FP32 arithmetic;
+    the summation order may differ in the last bits)."""
+    p = split_theta(theta)
+    inv = np.where(std > 0, np.float32(1) / np.asarray(std, np.float32), np.float32(0)).astype(np.float32)
+
+    def bf(w, shape):
+        return (to_bf16_bits(w).astype(np.uint32) << 16).view(np.float32).reshape(shape)
+    x = ((np.asarray(X, np.float32) - np.asarray(mean, np.float32)) * inv).astype(np.float32)
+    h1 = np.maximum(x @ bf(p["W1"], (N_H, N_IN)).T + p["b1"], 0).astype(np.float32)
+    h2 = np.maximum(h1 @ bf(p["W2"], (N_H, N_H)).T + p["b2"], 0).astype(np.float32)
+    z = (h2 @ bf(p["W3"], (N_CLASSES, N_H)).T + p["b3"]).astype(np.float32)
+    z -= z.max(axis=1, keepdims=True)
+    e = np.exp(z)
+    return e / e.sum(axis=1, keepdims=True)
+
+
+def decide(probs: np.ndarray, thr: float, fallback: int, s_lo: int = S_LO) -> np.ndarray:
+    """The decision rule: the smallest s whose cumulative probability of 's_min <= s' reaches thr."""
+    cum = np.cumsum(probs, axis=1)
+    hit = cum >= thr
+    return np.where(hit.any(1), s_lo + hit.argmax(1), fallback)
+
+
+def choose_threshold(probs, s_min, work, fallback, grid=None):
+    """Threshold minimising the expected tensor work on held-out GEMMs: s(s+1)/2 products at the
+    chosen s, plus a re-run at the fallback count whenever s is below the GEMM's minimal
+    sufficient count (the sampled check rejects it).  work: m n k per sample."""
+    grid = grid if grid is not None else [0.5, 0.6, 0.7, 0.8, 0.85, 0.9, 0.93, 0.95, 0.97, 0.98, 0.99, 0.995]
+    fb_cost = fallback * (fallback + 1) / 2
+    table = {}
+    for thr in grid:
+        s = decide(probs, thr, fallback)
+        miss = s < s_min
+        cost = float(np.sum(work * (s * (s + 1) / 2 + miss * fb_cost)))
+        table[thr] = {"cost": cost, "rerun_frac": float(miss.mean()), "mean_s": float(s.mean())}
+    best = min(table, key=lambda t: table[t]["cost"])
+    return best, table
+
+
 def fallback_from_smin(s_min: np.ndarray, q: float = 99.9) -> int:
     """The conservative fixed count: the q-th percentile of the training GEMMs' minimal
     sufficient slice counts (measured up to s = 16), capped to the library's maximum of 18."""
@@ -202,7 +246,8 @@ def main():
     ap.add_argument("--lo", type=int, default=64)
     ap.add_argument("--hi", type=int, default=4096)
     ap.add_argument("--epochs", type=int, default=40)
-    ap.add_argument("--threshold", type=float, default=0.99)
+    ap.add_argument("--threshold", type=float, default=0.0,
+                    help="decision threshold; <= 0 chooses it on held-out GEMMs by expected work")
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--out", required=True)
     args = ap.parse_args()
@@ -212,14 +257,22 @@ def main():
     t0 = time.time()
     X, y, meta = make_dataset(ctx, args.problems, seed=args.seed, lo=args.lo, hi=args.hi, log=print)
     t1 = time.time()
-    theta, mean, std, losses = train(ctx, X, y, epochs=args.epochs, log=print)
+    # every fifth GEMM is held out to choose the decision threshold
+    prob_idx = np.arange(len(y)) % args.problems
+    held = prob_idx % 5 == 0
+    theta, mean, std, losses = train(ctx, X[~held], y[~held], epochs=args.epochs, log=print)
     t2 = time.time()
     fb = fallback_from_smin(meta["s_min"])
-    write_model(args.out, theta, mean, std, args.threshold, fb)
-    # decision quality on the training set with the written model (GPU inference is checked
-    # against this in the tests): fraction of GEMMs whose chosen s meets the label
-    print(json.dumps({"problems": args.problems, "samples": int(len(y)), "data_s": t1 - t0, "train_s": t2 - t1,
-                      "final_loss": losses[-1], "first_loss": losses[0], "fallback": fb,
+    thr = args.threshold
+    table = None
+    if thr <= 0:
+        dims = meta["dims"][prob_idx[held]]
+        work = dims[:, 0].astype(float) * dims[:, 1] * dims[:, 2]
+        thr, table = choose_threshold(predict_probs(theta, mean, std, X[held]), meta["s_min"][held], work, fb)
+    write_model(args.out, theta, mean, std, thr, fb)
+    print(json.dumps({"problems": args.problems, "samples": int(len(y)), "held_out": int(held.sum()),
+                      "data_s": t1 - t0, "train_s": t2 - t1, "final_loss": losses[-1], "first_loss": losses[0],
+                      "fallback": fb, "threshold": thr, "threshold_table": table,
                       "label_hist": np.bincount(y, minlength=N_CLASSES).tolist(),
                       "s_min_hist": np.bincount(meta["s_min"], minlength=S_MEASURE + 2).tolist()}))
 

@@ -101,3 +101,40 @@ def test_features_closed_forms():
     assert abs(f[23] + 10) < 1e-6
     g = oracle.features(np.asfortranarray(A.T), B, 1e-14, transa="T")
     np.testing.assert_array_equal(f[:23], g[:23])
+
+
+def test_selector_training_helpers_match_oracle_inference(tmp_path):
+    """The training tool's NumPy forward pass and decision rule (used to choose the decision
+    threshold on held-out GEMMs) agree with the oracle's FP32 emulation of the GPU inference."""
+    from paper_2503_22875_gb300 import selector as S
+    rng = np.random.default_rng(11)
+    theta = S.init_params(3)
+    X = rng.normal(size=(200, S.N_IN)).astype(np.float32)
+    mean, std = X.mean(0), X.std(0) + 1e-3
+    P = S.predict_probs(theta, mean, std, X)
+    assert np.allclose(P.sum(1), 1, atol=1e-5)
+    path = str(tmp_path / "m.ozgsel")
+    S.write_model(path, theta, mean, std, 0.9, 13)
+    model = S.read_model(path)
+    agree = 0
+    for x, p in zip(X, P):
+        s_orc, probs = oracle.mlp_select(model, x, 13)
+        assert np.allclose(probs, p, atol=2e-5)
+        agree += int(S.decide(p[None], 0.9, 13)[0] == s_orc)
+    assert agree >= 198  # ties at the threshold may round differently
+
+
+def test_threshold_choice_minimises_expected_work():
+    from paper_2503_22875_gb300 import selector as S
+    # two classes of GEMMs: confident predictions make a low threshold cheap; the chosen
+    # threshold must be the grid minimum of the stated cost
+    probs = np.zeros((4, S.N_CLASSES), np.float32)
+    probs[:, 5] = 0.92  # s = 7
+    probs[:, 6] = 0.08  # s = 8
+    s_min = np.array([7, 7, 7, 8])
+    work = np.ones(4)
+    best, table = S.choose_threshold(probs, s_min, work, 13)
+    costs = {t: v["cost"] for t, v in table.items()}
+    assert costs[best] == min(costs.values())
+    # at thr <= 0.92 every GEMM runs at s = 7 and one re-runs at 13; above, all run at s = 8
+    assert table[0.9]["cost"] == 4 * 28 + 91 and table[0.95]["cost"] == 4 * 36
