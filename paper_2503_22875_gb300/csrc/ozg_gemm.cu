@@ -554,8 +554,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
             last_map = j.tmA;
           }
           for (int g = 2; g <= j.s + 1; ++g)
-            for (int kb = 0; kb < j.KB; ++kb)
+            for (int kbi = 0; kbi < j.KB; ++kbi)
               for (int p = 1; p < g; ++p) {
+                const int kb = (g & 1) ? j.KB - 1 - kbi : kbi;  // snake: each group starts where the last ended
                 if (!mbar_wait(&bar_empty[stage], phase ^ 1, abort_p, status)) goto producer_done;
                 uint8_t* sA = smem + stage * K::STAGE_BYTES;
                 const int nsub = kb == j.KB - 1 ? j.klast : K::SUB;  // an all-zero tail sub-tile is skipped
@@ -617,8 +618,9 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           for (int g = 2; g <= j.s + 1; ++g) {
             const int nblk = (g - 1) * j.KB;
             int b = 0;
-            for (int kb = 0; kb < j.KB; ++kb)
+            for (int kbi = 0; kbi < j.KB; ++kbi)
               for (int p = 1; p < g; ++p) {
+                const int kb = (g & 1) ? j.KB - 1 - kbi : kbi;  // snake: each group starts where the last ended
                 const bool chain_start = (b % K::SEG) == 0;
                 if (chain_start) {
                   if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, status)) goto mma_done;
