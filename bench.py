@@ -384,6 +384,7 @@ def single_section(ozg, torch, size, steps, phis=SINGLE_PHIS, slice_list=tuple(r
             gemm_ms = ph["gemm"][0] / max(ph["gemm"][1], 1)
             roof = tensor_roofline("slice_gemm_kernel", s * (s + 1) / 2 * flops, gemm_ms, f"slice_gemm_{n}_s{s}")
             roof["slices"] = s
+            roof["algorithmic_bytes"] = 2.0 * s * 2 * n * n + 8.0 * n * n
             ms_nat = timed(torch, st, lambda: ctx.native_dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n), 1,
                            warm=0)
             entry["native_fp64_tflops"] = flops / (ms_nat / 1e3) / 1e12
@@ -516,6 +517,9 @@ def run_gpu(args):
     gemm_ms = ph["gemm"][0] / rsteps
     grouped_ms_nograph = ph["grouped"][0] / max(ph["grouped"][1], 1)
     roof = tensor_roofline("slice_gemm_grouped_kernel", tflops_step, gemm_ms, f"slice_gemm_grouped_learned_{n}")
+    # algorithmic DRAM bytes of the launch: each selected digit plane read once, C written once
+    roof["algorithmic_bytes"] = sum(2.0 * r.selected * (c.m + c.n) * c.k + 8.0 * c.m * c.n
+                                    for c, r in zip(batch.calls, reps))
     roof["note"] = ("tensor flops = sum over calls of s(s+1)/2 * 2mnk at the selected s (plus fallback re-runs); "
                     "launch_ms = the step's grouped GEMM launches, CUDA events, without the graph")
 
