@@ -108,9 +108,8 @@ __global__ void __launch_bounds__(256) rowmax_batched(const SplitArgs* jobs, con
 // sub-tiles.  Thread t computes row t/8 and the 8 consecutive k at (t%8)*8 of a sub-tile;
 // strided jobs are staged (transposed) through shared memory so that global loads stay
 // coalesced.  The loads of the next sub-tile are issued before the current one is processed.
-__global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, const int2* units) {
+__device__ __forceinline__ void digits_unit(const SplitArgs* jobs, int2 ur) {
   __shared__ uint64_t tile[64][33];
-  const int2 ur = units[blockIdx.x];
   {
     const int* gate = jobs[ur.x].gate;
     if (gate != nullptr && *gate) return;
@@ -171,20 +170,36 @@ __global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, con
   }
 }
 
+// Grid-stride over the units; a gated pass (re-run completion) first reads one step-wide flag.
+__global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, const int2* units, int64_t nunits,
+                                                      const int* run) {
+  if (run != nullptr && *run == 0) return;  // nothing to do in this pass
+  for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
+    digits_unit(jobs, units[unit]);
+    __syncthreads();  // the next unit reuses the staging tile
+  }
+}
+
 // ---------------------------------------------------------------------------- native fallback
 // Device-side compaction of the calls whose non-finite flag is set, then a persistent FP64
 // kernel over their 64 x 64 output tiles.
-__global__ void native_compact(const NativeArgs* calls, int ncalls, const int* const* flags, int* list,
-                               int64_t* tile_prefix, int64_t* total) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One CTA: the flags are scanned in parallel (list order does not matter), then one thread
+// forms the tile prefix over the flagged calls only (usually none).
+__global__ void __launch_bounds__(1024) native_compact(const NativeArgs* calls, int ncalls, const int* const* flags,
+                                                       int* list, int64_t* tile_prefix, int64_t* total) {
+  __shared__ int n_sh;
+  if (threadIdx.x == 0) n_sh = 0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncalls; c += blockDim.x)
+    if (*flags[c] != 0) list[atomicAdd(&n_sh, 1)] = c;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int n = n_sh;
   int64_t acc = 0;
-  int n = 0;
-  for (int c = 0; c < ncalls; ++c) {
-    if (*flags[c] == 0) continue;
-    list[n] = c;
-    tile_prefix[n] = acc;
+  for (int i = 0; i < n; ++i) {
+    const int c = list[i];
+    tile_prefix[i] = acc;
     acc += ((calls[c].m + 63) / 64) * ((calls[c].n + 63) / 64);
-    ++n;
   }
   tile_prefix[n] = acc;
   total[0] = acc;
@@ -238,13 +253,14 @@ __global__ void __launch_bounds__(256) native_batched(const NativeArgs* calls, c
   }
 }
 
-__global__ void repair_prep_batched(const RepairJob* jobs, int njobs, double target) {
+__global__ void repair_prep_batched(const RepairJob* jobs, int njobs, double target, int* any_rerun) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= njobs) return;
   const RepairJob J = jobs[i];
   const double e = J.err ? *J.err : 0.0;
   const bool bad = J.auto_mode && !(J.nonfinite && *J.nonfinite) && !(e <= target);
   *J.skip2 = bad ? 0 : 1;
+  if (bad && any_rerun != nullptr) atomicOr(any_rerun, 1);
 }
 
 // unit = 256 elements of one automatic, beta != 0 call
@@ -264,9 +280,10 @@ __global__ void save_restore_batched(const RepairJob* jobs, const int64_t* prefi
 
 }  // namespace
 
-cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, cudaStream_t st) {
+cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, int* any_rerun,
+                                       cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  { repair_prep_batched<<<(njobs + 127) / 128, 128, 0, st>>>(jobs_dev, njobs, target); note_launch(); }
+  { repair_prep_batched<<<(njobs + 127) / 128, 128, 0, st>>>(jobs_dev, njobs, target, any_rerun); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -282,8 +299,11 @@ cudaError_t launch_rowmax_batched(const SplitArgs* jobs_dev, const int2* units_d
   return cudaGetLastError();
 }
 
-cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st) {
-  if (units > 0) { digits_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, units_dev); note_launch(); }
+cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, const int* run,
+                                  int grid_cap, cudaStream_t st) {
+  if (units <= 0) return cudaSuccess;
+  const int64_t grid = grid_cap > 0 && units > grid_cap ? grid_cap : units;
+  { digits_batched<<<(unsigned)grid, 256, 0, st>>>(jobs_dev, units_dev, units, run); note_launch(); }
   return cudaGetLastError();
 }
 
@@ -292,14 +312,14 @@ cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_u
   if (rowmax_units > 0) { rowmax_batched<<<(unsigned)rowmax_units, 256, 0, st>>>(jobs_dev, rowmax_units_dev); note_launch(); }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (digit_units > 0) { digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_units_dev); note_launch(); }
+  if (digit_units > 0) { digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_units_dev, digit_units, nullptr); note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_native_batched(const NativeArgs* calls_dev, int ncalls, const int* const* flags_dev, int* list_dev,
                                   int64_t* prefix_dev, int64_t* total_dev, int grid, cudaStream_t st) {
   if (ncalls <= 0) return cudaSuccess;
-  { native_compact<<<1, 32, 0, st>>>(calls_dev, ncalls, flags_dev, list_dev, prefix_dev, total_dev); note_launch(); }
+  { native_compact<<<1, 1024, 0, st>>>(calls_dev, ncalls, flags_dev, list_dev, prefix_dev, total_dev); note_launch(); }
   { native_batched<<<grid, 256, 0, st>>>(calls_dev, list_dev, prefix_dev, total_dev); note_launch(); }
   return cudaGetLastError();
 }

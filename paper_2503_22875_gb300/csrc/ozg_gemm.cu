@@ -25,11 +25,11 @@
 //
 // Warp roles (384 threads = 3 warpgroups, one CTA per SM, persistent over tiles):
 //   warpgroup 0: warp 0 TMA producer (one lane), warp 1 TMEM allocator + MMA issuer (one lane),
-//                warps 2-3 idle; the group shrinks its registers to 40 (setmaxnreg.dec)
-//   warpgroups 1-2 (warps 4..11): epilogue, grown to 232 registers (setmaxnreg.inc) to hold the
+//                warps 2-3 idle; the group shrinks its registers to 56 (setmaxnreg.dec)
+//   warpgroups 1-2 (warps 4..11): epilogue, grown to 224 registers (setmaxnreg.inc) to hold the
 //                int32 group sums; warp w reads TMEM lanes 32 (w % 4) .. +31 and half
 //                (w - 4) / 4 of the BN columns.
-// Register budget: 384 threads x 168 at launch = 64512 = 128 x 40 + 256 x 232.
+// Register budget: 384 threads x 168 at launch = 64512 = 128 x 56 + 256 x 224.
 //
 // Two tile widths (BN = 256 or 128; the autotuner picks per shape) and two work sources: one
 // GEMM (tiles rastered in GROUP_M row bands), or a grouped list of tiles drawn from many GEMMs,
@@ -44,7 +44,7 @@ namespace {
 constexpr int BM = 128, BK = 64;  // BK: k width of one 128-byte swizzle atom (one TMA box)
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 128 + EPI_WARPS * 32;
-constexpr int REG_PRODUCER = 40, REG_EPILOGUE = 232;
+constexpr int REG_PRODUCER = 56, REG_EPILOGUE = 224;
 static_assert(128 * REG_PRODUCER + EPI_WARPS * 32 * REG_EPILOGUE <= THREADS * 168, "register split");
 constexpr int TRING = 4;       // tile-index ring depth (grouped launches)
 constexpr int CHAIN_K = 1024;  // products per accumulation chain: 1024 * 127^2 = 16516096 < 2^24
@@ -895,6 +895,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 template <int BN_, int SUB_>
 __global__ void __launch_bounds__(THREADS, 1) slice_gemm_grouped_kernel(const GroupArgs G) {
+  if (G.run != nullptr && *G.run == 0) return;  // a re-run launch with nothing to re-run
   gemm_body<BN_, SUB_, true>(nullptr, nullptr, nullptr, &G);
 }
 

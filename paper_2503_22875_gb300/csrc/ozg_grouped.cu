@@ -79,7 +79,8 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oFlags), 0, P.flags_bytes, st));
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
-  OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oCounter), 0, sizeof(int) * 2, st));
+  // [0], [1]: tile counters of the main and the re-run launch; [2]: "some call is re-run"
+  OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oCounter), 0, sizeof(int) * 3, st));
   if (!P.any_auto) {
     OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units,
                                   gat<int2>(c, P.oDgTab), P.digit_units, st));
@@ -89,7 +90,8 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
     OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
     OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, st));
     OZG_CUDA(launch_select_batched(c->dsel, gat<SelectJob>(c, P.oSel), P.ncalls, (float)std::log10(c->target), st));
-    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, st));
+    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, nullptr, 0,
+                                   st));
     OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
                                          P.ncalls, 0, st));
   }
@@ -112,13 +114,16 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   if (P.nsamp > 0)
     OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, P.oChecks), P.ncalls, P.nsamp, gat<double>(c, P.oErrs), st));
   if (P.any_auto) {  // the check judges the selector: re-run rejected calls at the fallback count
-    OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, P.oRep), P.ncalls, c->target, st));
+    OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, P.oRep), P.ncalls, c->target, gat<int>(c, P.oCounter) + 2,
+                                        st));
     OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
                                          P.ncalls, 1, st));
-    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs2), gat<int2>(c, P.oDgTab), P.digit_units, st));
+    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs2), gat<int2>(c, P.oDgTab), P.digit_units,
+                                   gat<int>(c, P.oCounter) + 2, 8 * c->num_sms, st));
     GroupArgs g2 = g;
     g2.calls = gat<GroupCall>(c, P.oCalls2);
     g2.tile_counter = gat<int>(c, P.oCounter) + 1;
+    g2.run = gat<int>(c, P.oCounter) + 2;
     {
       PhaseScope ps(c, OZG_PHASE_GEMM);
       OZG_CUDA(launch_slice_gemm_grouped(g2, P.variant, P.grid, st));
@@ -217,7 +222,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->oErrs = cv.take(sizeof(double) * count);
   P->oCold = cv.take(sizeof(double) * 2 * (size_t)std::max(nsamp, 1) * count);
   P->oR = cv.take((size_t)P->grid * 128 * 256 * 16);
-  P->oCounter = cv.take(sizeof(int) * 2);  // tile counters of the main and the re-run launch
+  P->oCounter = cv.take(sizeof(int) * 3);  // tile counters (main, re-run) and the re-run flag
   std::vector<int64_t> sp(count + 1, 0);
   std::vector<size_t> oSv(count, 0);
   if (any_auto) {

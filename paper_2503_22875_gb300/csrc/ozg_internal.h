@@ -88,6 +88,7 @@ struct GroupArgs {
   const GroupTile* tiles = nullptr;  // in decreasing cost; CTA b starts with tile b, then claims
   int ntiles = 0;                    // grid + atomicAdd(tile_counter, 1) until the list ends
   int* tile_counter = nullptr;       // zero before the launch
+  const int* run = nullptr;          // if non-null and *run == 0 the launch returns at once
   const GroupCall* calls = nullptr;
   int* status = nullptr;
   double* Rws = nullptr;
@@ -168,7 +169,9 @@ cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_u
 // the two passes separately (row maxima; digits) for batches whose slice counts are chosen
 // between them
 cudaError_t launch_rowmax_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st);
-cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st);
+// run: if non-null and *run == 0 the launch does nothing; grid_cap > 0 bounds the grid (grid-stride)
+cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, const int* run,
+                                  int grid_cap, cudaStream_t st);
 // grouped automatic calls: after the check, skip2[c] = 0 for the calls to re-run (automatic,
 // finite, sampled error above the target), 1 otherwise; save / restore C of automatic calls
 // with beta != 0 (restore only for the calls being re-run)
@@ -181,7 +184,9 @@ struct RepairJob {
   double* saved = nullptr;
   int64_t m = 0, n = 0, ldc = 0;
 };
-cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, cudaStream_t st);
+// sets *any_rerun (zeroed by the caller) when some call is re-run
+cudaError_t launch_repair_prep_batched(const RepairJob* jobs_dev, int njobs, double target, int* any_rerun,
+                                       cudaStream_t st);
 cudaError_t launch_save_restore_batched(const RepairJob* jobs_dev, const int64_t* prefix_dev, int64_t units,
                                         int njobs, int restore, cudaStream_t st);
 // native FP64 for the real calls whose *flags_dev[c] != 0 (list, prefix, total: device scratch
