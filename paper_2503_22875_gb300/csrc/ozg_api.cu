@@ -87,8 +87,11 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   sa.maxbits = at<unsigned long long>(c, oMA);
   sa.exps = at<int32_t>(c, oE);
   sa.nonfinite = nonfinite;
+  // learned count: row maxima -> features -> selection -> digits up to the selected count only
+  int* s_dev = at<int>(c, oSd);  // [0] chosen s, [1] 1 unless the check forced a re-run
+  if (autos) sa.plane_to = s_dev;
   {
-    cudaError_t e = ozg::launch_split(sa, st);
+    cudaError_t e = autos ? ozg::launch_rowmax(sa, st) : ozg::launch_split(sa, st);
     if (e != cudaSuccess) delete split_scope;
     OZG_CUDA(e);
   }
@@ -103,11 +106,10 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   sb.maxbits = at<unsigned long long>(c, oMB);
   sb.exps = at<int32_t>(c, oF);
   {
-    cudaError_t e = ozg::launch_split(sb, st);
+    cudaError_t e = autos ? ozg::launch_rowmax(sb, st) : ozg::launch_split(sb, st);
     delete split_scope;
     OZG_CUDA(e);
   }
-  int* s_dev = at<int>(c, oSd);  // [0] chosen s, [1] 1 unless the check forced a re-run
   if (autos) {
     PhaseScope ps(c, OZG_PHASE_SELECT);
     unsigned long long* hist = at<unsigned long long>(c, oHist);
@@ -118,6 +120,11 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     OZG_CUDA(ozg::launch_gap_hist_pair(ha, hb, st));
     OZG_CUDA(ozg::launch_select_single(c->dsel, hist, hist + 10, m, n, k, (float)std::log10(c->target), s, s_dev,
                                        nullptr, nullptr, st));
+  }
+  if (autos) {
+    PhaseScope ps(c, OZG_PHASE_SPLIT);
+    OZG_CUDA(ozg::launch_digits(sa, st));
+    OZG_CUDA(ozg::launch_digits(sb, st));
   }
 
   CUtensorMap tmA, tmB[2];
@@ -252,6 +259,13 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   if (autos) {  // judged by the check: re-run at the fallback count when the error is too large
     OZG_CUDA(ozg::launch_repair_prep(c->dcheck, c->target, s_dev + 1, at<double>(c, oSaved), C, m, n, ldc,
                                      cplx ? 2 : 1, beta_zero0 ? 0 : 1, st));
+    // the planes above the selected count, for the re-run only
+    ozg::SplitArgs ca = sa, cb = sb;
+    ca.plane_from = cb.plane_from = s_dev;
+    ca.plane_to = cb.plane_to = nullptr;
+    ca.gate = cb.gate = s_dev + 1;
+    OZG_CUDA(ozg::launch_digits(ca, st));
+    OZG_CUDA(ozg::launch_digits(cb, st));
     ozg::GemmArgs g2 = ga;
     g2.s = s_rep;
     g2.s_dev = nullptr;

@@ -31,13 +31,16 @@ struct SplitArgs {
   int32_t* exps = nullptr;        // [rows] output exponents
   int* nonfinite = nullptr;       // set to 1 if any entry is Inf/NaN
   unsigned long long* hist = nullptr;  // selector features: 10 gap-histogram counters (nullable)
-  // batched split only: digit planes t_lo .. t_hi are written, t_lo = (plane_from ? *plane_from + 1
-  // : 1), t_hi = (plane_to ? *plane_to : s); a job whose *gate is non-zero writes nothing
+  // digit planes t_lo .. t_hi are written, t_lo = (plane_from ? *plane_from + 1 : 1),
+  // t_hi = (plane_to ? *plane_to : s); a job whose *gate is non-zero writes nothing
   const int* plane_from = nullptr;
   const int* plane_to = nullptr;
   const int* gate = nullptr;
 };
 cudaError_t launch_split(const SplitArgs& a, cudaStream_t st);
+// the two passes of launch_split (row maxima; digits over the plane range of a)
+cudaError_t launch_rowmax(const SplitArgs& a, cudaStream_t st);
+cudaError_t launch_digits(const SplitArgs& a, cudaStream_t st);
 
 // int8 copy of fp16 digit planes (inspection path): out[p][r][l] = D[p][r][l], l < k
 cudaError_t launch_digits_to_i8(const __half* D, int64_t planes, int64_t plane_rows, int64_t k, int64_t Kp,

@@ -11,6 +11,20 @@
 namespace ozg {
 namespace {
 
+// Digit planes t_lo .. t_hi a launch writes: t_lo = *from + 1 (else 1), t_hi = *to (else s);
+// nothing when *gate is non-zero.
+struct PlaneRange {
+  const int* from;
+  const int* to;
+  const int* gate;
+  __device__ __forceinline__ bool resolve(int s, int& lo, int& hi) const {
+    if (gate != nullptr && *gate) return false;
+    lo = from != nullptr ? *from + 1 : 1;
+    hi = to != nullptr ? *to : s;
+    return lo <= hi;
+  }
+};
+
 __device__ __forceinline__ void flag_nonfinite(uint64_t absbits, int* nonfinite) {
   if (absbits >= kInfBits) atomicExch(nonfinite, 1);
 }
@@ -83,13 +97,15 @@ __global__ void rowmax_strided(const double* __restrict__ X, int64_t ld, int64_t
 template <int CPLX>
 __global__ void digits_contig(const double* __restrict__ X, int64_t ld, int64_t rows, int64_t k, int conj, int s,
                               int64_t Kp, int64_t plane_rows, const unsigned long long* __restrict__ maxbits,
-                              int32_t* __restrict__ exps, __half* __restrict__ D) {
+                              int32_t* __restrict__ exps, __half* __restrict__ D, PlaneRange pr) {
+  int t_lo, t_hi;
+  if (!pr.resolve(s, t_lo, t_hi)) return;
   int64_t groups = (k + 7) / 8;
   int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= rows * groups) return;
   int64_t row = gid / groups, l0 = (gid % groups) * 8;
   int e = exponent_from_maxbits(maxbits[row]);
-  if (l0 == 0) exps[row] = e;
+  if (l0 == 0 && t_lo == 1) exps[row] = e;
   const int nparts = CPLX ? 2 : 1;
   uint64_t bits[2][8];
 #pragma unroll
@@ -109,7 +125,7 @@ __global__ void digits_contig(const double* __restrict__ X, int64_t ld, int64_t 
 #pragma unroll
     for (int j = 0; j < 8; ++j) ds[j] = digit_src(bits[part][j], e);
     int64_t orow = CPLX ? 2 * row + part : row;
-    for (int t = 1; t <= s; ++t)
+    for (int t = t_lo; t <= t_hi; ++t)
       *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0) = digits8(ds, t);
   }
 }
@@ -120,7 +136,10 @@ template <int CPLX>
 __global__ void __launch_bounds__(256) digits_strided(const double* __restrict__ X, int64_t ld, int64_t rows,
                                                       int64_t k, int conj, int s, int64_t Kp, int64_t plane_rows,
                                                       const unsigned long long* __restrict__ maxbits,
-                                                      int32_t* __restrict__ exps, __half* __restrict__ D) {
+                                                      int32_t* __restrict__ exps, __half* __restrict__ D,
+                                                      PlaneRange pr) {
+  int t_lo, t_hi;
+  if (!pr.resolve(s, t_lo, t_hi)) return;
   constexpr int TR = 32, TL = 64;
   constexpr int W = CPLX ? 2 : 1;
   __shared__ uint64_t tile[TL][TR * W + 1];
@@ -150,14 +169,14 @@ __global__ void __launch_bounds__(256) digits_strided(const double* __restrict__
   int lg = (tid % 8) * 8;
   if (row >= rows || l0 + lg >= k) return;
   int e = exponent_from_maxbits(maxbits[row]);
-  if (l0 + lg == 0) exps[row] = e;
+  if (l0 + lg == 0 && t_lo == 1) exps[row] = e;
 #pragma unroll
   for (int part = 0; part < W; ++part) {
     DigitSrc ds[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) ds[j] = digit_src(tile[lg + j][W * r + part], e);
     int64_t orow = CPLX ? 2 * row + part : row;
-    for (int t = 1; t <= s; ++t)
+    for (int t = t_lo; t <= t_hi; ++t)
       *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0 + lg) = digits8(ds, t);
   }
 }
@@ -172,7 +191,7 @@ __global__ void digits_to_i8(const __half* __restrict__ D, int64_t planes_rows, 
 
 }  // namespace
 
-cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
+cudaError_t launch_rowmax(const SplitArgs& a, cudaStream_t st) {
   if (a.rows <= 0) return cudaSuccess;
   cudaError_t err = cudaMemsetAsync(a.maxbits, 0, sizeof(unsigned long long) * a.rows, st);
   if (err != cudaSuccess) return err;
@@ -192,9 +211,13 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
       { rowmax_strided<<<dim3((unsigned)rb, (unsigned)ksplit), 256, 0, st>>>(a.X, a.ld, a.rows, a.k, kchunk, a.cplx,
                                                                            a.maxbits, a.nonfinite); note_launch(); }
     }
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_digits(const SplitArgs& a, cudaStream_t st) {
+  if (a.rows <= 0) return cudaSuccess;
+  const PlaneRange pr{a.plane_from, a.plane_to, a.gate};
   int64_t kk = a.k > 0 ? a.k : 1;
   if (!a.strided || a.k == 0) {
     int64_t groups = (kk + 7) / 8;
@@ -202,20 +225,26 @@ cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
     unsigned grid = (unsigned)((total + 255) / 256);
     if (a.cplx)
       { digits_contig<1><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                             a.exps, a.D); note_launch(); }
+                                             a.exps, a.D, pr); note_launch(); }
     else
       { digits_contig<0><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                             a.exps, a.D); note_launch(); }
+                                             a.exps, a.D, pr); note_launch(); }
   } else {
     dim3 grid((unsigned)((a.rows + 31) / 32), (unsigned)((a.k + 63) / 64));
     if (a.cplx)
       { digits_strided<1><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                              a.exps, a.D); note_launch(); }
+                                              a.exps, a.D, pr); note_launch(); }
     else
       { digits_strided<0><<<grid, 256, 0, st>>>(a.X, a.ld, a.rows, a.k, a.conj, a.s, a.Kp, a.plane_rows, a.maxbits,
-                                              a.exps, a.D); note_launch(); }
+                                              a.exps, a.D, pr); note_launch(); }
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_split(const SplitArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_rowmax(a, st);
+  if (e != cudaSuccess) return e;
+  return launch_digits(a, st);
 }
 
 cudaError_t launch_digits_to_i8(const __half* D, int64_t planes, int64_t plane_rows, int64_t k, int64_t Kp,

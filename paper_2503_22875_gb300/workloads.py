@@ -8,11 +8,15 @@ can feed both the CUDA path and the CPU oracle.  numpy PCG64 generators with fix
   kkr_like_pair         complex n = 113 blocks x 32, block (i,j) ~ CN(0,1) exp(-|r_i - r_j|)
                         with atom sites r ~ U(cube of unit density) plus (1 + 0.1i) on the
                         diagonal -- stands in for the MuST "MT u56" ZGEMMs of Sec. 3.2
+  kkr_kappa_pair        the same with A's diagonal shift moved next to an eigenvalue of the
+                        unshifted matrix so that cond_2(A) ~ 1e8 (shift found once, cached)
   grouped_batch         2048 GEMMs, m, n, k log-uniform in [32, 2048], phi ~ U(0, 4) per call
                         (grouped_batch_flat: the same batch drawn on the GPU into flat buffers)
 """
 from __future__ import annotations
 
+import json
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -58,6 +62,71 @@ def kkr_like_pair(nblk: int = 113, bs: int = 32, seed: int = 3, shift: complex =
     A = _kkr_matrix(nblk, bs, g, shift)
     B = _kkr_matrix(nblk, bs, g, shift)
     return A, B
+
+
+KAPPA_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "kkr_kappa_shift.json")
+
+
+def _cond2(M) -> float:
+    sv = np.linalg.svd(M, compute_uv=False)
+    return float(sv[0] / sv[-1])
+
+
+def kkr_kappa_shift(nblk: int = 113, bs: int = 32, seed: int = 3, kappa: float = 1e8, cache: str = KAPPA_CACHE,
+                    log=None) -> complex:
+    """Diagonal shift of A (the first matrix of kkr_like_pair) for which cond_2(A) is within a
+    factor 1.5 of `kappa`: shift = -lambda + t u, with lambda the eigenvalue of the unshifted
+    matrix M nearest to -(1 + 0.1i) and u the unit direction from -lambda towards 1 + 0.1i;
+    t by bisection on log t (cond_2 grows without bound as t -> 0).  Computed once per
+    (nblk, bs, seed, kappa) with LAPACK on the host and cached as JSON."""
+    key = f"{nblk}x{bs}:seed{seed}:kappa{kappa:g}"
+    table = {}
+    if os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+    if key in table:
+        return complex(table[key]["re"], table[key]["im"])
+    g = rng(seed)
+    M = _kkr_matrix(nblk, bs, g, 0.0)
+    lam = np.linalg.eigvals(M)
+    base = -(1.0 + 0.1j)
+    l0 = lam[np.argmin(np.abs(lam - base))]
+    u = ((1.0 + 0.1j) - (-l0)) / abs((1.0 + 0.1j) - (-l0))
+    n = M.shape[0]
+    idx = np.arange(n)
+
+    def cond_at(t):
+        A = M.copy()
+        A[idx, idx] += -l0 + t * u
+        return _cond2(A)
+    lo, hi = 1e-12, abs((1.0 + 0.1j) + l0)  # cond(lo) >> kappa, cond(hi) = the base matrix's
+    for _ in range(40):
+        mid = np.sqrt(lo * hi)
+        c = cond_at(mid)
+        if log:
+            log(f"  t = {mid:.3e}: cond_2 = {c:.3e}")
+        if c > kappa:
+            lo = mid
+        else:
+            hi = mid
+        if kappa / 1.5 <= c <= kappa * 1.5:
+            break
+    shift = complex(-l0 + mid * u)
+    table[key] = {"re": shift.real, "im": shift.imag, "cond2": c, "t": mid}
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    with open(cache, "w") as f:
+        json.dump(table, f, indent=1)
+    return shift
+
+
+def kkr_kappa_pair(nblk: int = 113, bs: int = 32, seed: int = 3, kappa: float = 1e8):
+    """kkr_like_pair with A's diagonal shift replaced so that cond_2(A) ~ kappa."""
+    g = rng(seed)
+    M = _kkr_matrix(nblk, bs, g, 0.0)
+    B = _kkr_matrix(nblk, bs, g, 1.0 + 0.1j)
+    n = M.shape[0]
+    M[np.arange(n), np.arange(n)] += kkr_kappa_shift(nblk, bs, seed, kappa)
+    return np.asfortranarray(M), B
 
 
 @dataclass

@@ -391,3 +391,16 @@ def test_zemu_error_bound_and_alpha_beta():
     C0 = rng.normal(size=(m, n)) + 1j * rng.normal(size=(m, n))
     C2 = oracle.zgemm_emu(A, B, s, alpha=al, beta=be, C=C0)
     np.testing.assert_allclose(C2, al * C + be * C0, rtol=1e-13, atol=1e-13)
+
+
+def test_kkr_kappa_variant_has_the_requested_condition_number():
+    """The KKR-like stand-in's conditioned variant: the cached diagonal shift puts cond_2(A)
+    within a factor 1.5 of 1e8 (SVD on the host), and B is the unshifted-workload's B."""
+    from paper_2503_22875_gb300 import workloads
+    A, B = workloads.kkr_kappa_pair(113, 32, seed=3, kappa=1e8)
+    A0, B0 = workloads.kkr_like_pair(113, 32, seed=3)
+    assert np.array_equal(B, B0)
+    off = ~np.eye(A.shape[0], dtype=bool)
+    assert np.array_equal(A[off], A0[off])  # only the diagonal shift differs
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert 1e8 / 1.5 <= sv[0] / sv[-1] <= 1e8 * 1.5
