@@ -293,6 +293,31 @@ __device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long 
   return __longlong_as_double(neg ? (r | (long long)0x8000000000000000ull) : r);
 }
 
+// RN(N 2^E) for N = W0 2^S + W1 (S = 7 wlen in [7, 56], |W0|, |W1| < 2^62; W0 = 0 for a single
+// window) without data-dependent branches, so the outputs of a chunk interleave.  With
+// q = W0 + floor(W1 / 2^S) and r = W1 mod 2^S, N = q 2^S + r (0 <= r < 2^S) and
+// |N| = qm 2^S + rm with qm = q, rm = r for q >= 0 and qm = -q - 1, rm = 2^S - r (r > 0) or
+// qm = -q, rm = 0 (r = 0) for q < 0.  The top 63 bits of |N| with a sticky bit below them are
+// converted with one correctly rounded conversion and the power of two goes into the exponent
+// field.  `ok` is false when the result is not a normal double (the caller takes final_val).
+__device__ __forceinline__ double rn_windows(long long W0, long long W1, int S, int E, bool& ok) {
+  const long long q = W0 + (W1 >> S);
+  const unsigned long long mask = (1ull << S) - 1ull;
+  const unsigned long long r = (unsigned long long)W1 & mask;
+  const bool neg = q < 0;
+  const unsigned long long qm = neg ? (unsigned long long)(~q) + (r == 0 ? 1ull : 0ull) : (unsigned long long)q;
+  const unsigned long long rm = neg ? ((0ull - r) & mask) : r;
+  const int bl = 64 - __clzll((long long)qm);  // 0 .. 63
+  const int z = max(0, bl + S - 63);           // low bits of |N| below the 63-bit window (<= S)
+  const unsigned long long t =
+      (qm << (S - z)) | (rm >> z) | ((rm & ((1ull << z) - 1ull)) != 0 ? 1ull : 0ull);
+  const long long bits = __double_as_longlong(__ull2double_rn(t));
+  const int ex = (int)(bits >> 52) + z + E;  // biased exponent of the result
+  ok = t == 0 || (ex >= 1 && ex <= 2046);
+  const long long rb = bits + ((long long)(z + E) << 52);
+  return t == 0 ? 0.0 : __longlong_as_double(neg ? (rb | (long long)0x8000000000000000ull) : rb);
+}
+
 // Window-closing or final step of one output, given the first slot's word s0 (int64 W0 while
 // widx == 1, FP64 bits from the second window's close on) and the active window Rw after this
 // push.  Final: returns RN(N 2^E).  Closing: returns the new s0 word.
@@ -419,43 +444,72 @@ __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushAr
   } else {
     prefetch_close<NCH>(a, j, o0, s0, fe);
   }
-  if (a.kind == kClose) {
-#pragma unroll
-    for (int i = 0; i < NCH; ++i) a.S0[(size_t)(o0 + i) * BM] = close_val(s0[i], rw[i], a.widx, a.wlen);
-    return;
-  }
+  // RN of the exact sum: for one or two windows all NCH outputs go through the branch-free
+  // rounding together, and only results outside the normal range take the general path
+  // (in batches of RB outputs, to bound the registers live at once)
+  constexpr int RB = NCH < 8 ? NCH : 8;
   const int64_t c0 = j.cplx ? (a.gcol0 >> 1) + o0 : a.gcol0 + o0;
-  if (!j.cplx) {
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-      const int64_t col = c0 + i;
-      if (a.row_ok && col < j.cols) {
-        const double tv = final_val(s0[i], rw[i], a.widx, a.wlen, a.ebase + fe[i]);
-        double* cp = j.C + a.orow + col * j.ldc;
-        *cp = a.unit_ab ? tv : (j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp));
+  for (int i0 = 0; i0 < NCH; i0 += RB) {
+    double tv[RB];
+    if (a.widx <= 1) {
+      const bool close = a.kind == kClose;
+      unsigned bad = 0;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        bool ok;
+        tv[i] = rn_windows(a.widx == 0 ? 0ll : s0[i0 + i], rw[i0 + i], 7 * a.wlen, close ? 0 : a.ebase + fe[i0 + i], ok);
+        bad |= ok ? 0u : 1u << i;
       }
-    }
-  } else {
+      if (bad != 0) {
 #pragma unroll
-    for (int i = 0; i < NCH; ++i) {
-      const int64_t jc = c0 + i;
-      const bool ok = a.row_ok && jc < j.n;
-      const double part = ok ? final_val(s0[i], rw[i], a.widx, a.wlen, a.ebase + fe[i]) : 0.0;
-      const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
-      if (ok) {
-        double* cp = j.C + 2 * (a.orow + jc * j.ldc);
-        if (a.unit_ab) {
-          cp[a.odd ? 1 : 0] = part;
-        } else {
-          const double tr = a.odd ? partner : part, ti = a.odd ? part : partner;
-          double re = fma(j.a0, tr, -(j.a1 * ti));
-          double im = fma(j.a0, ti, j.a1 * tr);
-          if (!j.beta_zero) {
-            const double cr = cp[0], ci = cp[1];
-            re += fma(j.b0, cr, -(j.b1 * ci));
-            im += fma(j.b0, ci, j.b1 * cr);
+        for (int i = 0; i < RB; ++i)
+          if ((bad >> i) & 1u)
+            tv[i] = close ? __longlong_as_double(close_val(s0[i0 + i], rw[i0 + i], a.widx, a.wlen))
+                          : final_val(s0[i0 + i], rw[i0 + i], a.widx, a.wlen, a.ebase + fe[i0 + i]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+        tv[i] = a.kind == kClose ? __longlong_as_double(close_val(s0[i0 + i], rw[i0 + i], a.widx, a.wlen))
+                                 : final_val(s0[i0 + i], rw[i0 + i], a.widx, a.wlen, a.ebase + fe[i0 + i]);
+    }
+    if (a.kind == kClose) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) a.S0[(size_t)(o0 + i0 + i) * BM] = __double_as_longlong(tv[i]);
+      continue;
+    }
+    if (!j.cplx) {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int64_t col = c0 + i0 + i;
+        if (a.row_ok && col < j.cols) {
+          double* cp = j.C + a.orow + col * j.ldc;
+          *cp = a.unit_ab ? tv[i] : (j.beta_zero ? j.a0 * tv[i] : fma(j.a0, tv[i], j.b0 * *cp));
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        const int64_t jc = c0 + i0 + i;
+        const bool ok = a.row_ok && jc < j.n;
+        const double part = ok ? tv[i] : 0.0;
+        const double partner = __shfl_xor_sync(0xffffffffu, part, 1);
+        if (ok) {
+          double* cp = j.C + 2 * (a.orow + jc * j.ldc);
+          if (a.unit_ab) {
+            cp[a.odd ? 1 : 0] = part;
+          } else {
+            const double tr = a.odd ? partner : part, ti = a.odd ? part : partner;
+            double re = fma(j.a0, tr, -(j.a1 * ti));
+            double im = fma(j.a0, ti, j.a1 * tr);
+            if (!j.beta_zero) {
+              const double cr = cp[0], ci = cp[1];
+              re += fma(j.b0, cr, -(j.b1 * ci));
+              im += fma(j.b0, ci, j.b1 * cr);
+            }
+            cp[a.odd ? 1 : 0] = a.odd ? im : re;
           }
-          cp[a.odd ? 1 : 0] = a.odd ? im : re;
         }
       }
     }

@@ -63,8 +63,13 @@ std::vector<GroupTile> ordered_tiles(const ozg_gemm_desc* d, const std::vector<i
   const int BN = tile_n_of(variant & 1);
   std::vector<T> all;
   for (int64_t c = 0; c < count; ++c) {
-    const int64_t tm = (d[c].m + 127) / 128, tn = (d[c].n + BN - 1) / BN, kb = (d[c].k + 63) / 64;
-    const double cost = (double)(s[c] * (s[c] + 1) / 2 * kb + 2 * s[c]) * BN;
+    const int64_t tm = (d[c].m + 127) / 128, tn = (d[c].n + BN - 1) / BN;
+    // per tile, the same for all tiles of a call (they stay together): slice products x k
+    // (in 16-wide steps) plus the epilogue's per-group work, times the call's mean valid tile
+    // width (16-column steps) -- an estimate that orders measurably better than the padded width
+    const double kb = (double)((d[c].k + 15) / 16) / 4.0;
+    const double w = (double)((d[c].n + 15) / 16 * 16) / (double)tn;
+    const double cost = ((double)(s[c] * (s[c] + 1) / 2) * kb + 2 * s[c]) * w;
     for (int64_t i = 0; i < tm; ++i)
       for (int64_t j = 0; j < tn; ++j) all.push_back({cost, {(int)c, (int)i, (int)j, 0}});
   }

@@ -180,3 +180,51 @@ def test_tile_variants_bit_identical(ozg):
     assert (np.abs(C - E) <= 4 * (s + 2) * U * 0.5 * AB + 2 * U * np.abs(E) + 2 * U * 0.75 * np.abs(C0)).all()
     with pytest.raises(ozg.OzgError):
         ozg.Context().set_tile_variant(4)
+
+
+NARROW_SHAPES = [(130, 1, 17), (33, 17, 1), (97, 40, 70), (1, 65, 33), (130, 161, 130), (65, 304, 47),
+                 (200, 100, 1000), (129, 48, 16)]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_narrow_tiles_ragged_k_bit_exact(ozg, variant):
+    """Narrow last column tiles (1 .. 48 valid columns of a 128- or 256-wide tile), k ending
+    inside a 16-wide step or a 64-wide TMA box, and row tiles with one to a few valid rows: in
+    every tile variant, single real and complex calls and a grouped batch of the same shapes
+    equal the oracle bit for bit (s = 7 uses at most two exact windows at any k)."""
+    s = 7
+    ctx = ozg.Context()
+    ctx.set_tile_variant(variant)
+    try:
+        batch = []
+        for i, (m, n, k) in enumerate(NARROW_SHAPES):
+            g = workloads.rng(900 + i)
+            A = np.asfortranarray(workloads.wide_exponent((m, k), 2.0, g))
+            B = np.asfortranarray(workloads.wide_exponent((k, n), 2.0, g))
+            C0 = np.asfortranarray(g.uniform(-1, 1, (m, n)))
+            dC = ozg.to_device(C0)
+            ctx.dgemm("N", "N", m, n, k, -0.5, ozg.to_device(A), m, ozg.to_device(B), k, 0.75, dC, m, s)
+            ctx.sync()
+            E = oracle.dgemm_emu(A, B, s, "N", "N", -0.5, 0.75, C0)
+            assert np.array_equal(ozg.from_device(dC, m, n), E), (m, n, k)
+            batch.append(dict(ta="N", tb="N", m=m, n=n, k=k, s=s, alpha=-0.5, beta=0.75, A=A, B=B, C0=C0,
+                              dA=ozg.to_device(A), dB=ozg.to_device(B), dC=ozg.to_device(C0)))
+        ctx.dgemm_grouped(calls_of(batch), [s] * len(batch))
+        ctx.sync()
+        for b in batch:
+            E = oracle.dgemm_emu(b["A"], b["B"], s, "N", "N", -0.5, 0.75, b["C0"])
+            assert np.array_equal(ozg.from_device(b["dC"], b["m"], b["n"]), E), (b["m"], b["n"], b["k"])
+        for i, (m, n, k) in enumerate([(45, 9, 23), (130, 70, 50), (3, 130, 17)]):
+            g = workloads.rng(950 + i)
+            A = np.asfortranarray(workloads.wide_exponent((m, k), 1.0, g) + 1j * workloads.wide_exponent((m, k), 1.0, g))
+            B = np.asfortranarray(workloads.wide_exponent((k, n), 1.0, g) + 1j * workloads.wide_exponent((k, n), 1.0, g))
+            C0 = np.asfortranarray(g.normal(size=(m, n)) + 1j * g.normal(size=(m, n)))
+            dC = ozg.to_device(C0)
+            ctx.zgemm("N", "T" if i == 1 else "N", m, n, k, 0.5 - 2j, ozg.to_device(A), m,
+                      ozg.to_device(np.asfortranarray(B.T) if i == 1 else B), n if i == 1 else k, 1.5 + 0.25j, dC, m, s)
+            ctx.sync()
+            E = oracle.zgemm_emu(A, np.asfortranarray(B.T) if i == 1 else B, s, "N", "T" if i == 1 else "N",
+                                 0.5 - 2j, 1.5 + 0.25j, C0)
+            assert np.array_equal(ozg.from_device(dC, m, n), E), (m, n, k)
+    finally:
+        ctx.close()
