@@ -224,7 +224,8 @@ struct SelectJob {
   int s_cap = 0, active = 0;
 };
 cudaError_t launch_gap_hist_pair(const SplitArgs& a, const SplitArgs& b, cudaStream_t st);
-cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* digit_units_dev, int64_t units,
+// the features of every job with a histogram, over the row-maximum unit table
+cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t units,
                                     cudaStream_t st);
 // M may be null: then only feat_out is written
 cudaError_t launch_select_single(const SelectorDev* M, const unsigned long long* hA, const unsigned long long* hB,

@@ -79,10 +79,27 @@ __global__ void __launch_bounds__(256) gap_hist_pair(SplitArgs a, SplitArgs b, i
 }
 
 
-// Batched features: a unit is 32 rows x kDgK k of a job (the digit units).  Each thread bins
-// its elements into ten 6-bit counters packed in one 64-bit word (at most 32 elements per
-// thread), the warp sums them with integer reductions, and one shared-memory add per bin and
+// Batched features over the row-maximum units (32 rows x kRmStridedK k of a strided job, each
+// thread one row and 16 of its elements; 8 rows x kRmContigK k of a contiguous job, each warp
+// one row and each thread 32 of its elements), so every thread reads its row's exponent once.
+// Each thread bins its elements into ten 6-bit counters packed in one 64-bit word (at most 32
+// elements), the warp sums them with integer reductions, and one shared-memory add per bin and
 // warp precedes one global add per bin and CTA.
+__device__ __forceinline__ int gap_bin(uint64_t b, int e_row) {
+  if (b == 0) return 9;
+  const int gap = e_row - exp_of_bits(b);
+  return gap < 36 ? (gap < 0 ? 0 : gap / 4) : 9;
+}
+__device__ __forceinline__ uint64_t abs_bits(const SplitArgs& J, int64_t row, int64_t l) {
+  if (!J.cplx) {
+    const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
+    return __ldg(J.strided ? X + row + l * J.ld : X + l + row * J.ld) & kAbsMask;
+  }
+  const ulonglong2* X = reinterpret_cast<const ulonglong2*>(J.X);
+  const ulonglong2 v = __ldg(J.strided ? X + row + l * J.ld : X + l + row * J.ld);
+  const uint64_t x = v.x & kAbsMask, y = v.y & kAbsMask;
+  return x > y ? x : y;
+}
 __global__ void __launch_bounds__(256) gap_hist_batched(const SplitArgs* jobs, const int2* units) {
   __shared__ unsigned int sh[10];
   if (threadIdx.x < 10) sh[threadIdx.x] = 0;
@@ -90,39 +107,36 @@ __global__ void __launch_bounds__(256) gap_hist_batched(const SplitArgs* jobs, c
   const int2 ur = units[blockIdx.x];
   const SplitArgs J = jobs[ur.x];
   if (J.hist != nullptr) {
-    const int64_t ktiles = (J.k + kDgK - 1) / kDgK;
-    const int64_t r0 = (ur.y / ktiles) * 32, lbase = (ur.y % ktiles) * kDgK;
-    const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long packed = 0;
-    int e_row = 0;
-    int64_t cached = -1;
-    for (int q = 0; q < kDgK / 8; ++q) {  // 32 elements per thread
-      const int idx = q * 256 + threadIdx.x;
-      int64_t row, l;
-      if (J.strided) {
-        row = r0 + idx % 32;
-        l = lbase + idx / 32;
-      } else {
-        row = r0 + idx / kDgK;
-        l = lbase + idx % kDgK;
+    if (J.strided) {
+      const int64_t kt = (J.k + kRmStridedK - 1) / kRmStridedK;
+      const int64_t row = (ur.y / kt) * 32 + lane, l0 = (ur.y % kt) * kRmStridedK + w;
+      if (row < J.rows) {
+        const int e_row = exponent_from_maxbits(J.maxbits[row]);
+#pragma unroll
+        for (int i = 0; i < kRmStridedK / 8; ++i) {
+          const int64_t l = l0 + 8 * i;
+          if (l < J.k) packed += 1ull << (6 * gap_bin(abs_bits(J, row, l), e_row));
+        }
       }
-      if (row >= J.rows || l >= J.k) continue;
-      const uint64_t b = __ldg(J.strided ? X + row + l * J.ld : X + l + row * J.ld) & kAbsMask;
-      if (row != cached) {
-        e_row = exponent_from_maxbits(J.maxbits[row]);
-        cached = row;
+    } else {
+      const int64_t kt = (J.k + kRmContigK - 1) / kRmContigK;
+      const int64_t row = (ur.y / kt) * 8 + w, l0 = (ur.y % kt) * kRmContigK + lane;
+      if (row < J.rows) {
+        const int e_row = exponent_from_maxbits(J.maxbits[row]);
+#pragma unroll 8
+        for (int i = 0; i < kRmContigK / 32; ++i) {
+          const int64_t l = l0 + 32 * i;
+          if (l < J.k) packed += 1ull << (6 * gap_bin(abs_bits(J, row, l), e_row));
+        }
       }
-      int bin = 9;
-      if (b != 0) {
-        const int gap = e_row - exp_of_bits(b);
-        bin = gap < 36 ? (gap < 0 ? 0 : gap / 4) : 9;
-      }
-      packed += 1ull << (6 * bin);
     }
+    static_assert(kRmStridedK / 8 <= 63 && kRmContigK / 32 <= 63, "6-bit counters");
 #pragma unroll
     for (int bin = 0; bin < 10; ++bin) {
       const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)((packed >> (6 * bin)) & 63ull));
-      if ((threadIdx.x & 31) == 0 && v) atomicAdd(&sh[bin], v);
+      if (lane == 0 && v) atomicAdd(&sh[bin], v);
     }
   }
   __syncthreads();
@@ -340,10 +354,10 @@ cudaError_t launch_gap_hist_pair(const SplitArgs& a, const SplitArgs& b, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* digit_units_dev, int64_t units,
+cudaError_t launch_gap_hist_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t units,
                                     cudaStream_t st) {
   if (units <= 0) return cudaSuccess;
-  { gap_hist_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, digit_units_dev); note_launch(); }
+  { gap_hist_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, rowmax_units_dev); note_launch(); }
   return cudaGetLastError();
 }
 
