@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--only-single", action="store_true", help="run only the single-DGEMM section (profiling)")
     ap.add_argument("--no-zgemm", action="store_true", help="skip the KKR-like ZGEMM section")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end number")
+    ap.add_argument("--no-shim", action="store_true", help="skip the BLAS shim data-strategy section")
+    ap.add_argument("--shim-size", type=int, default=8192, help="n of the shim's n^3 DGEMM")
     return ap.parse_args()
 
 
@@ -338,6 +340,59 @@ def parse_list(spec, cast):
         a, b = spec.split("-")
         return list(range(int(a), int(b) + 1))
     return [cast(x) for x in spec.split(",")]
+
+
+def shim_section(torch, n, reps=3):
+    """The BLAS interposition library's three data strategies (Sec. 2.1) on an n^3 DGEMM called
+    through dgemm_ on arrays in pageable host memory, at s = 7: wall-clock time of each
+    synchronous call.  copy: staging through pinned buffers; coherent: the kernels read and write
+    the host arrays in place over the CPU-GPU link; migrate: the first call moves the arrays'
+    pages to GPU memory, later calls find them there."""
+    import ctypes
+
+    from paper_2503_22875_gb300 import build
+    lib = ctypes.CDLL(build.SHIM_LIB)
+    lib.ozg_blas_set_mode.argtypes = [ctypes.c_int]
+    lib.ozg_blas_set_strategy.argtypes = [ctypes.c_int]
+    lib.ozg_blas_migrated_bytes.restype = ctypes.c_longlong
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(77)
+
+    def draw():  # a = (u - 0.5) exp(0.5 g), drawn on the GPU, returned in pageable host memory
+        u = torch.rand((n, n), generator=gen, device="cuda", dtype=torch.float64)
+        z = torch.randn((n, n), generator=gen, device="cuda", dtype=torch.float64)
+        return ((u - 0.5) * torch.exp(0.5 * z)).cpu().numpy()
+    A, B = draw(), draw()
+    torch.cuda.empty_cache()
+    ci, cd = ctypes.c_int, ctypes.c_double
+    one, zero, nn = cd(1.0), cd(0.0), ci(n)
+
+    def call(C):
+        lib.dgemm_(b"N", b"N", ctypes.byref(nn), ctypes.byref(nn), ctypes.byref(nn), ctypes.byref(one),
+                   ctypes.c_void_p(A.ctypes.data), ctypes.byref(nn), ctypes.c_void_p(B.ctypes.data), ctypes.byref(nn),
+                   ctypes.byref(zero), ctypes.c_void_p(C.ctypes.data), ctypes.byref(nn), ctypes.c_size_t(1),
+                   ctypes.c_size_t(1))
+    names = {0: "copy", 1: "coherent", 2: "migrate"}
+    out = {"workload": f"dgemm_ {n}^3 through libozg_blas.so on pageable host arrays, OZG_COMPUTE_MODE=fp64_int8_7, "
+                       "beta = 0, wall-clock per synchronous call", "slices": 7}
+    lib.ozg_blas_set_mode(7)
+    flops = 2.0 * n ** 3
+    for st, name in names.items():
+        lib.ozg_blas_set_strategy(st)
+        C = np.zeros((n, n))
+        times = []
+        for _ in range(reps + 1):
+            t0 = time.perf_counter()
+            call(C)
+            times.append(time.perf_counter() - t0)
+        steady = float(np.median(times[1:]))
+        entry = {"strategy_in_effect": names.get(lib.ozg_blas_get_strategy(), "?"), "first_call_ms": times[0] * 1e3,
+                 "steady_ms": steady * 1e3, "steady_tflops": flops / steady / 1e12}
+        if st == 2:
+            entry["migrated_bytes"] = int(lib.ozg_blas_migrated_bytes())
+        out[name] = entry
+    lib.ozg_blas_set_strategy(0)
+    return out
 
 
 def single_section(ozg, torch, size, steps, phis=SINGLE_PHIS, slice_list=tuple(range(3, 11))):
@@ -634,6 +689,7 @@ def run_gpu(args):
                                                         parse_list(args.single_phis, float),
                                                         parse_list(args.single_slices, int))
     zgemm = None if args.no_zgemm else zgemm_section(ozg, torch, max(1, min(args.steps, 3)))
+    shim = None if (world > 1 or args.no_shim) else shim_section(torch, args.shim_size)
     cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(args.count)
 
     line = {
@@ -655,6 +711,7 @@ def run_gpu(args):
         "compare": compare,
         "single_dgemm": single,
         "zgemm_kkr": zgemm,
+        "blas_shim_strategies": shim,
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -7,11 +7,27 @@
  * interposition layer for this library: preloaded (LD_PRELOAD=.../libozg_blas.so) or linked
  * before the CPU BLAS, its dgemm_ / zgemm_ replace the BLAS symbols of the same name.
  *
- * Each call copies op(A), op(B) (and C when beta != 0) from the caller's HOST memory through
- * pinned staging buffers to the GPU, runs ozg_dgemm / ozg_zgemm on the current device, copies C
- * back and returns when C is final (synchronous, like BLAS).  Rows m..ldc-1 of C are never
- * written.  Argument errors print the BLAS xerbla message on stderr and return with C
- * untouched.  Calls from several host threads are serialised.
+ * Each call runs ozg_dgemm / ozg_zgemm on the current device on the caller's HOST arrays and
+ * returns when C is final (synchronous, like BLAS).  Rows m..ldc-1 of C are never written.
+ * Argument errors print the BLAS xerbla message on stderr and return with C untouched.  Calls
+ * from several host threads are serialised.
+ *
+ * Data strategy (read once, at the first call; the three strategies of the paper's Sec. 2.1):
+ * OZG_DATA_STRATEGY =
+ *   "copy"      (default) op(A), op(B) (and C when beta != 0) are copied through pinned staging
+ *               buffers to GPU memory, and C back.
+ *   "coherent"  the kernels read op(A), op(B), C and write C in place, in host memory, through
+ *               the coherent CPU-GPU link.  No staging copy is made.
+ *   "migrate"   as "coherent", but the first call that uses an array moves its pages to GPU
+ *               memory (cudaMemPrefetchAsync on the page-aligned span), where later calls find
+ *               it.  The CPU keeps coherent access to moved pages.  At most OZG_MIGRATE_LIMIT_MB
+ *               (default: half the GPU's memory) is moved; later arrays are accessed in place.
+ * "coherent" and "migrate" need a GPU that can access pageable host memory
+ * (cudaDevAttrPageableMemoryAccess), and "migrate" also cudaDevAttrConcurrentManagedAccess.
+ * Without them the shim prints a message and falls back to "copy" (or from "migrate" to
+ * "coherent").  Results are the same bits in every strategy.  If an in-place call fails on the
+ * GPU, it is redone by the next BLAS in the link chain when beta == 0.  With beta != 0 an
+ * in-place failure is only reported on stderr, because C may already have been modified.
  *
  * Mode (read once, at the first call): OZG_COMPUTE_MODE, mirroring the paper's
  * OZIMMU_COMPUTE_MODE (Sec. 3.1):
@@ -50,6 +66,21 @@ int ozg_blas_get_mode(void);
 
 /* Override the mode for later calls (slices 1..18 or -1); returns 0, or -1 if invalid. */
 int ozg_blas_set_mode(int slices);
+
+/* Parse a data-strategy string as OZG_DATA_STRATEGY is parsed: 0 = "copy", 1 = "coherent",
+ * 2 = "migrate", or -1 if the string is not a valid strategy. */
+int ozg_blas_parse_strategy(const char* strategy);
+
+/* The data strategy in effect (same encoding).  Before the first GPU use this is the requested
+ * strategy; from then on it is the one the device supports. */
+int ozg_blas_get_strategy(void);
+
+/* Request a data strategy (0, 1 or 2) for later calls; returns 0, or -1 if invalid.  The device
+ * check above applies. */
+int ozg_blas_set_strategy(int strategy);
+
+/* Bytes of host arrays moved to GPU memory by the "migrate" strategy since the process started. */
+long long ozg_blas_migrated_bytes(void);
 
 /* Number of calls offloaded to the GPU / passed to the next BLAS since the process started. */
 long long ozg_blas_offloaded_calls(void);

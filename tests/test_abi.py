@@ -84,3 +84,8 @@ def test_blas_shim_exports_and_mode_parsing():
              b"fp64_int8_0": 0, b"fp64_int8_": 0, b"fp64_int8_x": 0, b"int8_7": 0, b"": 0, b"DGEMM": 0}
     for s, v in cases.items():
         assert shim.ozg_blas_parse_mode(s) == v, s
+    shim.ozg_blas_parse_strategy.argtypes = [ctypes.c_char_p]
+    for s, v in {b"copy": 0, b"coherent": 1, b"migrate": 2, b"": -1, b"COPY": -1, b"uma": -1}.items():
+        assert shim.ozg_blas_parse_strategy(s) == v, s
+    shim.ozg_blas_set_strategy.argtypes = [ctypes.c_int]
+    assert shim.ozg_blas_set_strategy(3) == -1 and shim.ozg_blas_set_strategy(-1) == -1

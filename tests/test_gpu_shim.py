@@ -25,6 +25,8 @@ def shim():
     lib = ctypes.CDLL(build.SHIM_LIB)
     lib.ozg_blas_set_mode.argtypes = [ctypes.c_int]
     lib.ozg_blas_offloaded_calls.restype = ctypes.c_longlong
+    lib.ozg_blas_set_strategy.argtypes = [ctypes.c_int]
+    lib.ozg_blas_migrated_bytes.restype = ctypes.c_longlong
     return lib
 
 
@@ -118,3 +120,78 @@ def test_shim_interposes_with_ld_preload(shim, tmp_path):
     env["OZG_OFFLOAD_MIN_MNK"] = str(10 ** 9)  # below the threshold -> the next (CPU) BLAS
     out = subprocess.run([str(tmp_path / "prog")], capture_output=True, text=True, env=env, check=True)
     assert out.stdout.split()[0] == "42"
+
+
+STRATEGIES = {0: "copy", 1: "coherent", 2: "migrate"}
+
+
+def in_place_supported(shim, strategy):
+    assert shim.ozg_blas_set_strategy(strategy) == 0
+    # the device check runs at the first GPU use: make one tiny call, then read the strategy
+    C = np.zeros((1, 1), order="F")
+    one = np.ones((1, 1), order="F")
+    call(shim, "dgemm_", "N", "N", 1, 1, 1, 1.0, one, 1, one, 1, 0.0, C, 1)
+    return shim.ozg_blas_get_strategy() == strategy
+
+
+def test_shim_data_strategies_same_bits(shim):
+    """The three data strategies (pinned copies, coherent in-place access, migration on first
+    use) give the same bits: a real call with beta != 0 and padding rows (left untouched), equal
+    to the oracle's definition, and a complex conjugate-transpose call."""
+    assert shim.ozg_blas_set_mode(7) == 0
+    m, n, k = 130, 70, 300
+    A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=211)
+    ldc = m + 3
+    C0 = np.asfortranarray(workloads.rng(212).uniform(-1, 1, (ldc, n)))
+    mz, nz, kz = 45, 38, 77
+    g = workloads.rng(213)
+    Az = np.asfortranarray(workloads.wide_exponent((kz, mz), 0.5, g) + 1j * workloads.wide_exponent((kz, mz), 0.5, g))
+    Bz = np.asfortranarray(workloads.wide_exponent((kz, nz), 0.5, g) + 1j * workloads.wide_exponent((kz, nz), 0.5, g))
+    Z0 = np.asfortranarray(g.normal(size=(mz, nz)) + 1j * g.normal(size=(mz, nz)))
+    res = {}
+    try:
+        for st in STRATEGIES:
+            if st and not in_place_supported(shim, st):
+                pytest.skip(f"this GPU cannot access pageable host memory ({STRATEGIES[st]} falls back)")
+            assert shim.ozg_blas_set_strategy(st) == 0
+            C = C0.copy(order="F")
+            call(shim, "dgemm_", "N", "N", m, n, k, 0.75, A, m, B, k, -0.5, C, ldc)
+            Z = Z0.copy(order="F")
+            call(shim, "zgemm_", "C", "N", mz, nz, kz, 0.5 - 1j, Az, kz, Bz, kz, 0.25 + 0.5j, Z, mz)
+            assert shim.ozg_blas_get_strategy() == st
+            res[st] = (C, Z)
+    finally:
+        shim.ozg_blas_set_strategy(0)
+    E = oracle.dgemm_emu(A, B, 7, "N", "N", 0.75, -0.5, np.asfortranarray(C0[:m]))
+    assert np.array_equal(res[0][0][:m], E)
+    assert np.array_equal(res[0][0][m:], C0[m:])
+    for st in (1, 2):
+        assert np.array_equal(res[st][0], res[0][0]), STRATEGIES[st]
+        assert np.array_equal(res[st][1], res[0][1]), STRATEGIES[st]
+
+
+def test_shim_migrate_first_use_and_coherence(shim):
+    """Migration on first use moves the arrays' pages once: a second call on the same arrays
+    moves nothing. After the CPU rewrites A in place (coherent access to pages now in GPU
+    memory), the next call sees the new values, and moves nothing either."""
+    assert shim.ozg_blas_set_mode(7) == 0
+    try:
+        if not in_place_supported(shim, 2):
+            pytest.skip("this GPU cannot migrate pageable host memory (migrate falls back)")
+        m, n, k = 256, 192, 320
+        A, B = workloads.wide_exponent_pair(m, n, k, 2.0, seed=221)
+        C = np.zeros((m, n), order="F")
+        b0 = shim.ozg_blas_migrated_bytes()
+        call(shim, "dgemm_", "N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m)
+        b1 = shim.ozg_blas_migrated_bytes()
+        assert b1 - b0 >= A.nbytes + B.nbytes + C.nbytes - 3 * 2 * 65536  # page-rounded spans
+        assert np.array_equal(C, oracle.dgemm_emu(A, B, 7, "N", "N"))
+        call(shim, "dgemm_", "N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m)
+        assert shim.ozg_blas_migrated_bytes() == b1
+        A *= 2.0  # the CPU writes the moved pages in place
+        A[3, 5] = -7.25
+        call(shim, "dgemm_", "N", "N", m, n, k, 1.0, A, m, B, k, 0.0, C, m)
+        assert shim.ozg_blas_migrated_bytes() == b1
+        assert np.array_equal(C, oracle.dgemm_emu(A, B, 7, "N", "N"))
+    finally:
+        shim.ozg_blas_set_strategy(0)
