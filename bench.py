@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-zgemm", action="store_true", help="skip the KKR-like ZGEMM section")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end number")
     ap.add_argument("--no-shim", action="store_true", help="skip the BLAS shim data-strategy section")
+    ap.add_argument("--e2e-parts", type=int, default=E2E_PARTS, help="sub-batches of the pipelined end-to-end number")
     ap.add_argument("--shim-size", type=int, default=8192, help="n of the shim's n^3 DGEMM")
     return ap.parse_args()
 
@@ -495,14 +496,14 @@ def zgemm_section(ozg, torch, steps):
 E2E_PARTS = 4
 
 
-def e2e_pipelined(ozg, torch, batch, make_ctx, steps, pg, world, flops):
+def e2e_pipelined(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=E2E_PARTS):
     """End to end with host buffers: pinned host copies of A, B and C; per step, for every part,
     H2D of its A and B on one copy stream, the learned grouped call on the part's own stream,
     D2H of its C on another copy stream, ordered by events (a part's buffers are reused only after
     the previous step is done with them)."""
     n = len(batch.calls)
     w = np.cumsum([2.0 * c.m * c.n * c.k for c in batch.calls])
-    cuts = [0] + [int(np.searchsorted(w, w[-1] * (i + 1) / E2E_PARTS)) + 1 for i in range(E2E_PARTS - 1)] + [n]
+    cuts = [0] + [int(np.searchsorted(w, w[-1] * (i + 1) / nparts)) + 1 for i in range(nparts - 1)] + [n]
     cuts = sorted(set(min(max(x, 0), n) for x in cuts))
     calls = batch.gemm_calls()
 
@@ -664,7 +665,7 @@ def run_gpu(args):
     # and graph each) so that copies of one part overlap the emulation of another.
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_pipelined(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops)
+        e2e = e2e_pipelined(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops, args.e2e_parts)
     ctx.close()
     if pg is not None:
         pg.barrier()
