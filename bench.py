@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-shim", action="store_true", help="skip the BLAS shim data-strategy section")
     ap.add_argument("--e2e-parts", type=int, default=E2E_PARTS, help="sub-batches of the pipelined end-to-end number")
     ap.add_argument("--shim-size", type=int, default=8192, help="n of the shim's n^3 DGEMM")
+    ap.add_argument("--no-regions", action="store_true", help="skip the region-adaptive slice-count section")
     return ap.parse_args()
 
 
@@ -396,6 +397,57 @@ def shim_section(torch, n, reps=3):
     return out
 
 
+def regions_section(ozg, torch, n, steps, cases=((0.5, 4.0), (0.1, 6.0)), bands=(4, 8)):
+    """Region-adaptive slice counts (the paper's Sec. 4 proposal): n^3 DGEMMs whose first quarter
+    of the rows of A has exponent spread phi_wide and the rest phi (B: phi), per (phi, phi_wide)
+    case.  One learned call on the whole matrix (one count for all of C) against row bands whose
+    counts the selector picks per region (ozg_dgemm_regions); target 1e-12, the 64-sample check
+    judging every call or region (a rejected one is re-run at the fallback count), graph-replayed,
+    CUDA events."""
+    st = torch.cuda.Stream()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(91)
+
+    def draw(rows, cols, p):
+        u = torch.rand((rows, cols), generator=gen, device="cuda", dtype=torch.float64)
+        z = torch.randn((rows, cols), generator=gen, device="cuda", dtype=torch.float64)
+        return (u - 0.5) * torch.exp(p * z)
+    flops = 2.0 * n ** 3
+    out = {"workload": f"DGEMM {n}^3, rows 0..{n // 4 - 1} of A with a=(u-0.5)exp(phi_wide g), the other rows and "
+                       f"B with exp(phi g); target {TARGET_ERR:g}, {CHECK_SAMPLES}-sample check per call or region",
+           "cases": []}
+    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    for phi, phi_wide in cases:
+        # column-major n x n: row i of A is column i of the row-major tensor
+        dA = draw(n, n, phi)
+        dA[:, : n // 4] = draw(n, n // 4, phi_wide)
+        dB = draw(n, n, phi)
+        ctx = ozg.Context(stream=st)
+        ctx.load_selector(SELECTOR_MODEL)
+        ctx.set_target_error(TARGET_ERR)
+        ctx.set_check_samples(CHECK_SAMPLES)
+        case = {"phi": phi, "phi_wide": phi_wide}
+        with torch.cuda.stream(st):
+            rep = ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, 0, report=True)
+        ms = timed(torch, st, lambda: ctx.dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, 0), steps)
+        case["whole_matrix"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "selected": rep.selected,
+                                "slices_used": rep.slices_used, "repaired": rep.repaired,
+                                "err_sampled_dd": rep.est_err}
+        for b in bands:
+            with torch.cuda.stream(st):
+                reps = ctx.dgemm_regions("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, b, 1, report=True)
+            ms = timed(torch, st,
+                       lambda: ctx.dgemm_regions("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, b, 1), steps)
+            case[f"row_bands_{b}"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+                                      "selected": [r.selected for r in reps],
+                                      "slices_used": [r.slices_used for r in reps],
+                                      "max_err_sampled_dd": max(r.est_err for r in reps)}
+        ctx.close()
+        out["cases"].append(case)
+        del dA, dB
+    return out
+
+
 def single_section(ozg, torch, size, steps, phis=SINGLE_PHIS, slice_list=tuple(range(3, 11))):
     """Config 2: emulated DGEMM size^3, a = (u - 0.5) exp(phi g), phi in {0.5, 2, 4}, s = 3..10:
     TFLOP/s and sampled double-double error per s, the native FP64 kernel, and the roofline of the
@@ -690,6 +742,7 @@ def run_gpu(args):
                                                         parse_list(args.single_phis, float),
                                                         parse_list(args.single_slices, int))
     zgemm = None if args.no_zgemm else zgemm_section(ozg, torch, max(1, min(args.steps, 3)))
+    regions = None if args.no_regions else regions_section(ozg, torch, args.single_size, max(1, min(args.steps, 3)))
     shim = None if (world > 1 or args.no_shim) else shim_section(torch, args.shim_size)
     cpu = None if (world > 1 or args.no_cpu_baseline) else cpu_baseline(args.count)
 
@@ -712,6 +765,7 @@ def run_gpu(args):
         "compare": compare,
         "single_dgemm": single,
         "zgemm_kkr": zgemm,
+        "regions": regions,
         "blas_shim_strategies": shim,
         "gpu_launches": launches,
         "clocks": clk,

@@ -194,12 +194,28 @@ typedef struct ozg_gemm_desc {
 } ozg_gemm_desc;
 
 /* descs: HOST array of count descriptors; slices: HOST array (NULL: all 0), per call 1..18, or
- * 0 for the context's fallback count (ozg_set_fallback_slices, default 7).  reps: NULL or a HOST
+ * 0: the learned selector's choice when a selector is loaded (ozg_load_selector), else the
+ * context's fallback count (ozg_set_fallback_slices, default 7).  reps: NULL or a HOST
  * array of count reports (status holds -i for an invalid argument i of that call); with reports
  * the call returns after the batch finished.  Returns OZG_ERR_INVALID if any descriptor is
  * invalid (nothing is queued), else 0 or a runtime error. */
 int ozg_dgemm_grouped(ozg_ctx* ctx, int64_t count, const ozg_gemm_desc* descs, const int* slices,
                       ozg_report* reps);
+
+/* Region-adaptive slice counts (the paper's proposed adjustment of the split number to the
+ * accuracy a region needs, Sec. 4): C = alpha op(A) op(B) + beta C computed as row_blocks x
+ * col_blocks regions of C.  The rows of C are cut into row_blocks bands and its columns into
+ * col_blocks bands, as equal as possible.  Each region is one call of a grouped launch over the
+ * full k with slice count 0, so with a selector loaded every region gets the count that its own
+ * rows of op(A) and columns of op(B) need.  Each region is then exactly the emulated product
+ * at that count (the digits of a row depend only on that row, so they are the same as in the
+ * whole-matrix call).  Arguments as ozg_dgemm (device pointers, BLAS numbering; row_blocks = 14,
+ * col_blocks = 15, each >= 1).  reps: NULL or a HOST array of row_blocks x col_blocks reports,
+ * band-row-major (region (i, j) at i * col_blocks + j).  Each of the operands' rows is split
+ * once per region that uses it. */
+int ozg_dgemm_regions(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                      int64_t ldc, int row_blocks, int col_blocks, ozg_report* reps);
 
 /* enable != 0 (default): capture grouped calls into CUDA graphs when the context stream is not
  * the legacy default stream.  Changing it drops the cached graph. */

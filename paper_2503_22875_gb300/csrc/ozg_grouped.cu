@@ -625,6 +625,53 @@ extern "C" int ozg_set_fallback_slices(ozg_ctx* c, int s) {
   return OZG_OK;
 }
 
+// Region-adaptive slice counts: one GEMM cut into row_blocks x col_blocks regions of C, each a
+// call of one grouped launch over the full k with slice count 0, so that (with a selector
+// loaded) every region gets the count its own rows of op(A) and columns of op(B) need.  The
+// regions' row and column bands differ by at most one in size; an empty band (more blocks than
+// rows or columns) is a quick return.
+extern "C" int ozg_dgemm_regions(ozg_ctx* c, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                                 int64_t ldc, int row_blocks, int col_blocks, ozg_report* reps) {
+  if (!c) return OZG_ERR_INVALID;
+  ozg_gemm_desc whole{};
+  whole.transa = transa;
+  whole.transb = transb;
+  whole.m = m;
+  whole.n = n;
+  whole.k = k;
+  whole.lda = lda;
+  whole.ldb = ldb;
+  whole.ldc = ldc;
+  char ta, tb;
+  int rc = check_desc(whole, ta, tb);
+  if (!rc && row_blocks < 1) rc = -14;
+  if (!rc && col_blocks < 1) rc = -15;
+  if (!rc && (int64_t)row_blocks * col_blocks > (1 << 20)) return OZG_ERR_UNSUPPORTED;
+  const int64_t count = rc ? 0 : (int64_t)row_blocks * col_blocks;
+  if (reps && !rc) std::memset(reps, 0, sizeof(ozg_report) * (size_t)count);
+  if (rc) return rc;
+  if (m == 0 || n == 0) return OZG_OK;
+  std::vector<ozg_gemm_desc> d((size_t)count);
+  for (int i = 0; i < row_blocks; ++i) {
+    const int64_t r0 = m * i / row_blocks, r1 = m * (i + 1) / row_blocks;
+    for (int j = 0; j < col_blocks; ++j) {
+      const int64_t c0 = n * j / col_blocks, c1 = n * (j + 1) / col_blocks;
+      ozg_gemm_desc& x = d[(size_t)i * col_blocks + j];
+      x = whole;
+      x.m = r1 - r0;
+      x.n = c1 - c0;
+      x.alpha = alpha;
+      x.beta = beta;
+      x.A = ta == 'N' ? A + r0 : A + r0 * lda;  // rows r0 .. r1-1 of op(A)
+      x.B = tb == 'N' ? B + c0 * ldb : B + c0;  // columns c0 .. c1-1 of op(B)
+      x.C = C + r0 + c0 * ldc;
+    }
+  }
+  std::vector<int> zero((size_t)count, 0);
+  return ozg_dgemm_grouped(c, count, d.data(), zero.data(), reps);
+}
+
 extern "C" int ozg_set_tile_variant(ozg_ctx* c, int variant) {
   if (!c || variant < -1 || variant >= OZG_NUM_TILE_VARIANTS) return OZG_ERR_INVALID;
   c->force_variant = variant;

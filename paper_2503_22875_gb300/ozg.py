@@ -78,6 +78,7 @@ def load():
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_dgemm_regions.argtypes = [vp, ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, i32, vp]
     L.ozg_load_selector.argtypes = [vp, ctypes.c_char_p]
     L.ozg_set_target_error.argtypes = [vp, dbl]
     L.ozg_selector_features.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, vp, vp, vp]
@@ -198,7 +199,8 @@ class Context:
 
     def dgemm_grouped(self, calls, slices=None, report=False):
         """calls: sequence of (transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc) with
-        device tensors or raw pointers; slices: per-call slice counts (0: fallback).  Returns the
+        device tensors or raw pointers; slices: per-call slice counts (0: the selector's choice when
+        one is loaded, else the fallback count).  Returns the
         list of Report when report=True."""
         n = len(calls)
         arr = (GemmDesc * n)()
@@ -211,6 +213,18 @@ class Context:
         rc = load().ozg_dgemm_grouped(self._h, n, arr, sl, reps)
         _check(rc, "ozg_dgemm_grouped")
         return list(reps) if report else None
+
+    def dgemm_regions(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, row_blocks, col_blocks,
+                      report=False):
+        """C = alpha op(A) op(B) + beta C as row_blocks x col_blocks regions, each with the slice
+        count the selector picks for it (one grouped launch).  Returns the band-row-major list of
+        Report when report=True."""
+        nreg = int(row_blocks) * int(col_blocks)
+        reps = (Report * max(nreg, 1))() if report else None
+        rc = load().ozg_dgemm_regions(self._h, _c(transa), _c(transb), m, n, k, float(alpha), _p(A), lda, _p(B), ldb,
+                                      float(beta), _p(C), ldc, int(row_blocks), int(col_blocks), reps)
+        _check(rc, "ozg_dgemm_regions")
+        return list(reps)[:nreg] if report else None
 
     def set_graphs(self, enable: bool):
         _check(load().ozg_set_graphs(self._h, int(bool(enable))), "ozg_set_graphs")

@@ -174,3 +174,61 @@ def test_training_labels_against_oracle(ozg):
             assert gpu <= full + 4 * (s + 2) * U
             assert gpu >= full / 100
     ctx.close()
+
+
+def test_regions_select_per_region_and_match_oracle(ozg):
+    """Region-adaptive slice counts: the first band of rows of A has a wide exponent spread and
+    the rest a narrow one. Each region's count is the selector's decision on that region's own
+    rows of op(A) and columns of op(B) (the oracle's features and MLP). The wide band gets a
+    larger count than the narrow ones. Each region meets the target and equals the oracle's
+    emulated product at the count it used. Empty bands (more blocks than columns) are quick
+    returns."""
+    import os
+    path = os.path.join(os.path.dirname(selector.__file__), "data", "selector_v1.ozgsel")
+    model = selector.read_model(path)
+    s_cap = max(model["s_lo"] + 10, model["fallback"])
+    m, n, k = 300, 200, 256
+    g = workloads.rng(490)
+    A = np.asfortranarray(workloads.wide_exponent((m, k), 0.3, g))
+    A[:100] = workloads.wide_exponent((100, k), 5.0, g)
+    B = np.asfortranarray(workloads.wide_exponent((k, n), 0.3, g))
+    ctx = ozg.Context()
+    ctx.load_selector(path)
+    ctx.set_target_error(1e-12)
+    ctx.set_check_samples(64)
+    dC = ozg.to_device(np.zeros((m, n), order="F"))
+    reps = ctx.dgemm_regions("N", "N", m, n, k, 1.0, ozg.to_device(A), m, ozg.to_device(B), k, 0.0, dC, m, 3, 2,
+                             report=True)
+    C = ozg.from_device(dC, m, n)
+    sel = {}
+    for i in range(3):
+        r0, r1 = m * i // 3, m * (i + 1) // 3
+        for j in range(2):
+            c0, c1 = n * j // 2, n * (j + 1) // 2
+            r = reps[i * 2 + j]
+            Ai, Bj = np.asfortranarray(A[r0:r1]), np.asfortranarray(B[:, c0:c1])
+            s_cpu, probs = oracle.mlp_select(model, oracle.features(Ai, Bj, 1e-12), s_cap)
+            near = np.any(np.abs(np.cumsum(probs) - model["thr"]) < 1e-5)
+            assert r.selected == s_cpu or near, (i, j, r.selected, s_cpu)
+            assert r.status == 0 and r.est_err <= 1e-12
+            E = oracle.dgemm_emu(Ai, Bj, r.slices_used)
+            if r.slices_used <= 10:  # two exact windows: bit-exact
+                assert np.array_equal(C[r0:r1, c0:c1], E), (i, j)
+            else:
+                emu_check(ozg, C[r0:r1, c0:c1], Ai, Bj, r.slices_used)
+            sel[i, j] = r.selected
+    assert min(sel[0, 0], sel[0, 1]) > max(sel[2, 0], sel[2, 1])
+    # 3 columns cut into 5 bands: [0, 0), [0, 1), [1, 1), [1, 2), [2, 3)
+    dC2 = ozg.to_device(np.zeros((m, 3), order="F"))
+    reps = ctx.dgemm_regions("N", "N", m, 3, k, 1.0, ozg.to_device(A), m, ozg.to_device(B), k, 0.0, dC2, m, 1, 5,
+                             report=True)
+    C2 = ozg.from_device(dC2, m, 3)
+    assert all(r.status == 0 for r in reps) and reps[0].samples == 0 and reps[2].samples == 0
+    for j, col in ((1, 0), (3, 1), (4, 2)):
+        Bc = np.asfortranarray(B[:, col:col + 1])
+        E = oracle.dgemm_emu(A, Bc, reps[j].slices_used)
+        if reps[j].slices_used <= 10:
+            assert np.array_equal(C2[:, col:col + 1], E), col
+        else:
+            emu_check(ozg, C2[:, col:col + 1], A, Bc, reps[j].slices_used)
+    ctx.close()
