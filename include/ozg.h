@@ -271,6 +271,17 @@ int ozg_debug_group_products(ozg_ctx* ctx, char transa, char transb, int64_t m, 
                              const double* A, int64_t lda, const double* B, int64_t ldb, int slices,
                              int64_t* G_out);
 
+/* ---- fault-path hooks (tests; no GPU fault is involved) ----
+ * ozg_debug_wait: queues one CTA that waits on an mbarrier nothing arrives at, bounded at
+ * `cycles` clock cycles (1000 .. 4e9); when the wait runs out, the kernel raises the
+ * context's timeout status and returns.  ozg_sync then reports OZG_ERR_TIMEOUT once, and the
+ * context stays usable.
+ * ozg_debug_fail_allocs: the next n workspace allocations of this context fail on the host side,
+ * as if cudaMalloc had failed.  The call that needs one returns OZG_ERR_ALLOC with C untouched,
+ * and later calls allocate again.  Both return 0 or OZG_ERR_INVALID. */
+int ozg_debug_wait(ozg_ctx* ctx, long long cycles);
+int ozg_debug_fail_allocs(ozg_ctx* ctx, int n);
+
 /* ---- emulated DGEMM without any device allocation ----
  * No counterpart in the paper.  For callers that must not call cudaMalloc: code running while
  * its stream is captured into a CUDA graph (allocation cannot be captured), an interposed

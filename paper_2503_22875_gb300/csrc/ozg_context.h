@@ -61,6 +61,7 @@ struct ozg_ctx {
   double target = 1e-12;             // requested error for automatic slice counts
   float* train = nullptr;            // [theta | grad | m1 | m2 | loss] for on-GPU training
   int adam_step = 0;
+  int fail_allocs = 0;  // test hook: the next n workspace allocations fail on the host side
 };
 
 namespace ozg {

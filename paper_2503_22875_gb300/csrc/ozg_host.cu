@@ -46,6 +46,10 @@ static int grow_buffer(ozg_ctx* c, void** buf, size_t* cap, size_t bytes) {
     *cap = 0;
   }
   size_t want = align_up(bytes + bytes / 8, 1 << 20);
+  if (c->fail_allocs > 0) {  // injected failure (test hook), as if cudaMalloc had failed
+    --c->fail_allocs;
+    return OZG_ERR_ALLOC;
+  }
   cudaError_t e = cudaMalloc(buf, want);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -78,6 +78,8 @@ def load():
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_debug_wait.argtypes = [vp, ctypes.c_longlong]
+    L.ozg_debug_fail_allocs.argtypes = [vp, i32]
     L.ozg_dgemm_regions.argtypes = [vp, ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, i32, vp]
     L.ozg_load_selector.argtypes = [vp, ctypes.c_char_p]
     L.ozg_set_target_error.argtypes = [vp, dbl]
