@@ -64,6 +64,7 @@ def _load():
                                           c_dbl, vp, c_i64, c_int, c_int]
             lib.orc_zgemm_emu.argtypes = [c_char, c_char, c_i64, c_i64, c_i64, vp, vp, c_i64, vp, c_i64,
                                           vp, vp, c_i64, c_int]
+            lib.orc_zgemm3m_combine.argtypes = [c_i64, c_i64, vp, vp, vp, vp, vp, vp, c_i64]
             lib.orc_emu_bound.argtypes = [c_char, c_char, c_i64, c_i64, c_i64, vp, c_i64, vp, c_i64, c_int, vp]
             lib.orc_mlp_loss_grad.argtypes = [vp, vp, vp, c_int, vp]
             lib.orc_mlp_loss_grad.restype = c_dbl
@@ -219,6 +220,62 @@ def zgemm_emu(A, B, s: int, transa="N", transb="N", alpha=1.0, beta=0.0, C=None)
     _load().orc_zgemm_emu(_b(transa), _b(transb), m, n, k, _ptr(al), _ptr(A), max(A.shape[0], 1),
                           _ptr(B), max(B.shape[0], 1), _ptr(be), _ptr(C), max(m, 1), int(s))
     return C
+
+
+def _op(X, t: str):
+    """op(X) as a column-major array: X, X^T or X^H."""
+    X = np.asarray(X)
+    return np.asfortranarray(X if t in "Nn" else (X.T if t in "Tt" else X.conj().T))
+
+
+def zgemm3m_operands(A, B, transa="N", transb="N"):
+    """The real operands of the 3M product: (Ar, Ai, Sa) of op(A) and (Br, Bi, Sb) of op(B), with
+    Sa = RN(Ar + Ai) and Sb = RN(Br + Bi) (one FP64 addition each), all column-major."""
+    oA, oB = _op(np.asarray(A, dtype=np.complex128), transa), _op(np.asarray(B, dtype=np.complex128), transb)
+    Ar, Ai = np.asfortranarray(oA.real), np.asfortranarray(oA.imag)
+    Br, Bi = np.asfortranarray(oB.real), np.asfortranarray(oB.imag)
+    return (Ar, Ai, np.asfortranarray(Ar + Ai)), (Br, Bi, np.asfortranarray(Br + Bi))
+
+
+def zgemm3m_emu(A, B, s: int, transa="N", transb="N", alpha=1.0, beta=0.0, C=None):
+    """O-emu 3M: complex C = alpha op(A) op(B) + beta C from THREE real emulated products (the
+    Karatsuba form, 3 real products instead of 4): P1 = emu(Ar, Br), P2 = emu(Ai, Bi),
+    P3 = emu(Sa, Sb); Re = RN(P1 - P2), Im = RN(RN(P3 - P1) - P2); alpha, beta as zgemm_emu."""
+    (Ar, Ai, Sa), (Br, Bi, Sb) = zgemm3m_operands(A, B, transa, transb)
+    m, n = Ar.shape[0], Br.shape[1]
+    P1, P2, P3 = dgemm_emu(Ar, Br, s), dgemm_emu(Ai, Bi, s), dgemm_emu(Sa, Sb, s)
+    C = np.zeros((m, n), order="F", dtype=np.complex128) if C is None else np.array(C, dtype=np.complex128, order="F", copy=True)
+    if m == 0 or n == 0:
+        return C
+    al = np.array([complex(alpha).real, complex(alpha).imag])
+    be = np.array([complex(beta).real, complex(beta).imag])
+    _load().orc_zgemm3m_combine(m, n, _ptr(P1), _ptr(P2), _ptr(P3), _ptr(al), _ptr(be), _ptr(C), max(m, 1))
+    return C
+
+
+def zgemm3m_bound(A, B, s: int, transa="N", transb="N"):
+    """O-bound 3M: a priori |Re(T) - Re(op(A)op(B))| and |Im(T) - Im(op(A)op(B))| per entry of the
+    3M result T (alpha = 1, beta = 0).  With e(X, Y) = emu_bound(X, Y) (the exact-arithmetic
+    emulation error), |P - XY| <= e(X, Y) + u |P| for each rounded product, and
+    |Sa Sb - (Ar + Ai)(Br + Bi)| <= (2u + u^2) (|Ar| + |Ai|)(|Br| + |Bi|).  The real part adds
+    one rounding of P1 - P2, the imaginary part two:
+      re: e1 + e2 + u(|P1| + |P2|) + u |t_r|
+      im: e3 + e1 + e2 + u(|P3| + |P1| + |P2|) + (2u + u^2)(|Ar| + |Ai|)(|Br| + |Bi|)
+          + u |P3 - P1| + u |t_i|
+    with |P| <= ((|X||Y|)(1 + 2(k + 1)u) + e)(1 + u): the FP64 evaluation of |X||Y| is within
+    gamma_k of the exact one, so no result is needed to evaluate the bound."""
+    (Ar, Ai, Sa), (Br, Bi, Sb) = zgemm3m_operands(A, B, transa, transb)
+    u = 2.0 ** -53
+    k = Ar.shape[1]
+    g = 1 + 2 * (k + 2) * u
+    e1, e2, e3 = emu_bound(Ar, Br, s), emu_bound(Ai, Bi, s), emu_bound(Sa, Sb, s)
+    a1, a2, a3 = abs_product(Ar, Br), abs_product(Ai, Bi), abs_product(Sa, Sb)
+    q = abs_product(np.abs(Ar) + np.abs(Ai), np.abs(Br) + np.abs(Bi)) * g
+    P1, P2, P3 = ((a * g + e) * (1 + u) for a, e in ((a1, e1), (a2, e2), (a3, e3)))
+    re = e1 + e2 + u * (P1 + P2) + u * (P1 + P2) * (1 + u)
+    d = (P3 + P1) * (1 + u)
+    im = e3 + e1 + e2 + u * (P3 + P1 + P2) + (2 * u + u * u) * q + u * d + u * (d + P2) * (1 + u)
+    return re * (1 + 16 * u), im * (1 + 16 * u)
 
 
 def emu_bound(A, B, s: int, transa="N", transb="N"):

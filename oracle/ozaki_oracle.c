@@ -452,6 +452,32 @@ ORC_EXPORT void orc_zgemm_emu(char ta, char tb, int64_t m, int64_t n, int64_t k,
   free(e); free(f); free(DA); free(DB); free(G); free(Gc);
 }
 
+/* 3M (Karatsuba) combine of three real emulated products into complex C (column-major m x n,
+ * interleaved, ld ldc), given P1 = emu(Ar, Br), P2 = emu(Ai, Bi), P3 = emu(Sa, Sb) with
+ * Sa = RN(Ar + Ai), Sb = RN(Br + Bi) (each m x n, ld m):
+ *   t_r = RN(P1 - P2),  t_i = RN(RN(P3 - P1) - P2)
+ * then alpha and beta exactly as orc_zgemm_emu applies them. */
+ORC_EXPORT void orc_zgemm3m_combine(int64_t m, int64_t n, const double* P1, const double* P2, const double* P3,
+                                    const double* alpha, const double* beta, double* C, int64_t ldc) {
+  int do_beta = (beta[0] != 0.0 || beta[1] != 0.0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) {
+      double p1 = P1[i + j * m], p2 = P2[i + j * m], p3 = P3[i + j * m];
+      double tr = p1 - p2;
+      double d = p3 - p1;
+      double ti = d - p2;
+      double* c = &C[2 * (i + j * ldc)];
+      double re = fma(alpha[0], tr, -(alpha[1] * ti));
+      double im = fma(alpha[0], ti, alpha[1] * tr);
+      if (do_beta) {
+        double br = fma(beta[0], c[0], -(beta[1] * c[1]));
+        double bi = fma(beta[0], c[1], beta[1] * c[0]);
+        re += br; im += bi;
+      }
+      c[0] = re; c[1] = im;
+    }
+}
+
 /* ------------------------------------------------------------------------ O-bound */
 /* A priori bound on |(op(A)op(B))_ij - T_ij| for the triangle set (exact arithmetic before
  * the final rounding).  With truncated digits every partial digit sum has the sign of a' and

@@ -393,6 +393,51 @@ def test_zemu_error_bound_and_alpha_beta():
     np.testing.assert_allclose(C2, al * C + be * C0, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "T"), ("N", "C"), ("C", "T")])
+def test_z3m_small_integers_exact_with_alpha_beta(ta, tb):
+    """3M on small integers: every emulated product, difference and alpha/beta step is exact, so
+    the result is the exact complex product (Python integers) -- a wrong sign or operand in the
+    combine, a missing conjugation or a transposed operand changes it."""
+    rng = np.random.default_rng(31)
+    m, k, n = 4, 6, 5
+    opA = rng.integers(-64, 65, (m, k)) + 1j * rng.integers(-64, 65, (m, k))
+    opB = rng.integers(-64, 65, (k, n)) + 1j * rng.integers(-64, 65, (k, n))
+    A = opA if ta == "N" else (opA.T if ta == "T" else opA.conj().T)
+    B = opB if tb == "N" else (opB.T if tb == "T" else opB.conj().T)
+    C0 = rng.integers(-8, 9, (m, n)) + 1j * rng.integers(-8, 9, (m, n))
+    al, be = 2 - 1j, 0.5 + 0.25j
+    C = oracle.zgemm3m_emu(np.asfortranarray(A), np.asfortranarray(B), 4, ta, tb, al, be, C0)
+    for i in range(m):
+        for j in range(n):
+            re = sum(int(opA[i, l].real) * int(opB[l, j].real) - int(opA[i, l].imag) * int(opB[l, j].imag)
+                     for l in range(k))
+            im = sum(int(opA[i, l].real) * int(opB[l, j].imag) + int(opA[i, l].imag) * int(opB[l, j].real)
+                     for l in range(k))
+            er = Fraction(2) * re + im + Fraction(1, 2) * int(C0[i, j].real) - Fraction(1, 4) * int(C0[i, j].imag)
+            ei = Fraction(2) * im - re + Fraction(1, 2) * int(C0[i, j].imag) + Fraction(1, 4) * int(C0[i, j].real)
+            assert Fraction(C[i, j].real) == er and Fraction(C[i, j].imag) == ei, (i, j)
+
+
+@pytest.mark.parametrize("s", [3, 5, 7, 9])
+def test_z3m_error_within_its_bound(s):
+    """The 3M result stays within its a priori bound (emulation error of the three real products,
+    the rounding of Ar + Ai and Br + Bi, and the roundings of the combine), per part, against the
+    double-double product, on inputs with wide exponent spreads and cancellation in the
+    imaginary part."""
+    rng = np.random.default_rng(32 + s)
+    m, k, n = 9, 40, 7
+    A = (rng.uniform(-1, 1, (m, k)) + 1j * rng.uniform(-1, 1, (m, k))) * np.exp(rng.normal(0, 2, (m, k)))
+    B = (rng.uniform(-1, 1, (k, n)) + 1j * rng.uniform(-1, 1, (k, n))) * np.exp(rng.normal(0, 2, (k, n)))
+    A[:, :3] = A[:, :3].real - 1j * A[:, :3].real  # Re + Im = 0 on some entries: Sa has zeros
+    C = oracle.zgemm3m_emu(A, B, s)
+    rh, rl, ih, il = oracle.zgemm_dd(A, B)
+    bre, bim = oracle.zgemm3m_bound(A, B, s)
+    assert (np.abs(C.real - rh - rl) <= bre).all()
+    assert (np.abs(C.imag - ih - il) <= bim).all()
+    # the bound is not vacuous: at these s it sits far below the products' magnitude
+    assert (bim < 1e-1 * oracle.abs_product(np.abs(A.real) + np.abs(A.imag), np.abs(B.real) + np.abs(B.imag))).all()
+
+
 def test_kkr_kappa_variant_has_the_requested_condition_number():
     """The KKR-like stand-in's conditioned variant: the cached diagonal shift puts cond_2(A)
     within a factor 1.5 of 1e8 (SVD on the host), and B is the unshifted-workload's B."""
