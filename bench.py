@@ -541,6 +541,18 @@ def zgemm_section(ozg, torch, steps):
     okk = [s for s, v in kap.items() if v["err_sampled_dd"] <= TARGET_ERR]
     out["kappa1e8"] = {"shift": str(workloads.kkr_kappa_shift(113, 32, 3, 1e8)), "by_slices": kap,
                        "smallest_s_meeting_target": min(okk) if okk else None}
+    # 3M: three real emulated products (3/4 of the slice-product work, the 3M error bound)
+    z3 = {}
+    for s in range(5, 11):
+        ctx.set_check_samples(0)
+        ms = timed(torch, st, lambda: ctx.zgemm3m("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s), steps)
+        ctx.set_check_samples(CHECK_SAMPLES)
+        with torch.cuda.stream(st):
+            rep = ctx.zgemm3m("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n, s, report=True)
+        z3[s] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, "err_sampled_dd": rep.est_err,
+                 "max_real": rep.max_real, "max_imag": rep.max_imag}
+    ok3 = [s for s, v in z3.items() if v["err_sampled_dd"] <= TARGET_ERR]
+    out["3m"] = {"by_slices": z3, "smallest_s_meeting_target": min(ok3) if ok3 else None}
     ctx.close()
     return out
 

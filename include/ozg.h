@@ -202,6 +202,21 @@ typedef struct ozg_gemm_desc {
 int ozg_dgemm_grouped(ozg_ctx* ctx, int64_t count, const ozg_gemm_desc* descs, const int* slices,
                       ozg_report* reps);
 
+/* 3M (Karatsuba) ZGEMM: the same contract as ozg_zgemm, computed from three real emulated
+ * products instead of four real sub-products.  With Ar, Ai the real and imaginary parts of op(A)
+ * (conjugated for 'C'), Sa = RN(Ar + Ai) and the same for op(B):
+ *   P1 = emu(Ar, Br), P2 = emu(Ai, Bi), P3 = emu(Sa, Sb)   (one grouped launch, s slices each)
+ *   Re = RN(P1 - P2), Im = RN(RN(P3 - P1) - P2), then alpha and beta as ozg_zgemm.
+ * It does 3/4 of the slice-product work, with the 3M form's weaker error bound: the error of Im
+ * scales with (|Ar| + |Ai|)(|Br| + |Bi|) instead of |Ar||Bi| + |Ai||Br|, and Sa, Sb add one
+ * rounding each.  slices: 1..18 or -1 (native FP64, as ozg_zgemm); the learned selector is not
+ * used here (0 is invalid, argument 14).  The report's est_err / max_real / max_imag come from
+ * the context's sampled check of the complex result.  Workspace: 3 (mk + kn + mn) doubles.
+ * Non-finite inputs reach the native kernel per real product. */
+int ozg_zgemm3m(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k, const double* alpha,
+                const double* A, int64_t lda, const double* B, int64_t ldb, const double* beta, double* C,
+                int64_t ldc, int slices, ozg_report* rep);
+
 /* Region-adaptive slice counts (the paper's proposed adjustment of the split number to the
  * accuracy a region needs, Sec. 4): C = alpha op(A) op(B) + beta C computed as row_blocks x
  * col_blocks regions of C.  The rows of C are cut into row_blocks bands and its columns into

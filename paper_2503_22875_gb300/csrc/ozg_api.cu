@@ -402,6 +402,7 @@ int ozg_destroy(ozg_ctx* c) {
   if (c->train) cudaFree(c->train);
   c->plan.reset();
   if (c->gws) cudaFree(c->gws);
+  if (c->z3ws) cudaFree(c->z3ws);
   delete c;
   return OZG_OK;
 }

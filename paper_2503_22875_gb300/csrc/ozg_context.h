@@ -62,6 +62,9 @@ struct ozg_ctx {
   float* train = nullptr;            // [theta | grad | m1 | m2 | loss] for on-GPU training
   int adam_step = 0;
   int fail_allocs = 0;  // test hook: the next n workspace allocations fail on the host side
+  // 3M complex products: the real operands and products
+  void* z3ws = nullptr;
+  size_t z3ws_cap = 0;
 };
 
 namespace ozg {
@@ -90,6 +93,7 @@ struct Carve {
 
 int ensure_ws(ozg_ctx* c, size_t bytes);
 int ensure_gws(ozg_ctx* c, size_t bytes);  // grouped workspace; bumps gws_epoch when it moves
+int ensure_z3ws(ozg_ctx* c, size_t bytes);  // 3M operands and products
 cudaEvent_t pool_get(ozg_ctx* c);
 
 // Records an event pair around one phase on the context stream when profiling is on.

@@ -61,6 +61,7 @@ static int grow_buffer(ozg_ctx* c, void** buf, size_t* cap, size_t bytes) {
 }
 
 int ensure_ws(ozg_ctx* c, size_t bytes) { return grow_buffer(c, &c->ws, &c->ws_cap, bytes); }
+int ensure_z3ws(ozg_ctx* c, size_t bytes) { return grow_buffer(c, &c->z3ws, &c->z3ws_cap, bytes); }
 
 int ensure_gws(ozg_ctx* c, size_t bytes) {
   if (bytes <= c->gws_cap) return OZG_OK;

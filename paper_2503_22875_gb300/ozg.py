@@ -78,6 +78,7 @@ def load():
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_zgemm3m.argtypes = [vp, ch, ch, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, i32, vp]
     L.ozg_debug_wait.argtypes = [vp, ctypes.c_longlong]
     L.ozg_debug_fail_allocs.argtypes = [vp, i32]
     L.ozg_dgemm_regions.argtypes = [vp, ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, i32, vp]
@@ -197,6 +198,16 @@ class Context:
         rc = load().ozg_zgemm(self._h, _c(transa), _c(transb), m, n, k, al, _p(A), lda, _p(B), ldb, be, _p(C), ldc,
                               int(slices), ctypes.byref(rep) if rep else None)
         _check(rc, "ozg_zgemm")
+        return rep
+
+    def zgemm3m(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, report=False):
+        """3M complex product from three real emulated products (ozg_zgemm3m)."""
+        rep = Report() if report else None
+        al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+        rc = load().ozg_zgemm3m(self._h, _c(transa), _c(transb), m, n, k, al, _p(A), lda, _p(B), ldb, be, _p(C), ldc,
+                                int(slices), ctypes.byref(rep) if rep else None)
+        _check(rc, "ozg_zgemm3m")
         return rep
 
     def dgemm_grouped(self, calls, slices=None, report=False):

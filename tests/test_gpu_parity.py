@@ -471,3 +471,56 @@ def test_check_reports_paper_part_errors_for_complex(ozg, ctx):
     assert 0 < rep.max_real <= full_re * (1 + 1e-9)
     assert 0 < rep.max_imag <= full_im * (1 + 1e-9)
     assert rep.max_real >= full_re / 1e4 and rep.max_imag >= full_im / 1e4
+
+
+# ----------------------------------------------------------------------------- 3M ZGEMM
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "T"), ("N", "C"), ("C", "T")])
+@pytest.mark.parametrize("m,n,k,s", [(70, 90, 300, 7), (5, 3, 2000, 10), (129, 257, 64, 4)])
+def test_zgemm3m_bit_exact_vs_oracle(ozg, ctx, ta, tb, m, n, k, s):
+    """3M ZGEMM (three real emulated products; Re = RN(P1 - P2), Im = RN(RN(P3 - P1) - P2))
+    equals the oracle's 3M definition bit for bit: each real product is the exactly rounded
+    emulation (s <= 10), the combine and alpha, beta are the same FP64 operations in the same
+    order."""
+    shA = (m, k) if ta == "N" else (k, m)
+    shB = (k, n) if tb == "N" else (n, k)
+    seed = 7 * m + 3 * n + k + ord(ta) + 2 * ord(tb)
+    A = wide(shA, 1.5, seed) + 1j * wide(shA, 1.5, seed + 1)
+    B = wide(shB, 1.5, seed + 2) + 1j * wide(shB, 1.5, seed + 3)
+    C0 = np.asfortranarray(workloads.rng(seed + 4).normal(size=(m, n)) + 1j * workloads.rng(seed + 5).normal(size=(m, n)))
+    al, be = 0.5 - 2j, 1.5 + 0.25j
+    C = dev(ozg, C0)
+    rep = ctx.zgemm3m(ta, tb, m, n, k, al, dev(ozg, A), A.shape[0], dev(ozg, B), B.shape[0], be, C, m, s, report=True)
+    ctx.sync()
+    assert rep.status == 0 and rep.slices_used == s
+    assert np.array_equal(host(ozg, C, m, n), oracle.zgemm3m_emu(A, B, s, ta, tb, al, be, C0))
+
+
+def test_zgemm3m_check_report_and_arguments(ozg, ctx):
+    """The sampled check judges the 3M result: its estimate lies within the 3M bound's scale;
+    slices = 0 is rejected (argument 14); native mode and alpha = 0 take the stacked path."""
+    m, n, k, s = 60, 50, 400, 7
+    A = wide((m, k), 1.0, 901) + 1j * wide((m, k), 1.0, 902)
+    B = wide((k, n), 1.0, 903) + 1j * wide((k, n), 1.0, 904)
+    ctx.set_check_samples(64)
+    try:
+        C = dev(ozg, np.zeros((m, n), dtype=np.complex128))
+        rep = ctx.zgemm3m("N", "N", m, n, k, 1.0, dev(ozg, A), m, dev(ozg, B), k, 0.0, C, m, s, report=True)
+    finally:
+        ctx.set_check_samples(0)
+    bre, bim = oracle.zgemm3m_bound(A, B, s)
+    scale = oracle.abs_product(np.abs(A.real) + np.abs(A.imag), np.abs(B.real) + np.abs(B.imag))
+    assert rep.samples == 64 and 0 <= rep.est_err <= max((bre / scale).max(), (bim / scale).max()) * 4
+    assert np.isfinite(rep.max_real) and np.isfinite(rep.max_imag)
+    dA, dB = dev(ozg, A), dev(ozg, B)
+    rc = ozg.load().ozg_zgemm3m(ctx._h, b"N", b"N", m, n, k, (ctypes_d2(1.0, 0.0)), dA.data_ptr(), m, dB.data_ptr(), k,
+                                (ctypes_d2(0.0, 0.0)), C.data_ptr(), m, 0, None)
+    assert rc == -14
+    Cn = dev(ozg, np.zeros((m, n), dtype=np.complex128))
+    ctx.zgemm3m("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, Cn, m, -1)
+    ctx.sync()
+    np.testing.assert_allclose(host(ozg, Cn, m, n), A @ B, rtol=0, atol=(k + 2) * 4 * U * scale.max())
+
+
+def ctypes_d2(re, im):
+    import ctypes
+    return (ctypes.c_double * 2)(re, im)
