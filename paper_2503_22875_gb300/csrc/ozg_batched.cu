@@ -166,7 +166,7 @@ __device__ __forceinline__ void digits_unit(const SplitArgs* jobs, int2 ur) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) ds[q] = digit_src(b[q], e);
     __half* out = J.D + row * J.Kp + l0 + lg;
-    for (int t = t_lo; t <= t_hi; ++t) *reinterpret_cast<uint4*>(out + (int64_t)(t - 1) * plane) = digits8(ds, t);
+    store_digit_planes<kMaxPlanes>(ds, t_lo, t_hi, out, plane);
   }
 }
 

@@ -5,8 +5,11 @@
 // Only integer bit operations are used (FP64 arithmetic is slow on this part and not
 // needed: the fixed-point value is the 53-bit significand shifted).  HBM-bound: one read of
 // op(X) for the maxima, one read plus s fp16 writes for the digits.
+#include "../../include/ozg.h"
 #include "ozg_internal.h"
 #include "ozg_split_dev.cuh"
+
+static_assert(ozg::kMaxPlanes == OZG_MAX_SLICES, "digit planes of the widest split");
 
 namespace ozg {
 namespace {
@@ -125,8 +128,7 @@ __global__ void digits_contig(const double* __restrict__ X, int64_t ld, int64_t 
 #pragma unroll
     for (int j = 0; j < 8; ++j) ds[j] = digit_src(bits[part][j], e);
     int64_t orow = CPLX ? 2 * row + part : row;
-    for (int t = t_lo; t <= t_hi; ++t)
-      *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0) = digits8(ds, t);
+    store_digit_planes<kMaxPlanes>(ds, t_lo, t_hi, D + orow * Kp + l0, plane_rows * Kp);
   }
 }
 
@@ -176,8 +178,7 @@ __global__ void __launch_bounds__(256) digits_strided(const double* __restrict__
 #pragma unroll
     for (int j = 0; j < 8; ++j) ds[j] = digit_src(tile[lg + j][W * r + part], e);
     int64_t orow = CPLX ? 2 * row + part : row;
-    for (int t = t_lo; t <= t_hi; ++t)
-      *reinterpret_cast<uint4*>(D + ((int64_t)(t - 1) * plane_rows + orow) * Kp + l0 + lg) = digits8(ds, t);
+    store_digit_planes<kMaxPlanes>(ds, t_lo, t_hi, D + orow * Kp + l0 + lg, plane_rows * Kp);
   }
 }
 

@@ -10,6 +10,7 @@ namespace ozg {
 
 constexpr uint64_t kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr uint64_t kInfBits = 0x7FF0000000000000ull;
+constexpr int kMaxPlanes = 18;  // digit planes of the widest split (the largest slice count)
 
 // e = frexp exponent of the row maximum (max = 0.1f... 2^e), 0 for an all-zero row
 __device__ __forceinline__ int exponent_from_maxbits(unsigned long long mb) {
@@ -68,6 +69,17 @@ __device__ __forceinline__ uint4 digits8(const DigitSrc (&d)[8], int t) {
   o.z = digits_to_half2(digit_mag(d[4], t), digit_mag(d[5], t), d[4].neg | (d[5].neg << 16));
   o.w = digits_to_half2(digit_mag(d[6], t), digit_mag(d[7], t), d[6].neg | (d[7].neg << 16));
   return o;
+}
+
+// Digit planes t_lo .. t_hi of eight consecutive elements, one 16-byte store per plane at
+// out + (t - 1) plane.  The loop runs over every possible t, unrolled, so that each digit is a
+// shift by a constant; planes outside [t_lo, t_hi] are skipped.
+template <int TMAX>
+__device__ __forceinline__ void store_digit_planes(const DigitSrc (&d)[8], int t_lo, int t_hi, __half* out,
+                                                   int64_t plane) {
+#pragma unroll
+  for (int t = 1; t <= TMAX; ++t)
+    if (t >= t_lo && t <= t_hi) *reinterpret_cast<uint4*>(out + (int64_t)(t - 1) * plane) = digits8(d, t);
 }
 
 }  // namespace ozg
