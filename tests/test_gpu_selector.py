@@ -232,3 +232,45 @@ def test_regions_select_per_region_and_match_oracle(ozg):
         else:
             emu_check(ozg, C2[:, col:col + 1], A, Bc, reps[j].slices_used)
     ctx.close()
+
+
+def test_learned_batched_beats_fixed_slice_baseline_and_meets_target(ozg):
+    """The trained selector on the benchmark's distribution: a 256-call batch of the same shapes
+    and spreads (seeded, on the GPU), learned + grouped with the 64-sample check, meets 1e-12 on
+    at least 99% of the calls (the check re-runs any rejected call), and beats the fixed-slice
+    baseline (s = 7, one ozg_dgemm call at a time) in FP64-equivalent throughput."""
+    import os
+    import time
+    path = os.path.join(os.path.dirname(selector.__file__), "data", "selector_v1.ozgsel")
+    b = workloads.grouped_batch_flat(256, seed=77)
+    calls = b.gemm_calls()
+    st = torch.cuda.Stream()
+    ctx = ozg.Context(stream=st)
+    ctx.load_selector(path)
+    ctx.set_target_error(1e-12)
+    ctx.set_check_samples(64)
+    with torch.cuda.stream(st):
+        reps = ctx.dgemm_grouped(calls, [0] * len(calls), report=True)
+    ok = sum(r.est_err <= 1e-12 for r in reps)
+    assert ok >= 0.99 * len(reps), ok
+
+    def timed(fn, reps=3):
+        with torch.cuda.stream(st):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    t_learned = timed(lambda: ctx.dgemm_grouped(calls, [0] * len(calls)))
+    base = ozg.Context(stream=st)
+
+    def one_at_a_time():
+        for c in calls:
+            base.dgemm(*c, 7)
+    t_fixed = timed(one_at_a_time, reps=1)
+    assert t_learned < t_fixed, (t_learned, t_fixed)
+    ctx.close()
+    base.close()
