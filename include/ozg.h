@@ -46,7 +46,7 @@ extern "C" {
 #define OZG_ERR_CUDA 1         /* a CUDA runtime call failed (see ozg_last_cuda_error) */
 #define OZG_ERR_ALLOC 2        /* device workspace allocation failed */
 #define OZG_ERR_TIMEOUT 3      /* a bounded device-side wait gave up; the kernel returned */
-#define OZG_ERR_UNSUPPORTED 4  /* the request is valid BLAS but outside what this build does */
+#define OZG_ERR_UNSUPPORTED 4  /* the request is valid BLAS but outside what this library implements */
 #define OZG_ERR_INVALID 5      /* null context or other non-BLAS argument error */
 
 #define OZG_MAX_SLICES 18      /* fp64_int8_18 is the largest mode of Sec. 3.1 */
@@ -178,7 +178,7 @@ int ozg_native_zgemm(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t 
  * inputs held Inf/NaN, and a batched sampled error check.  On a non-default context stream the
  * sequence is captured into a CUDA graph and replayed for as long as the same batch (same
  * descriptors and slice counts) is submitted again; the matrices' contents may change between
- * submissions.  Grouping many small GEMMs is the batching addition of the spec design; the
+ * submissions.  Grouping many small GEMMs is an addition of this library; the
  * paper has no grouped interface (its offload intercepts one BLAS call at a time, Sec. 3.1). */
 typedef struct ozg_gemm_desc {
   char transa, transb; /* 'N' or 'T' (case-insensitive; 'C' means 'T') */
