@@ -240,7 +240,9 @@ def zgemm3m_operands(A, B, transa="N", transb="N"):
 def zgemm3m_emu(A, B, s: int, transa="N", transb="N", alpha=1.0, beta=0.0, C=None):
     """O-emu 3M: complex C = alpha op(A) op(B) + beta C from THREE real emulated products (the
     Karatsuba form, 3 real products instead of 4): P1 = emu(Ar, Br), P2 = emu(Ai, Bi),
-    P3 = emu(Sa, Sb); Re = RN(P1 - P2), Im = RN(RN(P3 - P1) - P2); alpha, beta as zgemm_emu."""
+    P3 = emu(Sa, Sb); Re = RN(P1 - P2), Im = RN(RN(P3 - P1) - P2); alpha, beta as zgemm_emu.
+    The paper builds complex products from real sub-products (Sec. 2.2, Sec. 3.2) but does not
+    describe a 3M form; each real product here is dgemm_emu (Sec. 2.2's scheme)."""
     (Ar, Ai, Sa), (Br, Bi, Sb) = zgemm3m_operands(A, B, transa, transb)
     m, n = Ar.shape[0], Br.shape[1]
     P1, P2, P3 = dgemm_emu(Ar, Br, s), dgemm_emu(Ai, Bi, s), dgemm_emu(Sa, Sb, s)
