@@ -219,6 +219,10 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
     ck.err_out = c->dcheck;
     ck.part_err = cplx ? c->dcheck + 1 : nullptr;
     ck.gate = nonfinite;
+    if (!cplx) {  // the split's exponents bound every product: exact integer reference
+      ck.ea = sa.exps;
+      ck.fb = sb.exps;
+    }
     PhaseScope ps(c, OZG_PHASE_CHECK);
     OZG_CUDA(ozg::launch_check_pre(ck, st));
   }

@@ -111,12 +111,105 @@ __device__ __forceinline__ dd dot2_reduce_warp(dot2 a) {
   return fast_two_sum(a.s, a.c);
 }
 
+// Exact real dot product on the integer pipes.  With E = e_i + f_j from the split's row and
+// column exponents, every |a_il b_lj| < 2^E, so each term -- the 106-bit product of the two 53-bit
+// significands times a power of two -- is below 2^100 in units of 2^(E - 100).  The terms are
+// summed in a signed 128-bit fixed-point accumulator with that unit; bits below it are truncated
+// (each term toward zero), so the sum is exact to within k units, k 2^(E - 100), a relative 2^-100
+// of the largest term per term.  For k < 2^26 the sum stays below 2^126.  The double-double
+// result is formed from three exact 52-bit pieces.  FP64 is this part's slowest pipe; this path
+// issues no FP64 instruction per term beyond the |a||b| scale.
+struct i128 {
+  unsigned long long lo;
+  long long hi;
+};
+__device__ __forceinline__ void significand(uint64_t bits, uint64_t& m, int& x) {  // |v| = m 2^x
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  m = bits & 0xFFFFFFFFFFFFFull;
+  if (eb != 0) {
+    m |= 1ull << 52;
+    x = eb - 1075;
+  } else {
+    x = -1074;
+  }
+}
+__device__ __forceinline__ void add_exact_term(i128& acc, uint64_t abits, uint64_t bbits, int unit) {
+  if ((abits << 1) == 0 || (bbits << 1) == 0) return;  // a zero factor (either sign)
+  uint64_t ma, mb;
+  int xa, xb;
+  significand(abits, ma, xa);
+  significand(bbits, mb, xb);
+  const unsigned long long plo = ma * mb, phi = __umul64hi(ma, mb);
+  const int sh = xa + xb - unit;  // the term is (phi, plo) 2^sh units, below 2^100 units
+  unsigned long long qlo, qhi;
+  if (sh >= 0) {
+    if (sh >= 64) {  // then the product is below 2^36 and phi == 0
+      qhi = plo << (sh - 64);
+      qlo = 0;
+    } else if (sh == 0) {
+      qhi = phi;
+      qlo = plo;
+    } else {
+      qhi = (phi << sh) | (plo >> (64 - sh));
+      qlo = plo << sh;
+    }
+  } else {
+    const int r = -sh;
+    if (r >= 128) {
+      qhi = qlo = 0;
+    } else if (r >= 64) {
+      qhi = 0;
+      qlo = phi >> (r - 64);
+    } else {
+      qhi = phi >> r;
+      qlo = (plo >> r) | (phi << (64 - r));
+    }
+  }
+  if (((abits ^ bbits) >> 63) == 0) {
+    const unsigned long long nl = acc.lo + qlo;
+    acc.hi += (long long)qhi + (nl < acc.lo ? 1 : 0);
+    acc.lo = nl;
+  } else {
+    const unsigned long long nl = acc.lo - qlo;
+    acc.hi -= (long long)qhi + (acc.lo < qlo ? 1 : 0);
+    acc.lo = nl;
+  }
+}
+__device__ __forceinline__ dd exact_dot_reduce_warp(i128 a, int unit) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long olo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    const long long ohi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    const unsigned long long nl = a.lo + olo;
+    a.hi += ohi + (nl < a.lo ? 1 : 0);
+    a.lo = nl;
+  }
+  // S = s2 2^104 + s1 2^52 + s0 with s0, s1 in [0, 2^52) and |s2| < 2^22: three exact doubles
+  const unsigned long long m52 = (1ull << 52) - 1;
+  const double s0 = (double)(long long)(a.lo & m52);
+  const double s1 = ldexp((double)(long long)(((a.lo >> 52) | ((unsigned long long)a.hi << 12)) & m52), 52);
+  const double s2 = ldexp((double)(a.hi >> 40), 104);
+  dd r = two_sum(s2, s1);
+  r = dd_add(r, {s0, 0.0});
+  return {ldexp(r.hi, unit), ldexp(r.lo, unit)};
+}
+
 __device__ void check_one(const CheckArgs& P, int sample, int lane, double* err_slot) {
   int64_t i, j;
   sample_ij(P, sample, i, j);
   dd re = {0, 0}, im = {0, 0};
   double sabs = 0.0;
-  if (!P.cplx) {
+  if (!P.cplx && P.ea != nullptr && P.fb != nullptr && P.k < (1ll << 26)) {
+    const int unit = P.ea[i] + P.fb[j] - 100;
+    i128 acc = {0ull, 0ll};
+    for (int64_t l = lane; l < P.k; l += 32) {
+      const double ar = (P.ta == 'N') ? P.A[i + l * P.lda] : P.A[l + i * P.lda];
+      const double br = (P.tb == 'N') ? P.B[l + j * P.ldb] : P.B[j + l * P.ldb];
+      add_exact_term(acc, __double_as_longlong(ar), __double_as_longlong(br), unit);
+      sabs = fma(fabs(ar), fabs(br), sabs);
+    }
+    re = exact_dot_reduce_warp(acc, unit);
+  } else if (!P.cplx) {
     dot2 acc = {0.0, 0.0};
     for (int64_t l = lane; l < P.k; l += 32) {
       const double ar = (P.ta == 'N') ? P.A[i + l * P.lda] : P.A[l + i * P.lda];

@@ -349,6 +349,8 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     ck.cold = gat<double>(c, P->oCold) + 2 * (size_t)std::max(nsamp, 1) * i;
     ck.err_out = gat<double>(c, P->oErrs) + i;
     ck.gate = flags + i;
+    ck.ea = gat<int32_t>(c, oEA[i]);  // the split's exponents: exact integer reference
+    ck.fb = gat<int32_t>(c, oEB[i]);
   }
   c->check_seed += 1;
   std::vector<SelectJob> sel;

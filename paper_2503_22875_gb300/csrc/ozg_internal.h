@@ -147,6 +147,11 @@ struct CheckArgs {
   double* err_out = nullptr;  // max error (device double), reset by launch_check_post
   const int* gate = nullptr;  // skip when *gate != 0 (call routed to native FP64)
   double* part_err = nullptr;  // complex: [2] max relative error of the real / imaginary parts
+  // real calls: the split's exponents of the rows of op(A) and the columns of op(B)
+  // (|a_il| < 2^ea[i], |b_lj| < 2^fb[j]); when both are set the reference is summed exactly
+  // in integers instead of by Dot2
+  const int32_t* ea = nullptr;
+  const int32_t* fb = nullptr;
 };
 cudaError_t launch_check_pre(const CheckArgs& a, cudaStream_t st);
 cudaError_t launch_check_post(const CheckArgs& a, cudaStream_t st);
