@@ -635,7 +635,6 @@ extern "C" int ozg_set_fallback_slices(ozg_ctx* c, int s) {
 extern "C" int ozg_dgemm_regions(ozg_ctx* c, char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
                                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                                  int64_t ldc, int row_blocks, int col_blocks, ozg_report* reps) {
-  if (!c) return OZG_ERR_INVALID;
   ozg_gemm_desc whole{};
   whole.transa = transa;
   whole.transb = transb;
@@ -649,6 +648,7 @@ extern "C" int ozg_dgemm_regions(ozg_ctx* c, char transa, char transb, int64_t m
   int rc = check_desc(whole, ta, tb);
   if (!rc && row_blocks < 1) rc = -14;
   if (!rc && col_blocks < 1) rc = -15;
+  if (!rc && !c) return OZG_ERR_INVALID;  // BLAS argument errors are reported first
   if (!rc && (int64_t)row_blocks * col_blocks > (1 << 20)) return OZG_ERR_UNSUPPORTED;
   const int64_t count = rc ? 0 : (int64_t)row_blocks * col_blocks;
   if (reps && !rc) std::memset(reps, 0, sizeof(ozg_report) * (size_t)count);

@@ -69,7 +69,7 @@ int grid_for(const ozg_ctx* c, int64_t total) {
 extern "C" int ozg_zgemm3m(ozg_ctx* c, char transa, char transb, int64_t m, int64_t n, int64_t k,
                            const double* alpha, const double* A, int64_t lda, const double* B, int64_t ldb,
                            const double* beta, double* C, int64_t ldc, int slices, ozg_report* rep) {
-  if (!c || !alpha || !beta) return OZG_ERR_INVALID;
+  if (!alpha || !beta) return OZG_ERR_INVALID;
   const char ta = norm_trans(transa), tb = norm_trans(transb);
   const int64_t nrowa = ta == 'N' ? m : k, nrowb = tb == 'N' ? k : n;
   int info = 0;
@@ -88,6 +88,7 @@ extern "C" int ozg_zgemm3m(ozg_ctx* c, char transa, char transb, int64_t m, int6
     rep->est_err = rep->max_real = rep->max_imag = NAN;
   }
   if (info) return info;
+  if (!c) return OZG_ERR_INVALID;  // BLAS argument errors are reported first
   if (m == 0 || n == 0) return OZG_OK;
   // native mode, k == 0 and alpha == 0 need no products: the stacked path handles them
   if (slices == OZG_NATIVE || k == 0 || (alpha[0] == 0.0 && alpha[1] == 0.0))

@@ -89,3 +89,35 @@ def test_blas_shim_exports_and_mode_parsing():
         assert shim.ozg_blas_parse_strategy(s) == v, s
     shim.ozg_blas_set_strategy.argtypes = [ctypes.c_int]
     assert shim.ozg_blas_set_strategy(3) == -1 and shim.ozg_blas_set_strategy(-1) == -1
+
+
+@pytest.mark.parametrize("args,code", [
+    (("N", "N", 4, 4, 4, 4, 4, 4, 2, 2), 5),    # valid arguments, null context
+    (("X", "N", 4, 4, 4, 4, 4, 4, 2, 2), -1),
+    (("N", "N", 4, 4, 4, 3, 4, 4, 2, 2), -8),
+    (("N", "T", 4, 6, 4, 4, 4, 4, 2, 2), -10),
+    (("N", "N", 4, 4, 4, 4, 4, 3, 2, 2), -13),
+    (("N", "N", 4, 4, 4, 4, 4, 4, 0, 2), -14),  # row_blocks
+    (("N", "N", 4, 4, 4, 4, 4, 4, 2, 0), -15),  # col_blocks
+])
+def test_regions_argument_errors(lib, args, code):
+    ta, tb, m, n, k, lda, ldb, ldc, rb, cb = args
+    rc = lib.ozg_dgemm_regions(None, ta.encode(), tb.encode(), m, n, k, 1.0, None, lda, None, ldb, 0.0, None, ldc,
+                               rb, cb, None)
+    assert rc == code
+
+
+@pytest.mark.parametrize("args,code", [
+    (("C", "T", 4, 4, 4, 4, 4, 4, 7), 5),       # valid arguments, null context
+    (("Q", "N", 4, 4, 4, 4, 4, 4, 7), -1),
+    (("N", "N", 4, -1, 4, 4, 4, 4, 7), -4),
+    (("C", "N", 4, 4, 6, 5, 6, 4, 7), -8),      # op(A) = A^H: A is k x m, lda >= k
+    (("N", "N", 4, 4, 4, 4, 4, 2, 7), -13),
+    (("N", "N", 4, 4, 4, 4, 4, 4, 0), -14),     # the selector is not used for 3M
+    (("N", "N", 4, 4, 4, 4, 4, 4, -1), 5),      # native FP64 is valid
+])
+def test_zgemm3m_argument_errors(lib, args, code):
+    ta, tb, m, n, k, lda, ldb, ldc, s = args
+    al = (ctypes.c_double * 2)(1.0, 0.0)
+    rc = lib.ozg_zgemm3m(None, ta.encode(), tb.encode(), m, n, k, al, None, lda, None, ldb, al, None, ldc, s, None)
+    assert rc == code
