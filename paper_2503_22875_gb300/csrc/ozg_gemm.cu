@@ -444,6 +444,8 @@ __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushAr
   } else {
     prefetch_close<NCH>(a, j, o0, s0, fe);
   }
+  // C is written with evict-first (streaming) stores: it is not read again by this launch, and
+  // normal stores would displace digit-plane lines that the next groups read again from L2.
   // RN of the exact sum: for one or two windows all NCH outputs go through the branch-free
   // rounding together, and only results outside the normal range take the general path
   // (in batches of RB outputs, to bound the registers live at once)
@@ -485,7 +487,7 @@ __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushAr
         const int64_t col = c0 + i0 + i;
         if (a.row_ok && col < j.cols) {
           double* cp = j.C + a.orow + col * j.ldc;
-          *cp = a.unit_ab ? tv[i] : (j.beta_zero ? j.a0 * tv[i] : fma(j.a0, tv[i], j.b0 * *cp));
+          __stcs(cp, a.unit_ab ? tv[i] : (j.beta_zero ? j.a0 * tv[i] : fma(j.a0, tv[i], j.b0 * *cp)));
         }
       }
     } else {
@@ -498,7 +500,7 @@ __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushAr
         if (ok) {
           double* cp = j.C + 2 * (a.orow + jc * j.ldc);
           if (a.unit_ab) {
-            cp[a.odd ? 1 : 0] = part;
+            __stcs(cp + (a.odd ? 1 : 0), part);
           } else {
             const double tr = a.odd ? partner : part, ti = a.odd ? part : partner;
             double re = fma(j.a0, tr, -(j.a1 * ti));
@@ -508,7 +510,7 @@ __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushAr
               re += fma(j.b0, cr, -(j.b1 * ci));
               im += fma(j.b0, ci, j.b1 * cr);
             }
-            cp[a.odd ? 1 : 0] = a.odd ? im : re;
+            __stcs(cp + (a.odd ? 1 : 0), a.odd ? im : re);
           }
         }
       }
@@ -890,7 +892,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                 const double tv = horner_step(Rt + (size_t)c * BM * 16, Gs[c], true, first_push, g == 2, final_push, E);
                 if (final_push && ok) {
                   double* cp = j.C + orow + col * j.ldc;
-                  *cp = j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp);
+                  __stcs(cp, j.beta_zero ? j.a0 * tv : fma(j.a0, tv, j.b0 * *cp));
                 }
               }
             } else {
@@ -915,7 +917,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                       re += fma(j.b0, cr, -(j.b1 * ci));
                       im += fma(j.b0, ci, j.b1 * cr);
                     }
-                    cp[odd ? 1 : 0] = odd ? im : re;
+                    __stcs(cp + (odd ? 1 : 0), odd ? im : re);
                   }
                 }
               }
