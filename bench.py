@@ -646,7 +646,14 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
-    build.build()
+    # rank 0 compiles if anything is stale; the others wait and then find the library up to date
+    # (concurrent builds would write the same object files)
+    if pg is None or rank == 0:
+        build.build()
+    if pg is not None:
+        pg.barrier()
+        if rank != 0:
+            build.build()
     ozg.load()
     batch = workloads.grouped_batch_flat(args.count, seed=rank_batch_seed(rank))
     calls = batch.gemm_calls()
