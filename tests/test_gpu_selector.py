@@ -274,3 +274,44 @@ def test_learned_batched_beats_fixed_slice_baseline_and_meets_target(ozg):
     assert t_learned < t_fixed, (t_learned, t_fixed)
     ctx.close()
     base.close()
+
+
+def test_regions_transposed_operands_match_oracle(ozg):
+    """Regions over transposed operands (op(A) = A^T, op(B) = B^T, with padded leading
+    dimensions): each region equals the oracle's emulation of its own rows of op(A) and columns
+    of op(B) at the count it used, and C's padding rows stay untouched."""
+    import os
+    path = os.path.join(os.path.dirname(selector.__file__), "data", "selector_v1.ozgsel")
+    m, n, k = 150, 110, 90
+    g = workloads.rng(495)
+    opA = np.asfortranarray(workloads.wide_exponent((m, k), 1.5, g))
+    opB = np.asfortranarray(workloads.wide_exponent((k, n), 1.5, g))
+    lda, ldb, ldc = k + 3, n + 5, m + 2
+    A = np.zeros((lda, m), order="F")
+    A[:k] = opA.T
+    B = np.zeros((ldb, k), order="F")
+    B[:n] = opB.T
+    C0 = np.asfortranarray(workloads.rng(496).uniform(-1, 1, (ldc, n)))
+    ctx = ozg.Context()
+    ctx.load_selector(path)
+    ctx.set_target_error(1e-12)
+    ctx.set_check_samples(64)
+    dC = ozg.to_device(C0)
+    reps = ctx.dgemm_regions("T", "T", m, n, k, 0.5, ozg.to_device(A), lda, ozg.to_device(B), ldb, 0.25, dC, ldc,
+                             3, 2, report=True)
+    C = ozg.from_device(dC, ldc, n)
+    assert np.array_equal(C[m:], C0[m:])
+    for i in range(3):
+        r0, r1 = m * i // 3, m * (i + 1) // 3
+        for j in range(2):
+            c0, c1 = n * j // 2, n * (j + 1) // 2
+            r = reps[i * 2 + j]
+            assert r.status == 0 and r.est_err <= 1e-12
+            E = oracle.dgemm_emu(np.asfortranarray(opA[r0:r1]), np.asfortranarray(opB[:, c0:c1]), r.slices_used,
+                                 "N", "N", 0.5, 0.25, np.asfortranarray(C0[r0:r1, c0:c1]))
+            if r.slices_used <= 10:
+                assert np.array_equal(C[r0:r1, c0:c1], E), (i, j)
+            else:
+                emu_check(ozg, C[r0:r1, c0:c1], np.asfortranarray(opA[r0:r1]), np.asfortranarray(opB[:, c0:c1]),
+                          r.slices_used, 0.5, 0.25, np.asfortranarray(C0[r0:r1, c0:c1]))
+    ctx.close()
