@@ -524,3 +524,27 @@ def test_zgemm3m_check_report_and_arguments(ozg, ctx):
 def ctypes_d2(re, im):
     import ctypes
     return (ctypes.c_double * 2)(re, im)
+
+
+def test_zgemm3m_padded_leading_dimensions(ozg, ctx):
+    """3M with lda, ldb, ldc above the matrix heights (the deinterleave and combine kernels do
+    their own leading-dimension arithmetic): bit-equal to the oracle on the op'd matrices, C's
+    padding rows untouched."""
+    m, n, k, s = 37, 29, 53, 8
+    g = workloads.rng(930)
+    opA = wide((m, k), 1.0, 931) + 1j * wide((m, k), 1.0, 932)
+    opB = wide((k, n), 1.0, 933) + 1j * wide((k, n), 1.0, 934)
+    lda, ldb, ldc = k + 4, k + 1, m + 3
+    A = np.zeros((lda, m), dtype=np.complex128, order="F")
+    A[:k] = opA.T                                  # op = 'T'
+    B = np.zeros((ldb, n), dtype=np.complex128, order="F")
+    B[:k] = opB                                    # op = 'N'
+    C0 = np.asfortranarray(g.normal(size=(ldc, n)) + 1j * g.normal(size=(ldc, n)))
+    C = dev(ozg, C0)
+    ctx.zgemm3m("T", "N", m, n, k, 1.25 - 0.5j, dev(ozg, A), lda, dev(ozg, B), ldb, -0.5 + 1j, C, ldc, s)
+    ctx.sync()
+    out = host(ozg, C, ldc, n)
+    assert np.array_equal(out[m:], C0[m:])
+    E = oracle.zgemm3m_emu(np.asfortranarray(opA), np.asfortranarray(opB), s, "N", "N", 1.25 - 0.5j, -0.5 + 1j,
+                           np.asfortranarray(C0[:m]))
+    assert np.array_equal(out[:m], E)
