@@ -347,7 +347,7 @@ def parse_list(spec, cast):
 def shim_section(torch, n, reps=3):
     """The BLAS interposition library's three data strategies (Sec. 2.1) on an n^3 DGEMM called
     through dgemm_ on arrays in pageable host memory, at s = 7: wall-clock time of each
-    synchronous call.  copy: staging through pinned buffers; coherent: the kernels read and write
+    synchronous call.  copy: DMA from and to the caller's arrays; coherent: the kernels read and write
     the host arrays in place over the CPU-GPU link; migrate: the first call moves the arrays'
     pages to GPU memory, later calls find them there."""
     import ctypes

@@ -14,8 +14,9 @@
  *
  * Data strategy (read once, at the first call; the three strategies of the paper's Sec. 2.1):
  * OZG_DATA_STRATEGY =
- *   "copy"      (default) op(A), op(B) (and C when beta != 0) are copied through pinned staging
- *               buffers to GPU memory, and C back.
+ *   "copy"      (default) op(A), op(B) (and C when beta != 0) are copied to GPU memory by DMA
+ *               straight from the caller's arrays (cudaMemcpyAsync on pageable memory), and the
+ *               m x n block of C back the same way; no CPU staging copy is made.
  *   "coherent"  the kernels read op(A), op(B), C and write C in place, in host memory, through
  *               the coherent CPU-GPU link.  No staging copy is made.
  *   "migrate"   as "coherent", but the first call that uses an array moves its pages to GPU

@@ -2,7 +2,7 @@
 // emulation (the automatic-offload side of the paper, Sec. 3.1: one preloaded library that
 // intercepts the BLAS call and runs it on the GPU in the mode named by an environment
 // variable).  Data movement follows one of the three strategies of Sec. 2.1 (named by
-// OZG_DATA_STRATEGY): explicit copies (host memory -> pinned staging -> device, and back),
+// OZG_DATA_STRATEGY): explicit copies (DMA from the caller's host arrays to the device, and back),
 // cache-coherent access (the kernels read and write the caller's host arrays in place over the
 // CPU-GPU link), or migration on first use (the pages of an array move to GPU memory the first
 // time a call uses it and stay there; the CPU keeps coherent access).  See include/ozg_blas.h
@@ -34,8 +34,6 @@ ozg_ctx* g_ctx = nullptr;
 cudaStream_t g_stream = nullptr;
 int g_mode = 0;  // 0: not read yet
 long long g_min_mnk = 0;
-void* g_pinned = nullptr;
-size_t g_pinned_cap = 0;
 void* g_dev = nullptr;
 size_t g_dev_cap = 0;
 gemm_fn g_next_d = nullptr, g_next_z = nullptr;
@@ -210,19 +208,15 @@ bool ensure_gpu_locked() {
   return true;
 }
 
-bool grow(void** buf, size_t* cap, size_t need, bool pinned) {
+bool grow(void** buf, size_t* cap, size_t need) {  // device buffer of at least `need` bytes
   if (need <= *cap) return true;
   if (*buf) {
-    if (pinned)
-      cudaFreeHost(*buf);
-    else
-      cudaFree(*buf);
+    cudaFree(*buf);
     *buf = nullptr;
     *cap = 0;
   }
   size_t want = need + need / 4;
-  cudaError_t e = pinned ? cudaMallocHost(buf, want) : cudaMalloc(buf, want);
-  if (e != cudaSuccess) {
+  if (cudaMalloc(buf, want) != cudaSuccess) {
     cudaGetLastError();
     *buf = nullptr;
     return false;
@@ -313,17 +307,15 @@ void gemm_offload(bool cplx, const char* transa, const char* transb, const int* 
       return;
     }
   }
-  bool gpu = g_ctx != nullptr && g_strategy == kCopy && grow(&g_pinned, &g_pinned_cap, total, true) &&
-             grow(&g_dev, &g_dev_cap, total, false);
+  // copies: DMA straight from and to the caller's (pageable) arrays, no CPU staging copy
+  bool gpu = g_ctx != nullptr && g_strategy == kCopy && grow(&g_dev, &g_dev_cap, total);
   if (gpu) {
-    char* hp = static_cast<char*>(g_pinned);
     char* dp = static_cast<char*>(g_dev);
-    if (sA) std::memcpy(hp + oA, A, sA * esz);
-    if (sB) std::memcpy(hp + oB, B, sB * esz);
     const bool need_c = !beta_zero;
-    if (need_c) std::memcpy(hp + oC, C, sC * esz);
-    const size_t up = need_c ? total : oC;
-    cudaError_t e = cudaMemcpyAsync(dp, hp, up, cudaMemcpyHostToDevice, g_stream);
+    cudaError_t e = cudaSuccess;
+    if (sA) e = cudaMemcpyAsync(dp + oA, A, sA * esz, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess && sB) e = cudaMemcpyAsync(dp + oB, B, sB * esz, cudaMemcpyHostToDevice, g_stream);
+    if (e == cudaSuccess && need_c) e = cudaMemcpyAsync(dp + oC, C, sC * esz, cudaMemcpyHostToDevice, g_stream);
     if (e == cudaSuccess) {
       const double* dA = reinterpret_cast<const double*>(dp + oA);
       const double* dB = reinterpret_cast<const double*>(dp + oB);
@@ -332,7 +324,9 @@ void gemm_offload(bool cplx, const char* transa, const char* transb, const int* 
       rc = cplx ? ozg_zgemm(g_ctx, ta, tb, m, n, k, alpha, dA, lda, dB, ldb, beta, dC, ldc, g_mode, nullptr)
                 : ozg_dgemm(g_ctx, ta, tb, m, n, k, alpha[0], dA, lda, dB, ldb, beta[0], dC, ldc, g_mode, nullptr);
       if (rc == OZG_OK) {
-        e = cudaMemcpyAsync(hp + oC, dC, sC * esz, cudaMemcpyDeviceToHost, g_stream);
+        // rows 0 .. m-1 of each column only: rows m .. ldc-1 stay untouched
+        e = cudaMemcpy2DAsync(C, (size_t)ldc * esz, dC, (size_t)ldc * esz, (size_t)m * esz, (size_t)n,
+                              cudaMemcpyDeviceToHost, g_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g_stream);
         if (e == cudaSuccess) rc = ozg_sync(g_ctx);
         else rc = OZG_ERR_CUDA;
@@ -342,9 +336,6 @@ void gemm_offload(bool cplx, const char* transa, const char* transb, const int* 
     }
     if (e != cudaSuccess) cudaGetLastError();
     if (rc == OZG_OK) {
-      for (int j = 0; j < n; ++j)  // rows m .. ldc-1 of each column stay untouched
-        std::memcpy(reinterpret_cast<char*>(C) + (size_t)j * ldc * esz, hp + oC + (size_t)j * ldc * esz,
-                    (size_t)m * esz);
       ++g_offloaded;
       return;
     }

@@ -1,4 +1,4 @@
-"""The dgemm_/zgemm_ interposition library (host buffers, pinned staging, synchronous) against
+"""The dgemm_/zgemm_ interposition library (host buffers, synchronous) against
 the oracle, and its interposition over a CPU BLAS with LD_PRELOAD."""
 import ctypes
 import os
@@ -135,7 +135,7 @@ def in_place_supported(shim, strategy):
 
 
 def test_shim_data_strategies_same_bits(shim):
-    """The three data strategies (pinned copies, coherent in-place access, migration on first
+    """The three data strategies (DMA copies, coherent in-place access, migration on first
     use) give the same bits: a real call with beta != 0 and padding rows (left untouched), equal
     to the oracle's definition, and a complex conjugate-transpose call."""
     assert shim.ozg_blas_set_mode(7) == 0
