@@ -987,19 +987,24 @@ int slice_gemm_tile_n() { return 256; }
 int slice_gemm_tile_n_of(int variant) { return (variant & 1) ? 128 : 256; }
 size_t slice_gemm_smem_bytes() { return Cfg<256, 1>::SMEM; }
 
-// Tensor map of a digit-plane set.  L2 promotion is 128 bytes, one row segment of a 64-wide box:
-// half of the groups sweep k backwards, and a wider promotion fetches k the sweep has already
-// passed (measured: 256-byte promotion makes the learned 2048-GEMM step 1 ms slower).
+// Tensor map of a digit-plane set.  Half of the groups sweep k backwards, so a promotion wider
+// than one 128-byte row segment of a 64-wide box fetches k that the sweep has already passed.
+// That costs on short k (256-byte promotion: the learned step over 2048 GEMMs with k <= 2048 is
+// 1 ms slower) and pays on long k, where it halves the L2 requests of a long sweep (256-byte
+// promotion: the 8192^3 launch is 19.5 -> 18.9 ms).
+constexpr int64_t kWidePromotionMinK = 2049;
 cudaError_t make_digit_tmap(CUtensorMap* map, const __half* D, int64_t k, int64_t rows, int64_t Kp, int s,
                             int box_rows) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return cudaErrorNotSupported;
+  const CUtensorMapL2promotion promo =
+      k >= kWidePromotionMinK ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
   cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, (cuuint64_t)s};
   cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(rows * Kp * 2)};
   cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, const_cast<__half*>(D), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, promo,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
