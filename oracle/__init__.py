@@ -46,7 +46,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # OZG_ORACLE_LIB: a separately compiled copy of this file's C source (the mutation
+            # tests load copies with one planted mistake each and expect the pins to fail)
+            lib = ctypes.CDLL(os.environ.get("OZG_ORACLE_LIB") or build())
             c_i64, c_dbl, c_int, c_char, vp = (ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                                ctypes.c_char, ctypes.c_void_p)
             lib.orc_dgemm_naive.argtypes = [c_char, c_char, c_i64, c_i64, c_i64, c_dbl, vp, c_i64, vp, c_i64,

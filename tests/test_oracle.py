@@ -251,6 +251,24 @@ def test_emu_rounding_ties_and_subnormals():
     assert C[0, 0] == np.inf
 
 
+def test_emu_single_rounding_at_the_subnormal_and_overflow_edges():
+    """One rounding of the exact sum, also where a 53-bit rounding followed by a second one onto
+    the subnormal grid (or past the largest finite value) would differ (s = 18 keeps every term).
+    2^-1075 + 2^-1130 lies above half of the smallest subnormal, so RN gives 2^-1074, while
+    rounding to 53 bits first gives exactly 2^-1075, whose tie goes to 0.  The largest finite
+    double plus half its ulp (2^970) ties to even, which is upwards here: +inf."""
+    A = np.array([[2.0 ** -500, 2.0 ** -555]])
+    B = np.array([[2.0 ** -575], [2.0 ** -575]])
+    assert oracle.dgemm_emu(A, B, 18)[0, 0] == 2.0 ** -1074
+    assert oracle.dgemm_emu(-A, B, 18)[0, 0] == -(2.0 ** -1074)
+    big = float(np.finfo(np.float64).max)
+    assert big == 2.0 ** 1023 + (2.0 ** 1023 - 2.0 ** 971)
+    A = np.array([[2.0 ** 1023, 2.0 ** 1023 - 2.0 ** 971, 2.0 ** 970]])
+    B = np.ones((3, 1))
+    assert oracle.dgemm_emu(A, B, 18)[0, 0] == np.inf
+    assert oracle.dgemm_emu(A[:, :2], B[:2], 18)[0, 0] == big        # exactly the largest finite
+
+
 def test_emu_triangle_matches_definition_on_tiny():
     # brute-force T from the (already pinned) digits with Python integers, then RN
     rng = np.random.default_rng(11)
@@ -311,11 +329,26 @@ def test_emu_transposes_alpha_beta(ta, tb):
     C0 = rng.normal(size=(m, n))
     t = oracle.dgemm_emu(np.asfortranarray(opA), np.asfortranarray(opB), s)
     C = oracle.dgemm_emu(A, B, s, ta, tb, alpha=-0.75, beta=0.5, C=C0)
-    exp = np.array([[math.fma(-0.75, t[i, j], 0.5 * C0[i, j]) for j in range(n)] for i in range(m)]) \
-        if hasattr(math, "fma") else None
-    if exp is not None:
-        assert (C == exp).all()
+    exp = np.array([[fma_exact(-0.75, t[i, j], 0.5 * C0[i, j]) for j in range(n)] for i in range(m)])
+    assert (C == exp).all()
     np.testing.assert_allclose(C, -0.75 * opA @ opB + 0.5 * C0, rtol=0, atol=1e-9)
+
+
+def fma_exact(x, y, z):
+    """RN(x y + z) with one rounding: the sum formed exactly in rationals, then rounded to the
+    nearest double (CPython's int / int division rounds correctly)."""
+    return float(Fraction(x) * Fraction(y) + Fraction(z))
+
+
+def test_emu_alpha_beta_single_rounding_directed():
+    """C = RN(alpha t + RN(beta C_old)) in one rounding (the fma reading of the update): with
+    alpha = t = 1 + 2^-30 and beta C_old = -(1 + 2^-29), the exact update is 2^-60, while
+    rounding alpha t first would give 0."""
+    x = 1.0 + 2.0 ** -30
+    A, B = np.array([[x]]), np.array([[1.0]])
+    C0 = np.array([[1.0 + 2.0 ** -29]])
+    C = oracle.dgemm_emu(A, B, 6, alpha=x, beta=-1.0, C=C0)   # 31 significant bits: exact at s = 6
+    assert C[0, 0] == 2.0 ** -60 == fma_exact(x, x, -(1.0 + 2.0 ** -29))
 
 
 def test_emu_trend_error_falls_per_slice():
@@ -393,6 +426,23 @@ def test_zemu_error_bound_and_alpha_beta():
     np.testing.assert_allclose(C2, al * C + be * C0, rtol=1e-13, atol=1e-13)
 
 
+def test_zemu_alpha_beta_single_rounding_directed():
+    """Complex update in the fma order: Re = RN(alpha_r t_r - RN(alpha_i t_i)) and
+    Im = RN(alpha_r t_i + RN(alpha_i t_r)).  With t = (1 + 2^-30) + i (1 + 2^-29) and alpha =
+    (1 + 2^-30) + i, the exact real part is 2^-60, which rounding alpha_r t_r first would lose."""
+    x, y = 1.0 + 2.0 ** -30, 1.0 + 2.0 ** -29
+    A, B = np.array([[complex(x, y)]]), np.array([[1.0 + 0j]])
+    C = oracle.zgemm_emu(A, B, 6, alpha=complex(x, 1.0))   # 31 significant bits: exact at s = 6
+    assert C[0, 0].real == 2.0 ** -60 == fma_exact(x, x, -(1.0 * y))
+    assert C[0, 0].imag == fma_exact(x, y, 1.0 * x)
+    be = complex(1.0, -(1.0 + 2.0 ** -30))
+    C0 = np.array([[complex(x, 2.0)]])
+    C = oracle.zgemm_emu(A, B, 6, alpha=complex(x, 1.0), beta=be, C=C0)
+    br = fma_exact(be.real, C0[0, 0].real, -(be.imag * C0[0, 0].imag))
+    bi = fma_exact(be.real, C0[0, 0].imag, be.imag * C0[0, 0].real)
+    assert C[0, 0].real == 2.0 ** -60 + br and C[0, 0].imag == fma_exact(x, y, 1.0 * x) + bi
+
+
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "T"), ("N", "C"), ("C", "T")])
 def test_z3m_small_integers_exact_with_alpha_beta(ta, tb):
     """3M on small integers: every emulated product, difference and alpha/beta step is exact, so
@@ -449,3 +499,57 @@ def test_kkr_kappa_variant_has_the_requested_condition_number():
     assert np.array_equal(A[off], A0[off])  # only the diagonal shift differs
     sv = np.linalg.svd(A, compute_uv=False)
     assert 1e8 / 1.5 <= sv[0] / sv[-1] <= 1e8 * 1.5
+
+
+# ------------------------------------------------------------------ worked example (golden)
+GOLDEN = __import__("pathlib").Path(__file__).parent / "golden"
+
+
+def read_golden(name):
+    """key -> list of rows of Fractions from a tests/golden fixture ('a b ; c d' = two rows)."""
+    out = {}
+    for line in (GOLDEN / name).read_text().splitlines():
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, vals = line.split(":", 1)
+        out[key.strip()] = [[Fraction(v) for v in row.split()] for row in vals.split(";")]
+    return out
+
+
+def test_worked_example_split_groups_and_triangle_by_hand():
+    """The hand-derived example of tests/golden/worked_example_split_triangle.txt (Sec. 2.2):
+    exponents, digits and group products equal the derivation; s = 2 drops exactly the pair
+    (2, 2) of group 4 (+15 / 2^28 on entry (1, 1)), and s = 3 gives the exact product."""
+    g = read_golden("worked_example_split_triangle.txt")
+    A = np.array([[float(x) for x in r] for r in g["A"]])
+    B = np.array([[float(x) for x in r] for r in g["B"]])
+    e, DA = oracle.split(A, 3)
+    f, DB = oracle.split_cols(B, 3)
+    assert e.tolist() == [int(x) for x in g["e"][0]]
+    assert f.tolist() == [int(x) for x in g["f"][0]]
+    for t in range(3):
+        assert DA[t].tolist() == [[int(x) for x in r] for r in g[f"DA_{t + 1}"]]
+        assert DB[t].tolist() == [[int(x) for x in r] for r in g[f"DB_{t + 1}"]]
+    G = oracle.group_products(DA, DB)
+    for gi in range(3):
+        assert G[gi].tolist() == [[int(x) for x in r] for r in g[f"G_s3_g{gi + 2}"]]
+    exact = frac_matmul(A, B)
+    assert exact == g["C_exact"]
+    for s in (2, 3):
+        C = oracle.dgemm_emu(A, B, s)
+        assert [[Fraction(float(x)) for x in r] for r in C] == g[f"C_s{s}"]
+    # the dropped pair, by itself: s = 2 minus the exact product on entry (1, 1)
+    assert Fraction(float(oracle.dgemm_emu(A, B, 2)[0, 0])) - exact[0][0] == Fraction(15, 2 ** 28)
+
+
+@pytest.mark.parametrize("ta", ["N", "C"])
+def test_worked_example_complex_by_hand(ta):
+    """The one-element complex example of the same fixture: shared exponent, conjugation of the
+    imaginary digits for op = 'C', and the exact product at s = 1."""
+    g = read_golden("worked_example_split_triangle.txt")
+    a = complex(float(g["zA"][0][0]), float(g["zA"][0][1]))
+    b = complex(float(g["zB"][0][0]), float(g["zB"][0][1]))
+    C = oracle.zgemm_emu(np.array([[a]]), np.array([[b]]), 1, transa=ta)
+    want = g[f"zC_{ta}"][0]
+    assert (Fraction(C[0, 0].real), Fraction(C[0, 0].imag)) == (want[0], want[1])

@@ -1,0 +1,111 @@
+"""The oracle's pins catch plausible mistakes.  Each mutant is a copy of oracle/ozaki_oracle.c
+with one mistake planted (a dropped term, a wrong sign or index, a transposed operand, a wrong
+rounding rule), compiled on the CPU into its own library; the pin suites (tests/test_oracle.py,
+tests/test_oracle_selector.py) then run against that library in a subprocess and must fail.
+The unmodified source, compiled the same way, must pass (the control), so a failure comes from
+the planted mistake and not from the harness.  No GPU is involved."""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "ozaki_oracle.c")
+
+# (name, text in the source, replacement): each text occurs exactly once
+MUTANTS = [
+    ("digits rounded instead of truncated", "    double q = trunc(y);", "    double q = round(y);"),
+    ("row exponent off by one", "    e[i] = ex;\n    for (int64_t l = 0; l < k; ++l) {\n      double a = ldexp(",
+     "    e[i] = ex + 1;\n    for (int64_t l = 0; l < k; ++l) {\n      double a = ldexp("),
+    ("last group dropped", "  for (int gi = 0; gi < ng; ++gi) {\n    int g = gi + 2;",
+     "  for (int gi = 0; gi < ng - 1; ++gi) {\n    int g = gi + 2;"),
+    ("triangle bound p + q <= s", "if (!square && p + q > s + 1) continue;", "if (!square && p + q > s) continue;"),
+    ("column exponent with the wrong sign", "int64_t E = (int64_t)ei + fj - 7 * top;",
+     "int64_t E = (int64_t)ei - fj - 7 * top;"),
+    ("op(X) indexes transposed", "return (t == 'N' || t == 'n') ? X[r + c * ld] : X[c + r * ld];",
+     "return (t == 'N' || t == 'n') ? X[c + r * ld] : X[r + c * ld];"),
+    ("final rounding: ties away from zero", "if (rbit && (sticky || (Q & 1ull))) Q += 1;", "if (rbit) Q += 1;"),
+    ("final rounding: sticky bits ignored", "if (rbit && (sticky || (Q & 1ull))) Q += 1;",
+     "if (rbit && (Q & 1ull)) Q += 1;"),
+    ("two_sum without the error of b", "dd_t r = {s, (a - (s - bb)) + (b - bb)};", "dd_t r = {s, (a - (s - bb))};"),
+    ("double-double reference drops beta C", "if (beta != 0.0) r = dd_add(r, two_prod(beta, C[i + j * ldc]));",
+     "if (0) r = dd_add(r, two_prod(beta, C[i + j * ldc]));"),
+    ("complex combine Re = rr + ii", "Gc[((int64_t)gi * m + i) * n + j] = rr - ii;",
+     "Gc[((int64_t)gi * m + i) * n + j] = rr + ii;"),
+    ("conjugation not applied", "*im = (t == 'C' || t == 'c') ? -p[1] : p[1];", "*im = p[1];"),
+    ("complex exponent from the real parts only",
+     "      if (fabs(re) > amax) amax = fabs(re);\n      if (fabs(im) > amax) amax = fabs(im);\n",
+     "      if (fabs(re) > amax) amax = fabs(re);\n"),
+    ("3M imaginary part RN(P3 - P1) + P2", "double ti = d - p2;", "double ti = d + p2;"),
+    ("alpha and beta in two roundings instead of one fma",
+     "*c = (beta == 0.0) ? alpha * t : fma(alpha, t, beta * (*c));",
+     "*c = (beta == 0.0) ? alpha * t : alpha * t + beta * (*c);"),
+    ("a priori bound 2^7 too small", "ldexp(acc * (1.0 + 4.0 * k * ldexp(1.0, -53)), e[i] + f[j] - 7 * s)",
+     "ldexp(acc * (1.0 + 4.0 * k * ldexp(1.0, -53)), e[i] + f[j] - 7 * s - 7)"),
+    ("feature bins five wide", "bin = gap < 36 ? (gap < 0 ? 0 : gap / 4) : 9;",
+     "bin = gap < 36 ? (gap < 0 ? 0 : gap / 5) : 9;"),
+    ("BF16 rounding ties away", "u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0x8000u;"),
+    ("ReLU derivative dropped in layer 1", "dh1[j] = h1[j] > 0 ? a : 0;", "dh1[j] = a;"),
+    ("selector decision one class high", "int s = chosen < 0 ? fallback : s_lo + chosen;",
+     "int s = chosen < 0 ? fallback : s_lo + chosen + 1;"),
+    ("complex alpha in two roundings", "double re = fma(alpha[0], tr, -(alpha[1] * ti));\n      double im = fma(alpha[0], ti, alpha[1] * tr);\n      if (do_beta) {\n        double br = fma(beta[0], c[0], -(beta[1] * c[1]));\n        double bi = fma(beta[0], c[1], beta[1] * c[0]);\n        re += br; im += bi;\n      }\n      c[0] = re; c[1] = im;\n    }\n  free(e);",
+     "double re = alpha[0] * tr - alpha[1] * ti;\n      double im = fma(alpha[0], ti, alpha[1] * tr);\n      if (do_beta) {\n        double br = fma(beta[0], c[0], -(beta[1] * c[1]));\n        double bi = fma(beta[0], c[1], beta[1] * c[0]);\n        re += br; im += bi;\n      }\n      c[0] = re; c[1] = im;\n    }\n  free(e);"),
+    ("double-double times a double drops the low part", "  p.lo += a.lo * b;\n", ""),
+    ("naive GEMM ignores alpha when beta != 0", "alpha * acc + beta * (*c);", "acc + beta * (*c);"),
+    ("slice products pair digits of different k", "for (int64_t l = 0; l < k; ++l) acc += (int64_t)a[l] * (int64_t)b[l];",
+     "for (int64_t l = 0; l < k; ++l) acc += (int64_t)a[l] * (int64_t)b[k - 1 - l];"),
+    ("op(B) = B^H without the conjugation", "digits_of(ldexp(-p[1], -ex), s, &DB[(2 * j + 1) * k + l], R2 * k);",
+     "digits_of(ldexp(p[1], -ex), s, &DB[(2 * j + 1) * k + l], R2 * k);"),
+    ("subnormal results not clamped to 2^-1074", "  if (q < -1074) q = -1074;\n", ""),
+    ("overflow saturates at the largest finite value", "if (top > 1023) return neg ? -INFINITY : INFINITY;",
+     "if (top > 1023) return neg ? -1.7976931348623157e308 : 1.7976931348623157e308;"),
+    ("a dropped dd error term in the complex reference", "        sr = dd_add(sr, two_prod(-ai, bi));\n", ""),
+]
+
+PIN_SUITES = ["tests/test_oracle.py", "tests/test_oracle_selector.py"]
+# a workload-generator test with no oracle arithmetic, and the slowest of the suites
+DESELECT = "not kkr_kappa"
+
+
+def _compile(text, out):
+    c_path = out + ".c"
+    with open(c_path, "w") as f:
+        f.write(text)
+    subprocess.check_call(["gcc", *oracle._CFLAGS, c_path, "-o", out, "-lm"])
+    return out
+
+
+def _run_pins(lib):
+    env = dict(os.environ, OZG_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                        "-k", DESELECT, *PIN_SUITES], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=900)
+    return r.returncode, (r.stdout + r.stderr)[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    src = open(SRC).read()
+    d = tmp_path_factory.mktemp("mutants")
+    libs = {"control": _compile(src, str(d / "control.so"))}
+    for idx, (name, old, new) in enumerate(MUTANTS):
+        assert src.count(old) == 1, f"mutant '{name}': its text must occur exactly once"
+        libs[name] = _compile(src.replace(old, new), str(d / f"m{idx}.so"))
+    with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as ex:
+        res = dict(zip(libs, ex.map(_run_pins, libs.values())))
+    return res
+
+
+def test_control_copy_passes_the_pins(outcomes):
+    rc, log = outcomes["control"]
+    assert rc == 0, log
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    rc, log = outcomes[name]
+    assert rc == 1, f"mutant '{name}' survived the pins (pytest rc {rc}):\n{log}"

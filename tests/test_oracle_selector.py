@@ -103,6 +103,14 @@ def test_features_closed_forms():
     np.testing.assert_array_equal(f[:23], g[:23])
 
 
+def test_features_bin_edges():
+    """Gaps on the bin edges: the row maximum 1.0 has frexp exponent 1; 2^-3, 2^-4, 2^-35 and
+    2^-36 have gaps 3, 4, 35 and 36, so they fall in [0, 4), [4, 8), [32, 36) and the last bin."""
+    A = np.array([[1.0, 2.0 ** -3, 2.0 ** -4, 2.0 ** -35, 2.0 ** -36]])
+    f = oracle.features(A, np.ones((5, 1)), 1e-12)
+    np.testing.assert_array_equal(f[3:13], np.array([2, 1, 0, 0, 0, 0, 0, 0, 1, 1], np.float32) / 5)
+
+
 def test_selector_training_helpers_match_oracle_inference(tmp_path):
     """The training tool's NumPy forward pass and decision rule (used to choose the decision
     threshold on held-out GEMMs) agree with the oracle's FP32 emulation of the GPU inference."""
