@@ -111,7 +111,7 @@ def measured_peaks():
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("ozg_gemm.cu", "ozg_device.cuh", "ozg_internal.h"):
+    for f in ("ozg_gemm.cu", "ozg_device.cuh", "ozg_internal.h", "ozg_round.cuh"):
         with open(os.path.join(ROOT, "paper_2503_22875_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

@@ -37,6 +37,7 @@
 // for a whole batch of uneven problems).
 #include "ozg_device.cuh"
 #include "ozg_internal.h"
+#include "ozg_round.cuh"
 
 namespace ozg {
 namespace {
@@ -189,34 +190,6 @@ __device__ __forceinline__ void horner128(const void* Rp, int g, bool first, boo
   lo = nl;
 }
 
-// RN(N 2^E) for the 128-bit integer N = (hi, lo): the top 64 bits with a sticky bit are
-// converted with one correct rounding, then scaled exactly by a power of two.
-__device__ __forceinline__ double round_i128(int64_t hi, uint64_t lo, int E) {
-  const bool neg = hi < 0;
-  uint64_t mh = (uint64_t)hi, ml = lo;
-  if (neg) {
-    ml = ~ml + 1;
-    mh = ~mh + (ml == 0 ? 1 : 0);
-  }
-  double mag;
-  int sh = 0;
-  if (mh == 0) {
-    mag = __ull2double_rn(ml);
-  } else {
-    sh = 64 - __clzll((long long)mh);
-    uint64_t top, sticky;
-    if (sh == 64) {
-      top = mh;
-      sticky = ml != 0;
-    } else {
-      top = (mh << (64 - sh)) | (ml >> sh);
-      sticky = (ml << (64 - sh)) != 0;
-    }
-    mag = __ull2double_rn(top | sticky);
-  }
-  const double v = scale_pow2(mag, E + sh);
-  return neg ? -v : v;
-}
 
 // One output's Horner step in either mode; returns the final value (scaled) on the last push.
 __device__ __forceinline__ double horner_step(void* Rp, int g, bool exact, bool first, bool group2, bool final_push,

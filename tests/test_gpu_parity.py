@@ -429,6 +429,38 @@ def test_zgemm_default_bit_exact_two_windows(ozg, ctx, ta, tb, alpha, beta):
     assert np.array_equal(host(ozg, C, m, n), oracle.zgemm_emu(A, B, s, ta, tb, alpha, beta, C0))
 
 
+@pytest.mark.parametrize("exact", [False, True])
+def test_dgemm_subnormal_and_overflow_results_single_rounding(ozg, ctx, exact):
+    """Results below 2^-1022 and past the largest finite value are rounded once, as the oracle
+    defines them: onto the grid of the smallest subnormal directly (rounding to 53 bits first
+    would take 2^-1075 + 2^-1130 to the tie 2^-1075 and then to 0), or to +-inf; in the default
+    (two-window) and in the exact epilogue."""
+    cases = [(np.asfortranarray([[2.0 ** -500, 2.0 ** -555]]), np.asfortranarray([[2.0 ** -575], [2.0 ** -575]]), 8)]
+    m, n, k = 150, 140, 300
+    for scale, seed in ((-540, 1), (510, 2)):
+        cases.append((np.asfortranarray(wide((m, k), 2.0, 951 + seed) * 2.0 ** scale),
+                      np.asfortranarray(wide((k, n), 2.0, 961 + seed) * 2.0 ** scale), 7))
+    ctx.set_exact_epilogue(exact)
+    try:
+        for i, (A, B, s) in enumerate(cases):
+            m_, k_ = A.shape
+            n_ = B.shape[1]
+            assert windows(s, k_) <= 2
+            C = torch.zeros((n_, m_), dtype=torch.float64, device="cuda")
+            ctx.dgemm("N", "N", m_, n_, k_, 1.0, dev(ozg, A), m_, dev(ozg, B), k_, 0.0, C, m_, s)
+            ctx.sync()
+            want = oracle.dgemm_emu(A, B, s)
+            if i == 0:
+                assert want[0, 0] == 2.0 ** -1074
+            elif i == 1:
+                assert ((want != 0) & (np.abs(want) < 2.0 ** -1022)).sum() > 1000
+            else:
+                assert np.isinf(want).sum() > 100 and np.isfinite(want).sum() > 100
+            assert np.array_equal(host(ozg, C, m_, n_), want)
+    finally:
+        ctx.set_exact_epilogue(False)
+
+
 @pytest.mark.parametrize("k,s", [(1100, 13), (300, 14), (300, 18), (5000, 16)])
 def test_dgemm_three_or_more_windows_fp64(ozg, ctx, k, s):
     """Beyond two windows the partial sum continues in FP64 (one rounding per window): within the
