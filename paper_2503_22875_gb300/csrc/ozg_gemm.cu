@@ -224,73 +224,6 @@ __device__ __forceinline__ int window_len(int s, int64_t kpad, int cplx) {
   return c < 1 ? 1 : c;
 }
 
-// (a 2^sh + b) as a 128-bit two's complement integer (hi, lo), 1 <= sh <= 63.
-__device__ __forceinline__ void i128_shl_add(long long a, int sh, long long b, long long& hi, unsigned long long& lo) {
-  lo = (unsigned long long)a << sh;
-  hi = a >> (64 - sh);
-  const unsigned long long nl = lo + (unsigned long long)b;
-  hi += (b < 0 ? -1 : 0) + (nl < lo ? 1 : 0);
-  lo = nl;
-}
-
-__device__ __noinline__ double round_i128_slow(long long hi, unsigned long long lo, int E) { return round_i128(hi, lo, E); }
-
-// RN(N 2^E) for the 128-bit integer N = (hi, lo), |N| < 2^126: the magnitude's top 64 bits with
-// a sticky bit for everything below are converted with one correctly rounded conversion (the
-// sticky bit sits below the guard bit, so the rounding is that of N itself), and the power of
-// two is applied by adding to the exponent field.  Results outside the normal range take the
-// general path.
-__device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long lo, int E) {
-  const bool neg = hi < 0;
-  unsigned long long mh = (unsigned long long)hi, ml = lo;
-  if (neg) {
-    ml = ~ml + 1;
-    mh = ~mh + (ml == 0 ? 1 : 0);
-  }
-  double mag;
-  int sh = 0;
-  if (mh == 0) {
-    if (ml == 0) return 0.0;
-    mag = __ull2double_rn(ml);
-  } else {
-    sh = 64 - __clzll((long long)mh);  // 1 .. 62 for |N| < 2^126
-    if (sh >= 64) return round_i128_slow(hi, lo, E);
-    const unsigned long long top = (mh << (64 - sh)) | (ml >> sh);
-    const unsigned long long sticky = (ml << (64 - sh)) != 0 ? 1ull : 0ull;
-    mag = __ull2double_rn(top | sticky);
-  }
-  const long long bits = __double_as_longlong(mag);
-  const int ex = (int)(bits >> 52) + E + sh;  // biased exponent of the result
-  if (ex < 1 || ex > 2046) return round_i128_slow(hi, lo, E);
-  const long long r = bits + ((long long)(E + sh) << 52);
-  return __longlong_as_double(neg ? (r | (long long)0x8000000000000000ull) : r);
-}
-
-// RN(N 2^E) for N = W0 2^S + W1 (S = 7 wlen in [7, 56], |W0|, |W1| < 2^62; W0 = 0 for a single
-// window) without data-dependent branches, so the outputs of a chunk interleave.  With
-// q = W0 + floor(W1 / 2^S) and r = W1 mod 2^S, N = q 2^S + r (0 <= r < 2^S) and
-// |N| = qm 2^S + rm with qm = q, rm = r for q >= 0 and qm = -q - 1, rm = 2^S - r (r > 0) or
-// qm = -q, rm = 0 (r = 0) for q < 0.  The top 63 bits of |N| with a sticky bit below them are
-// converted with one correctly rounded conversion and the power of two goes into the exponent
-// field.  `ok` is false when the result is not a normal double (the caller takes final_val).
-__device__ __forceinline__ double rn_windows(long long W0, long long W1, int S, int E, bool& ok) {
-  const long long q = W0 + (W1 >> S);
-  const unsigned long long mask = (1ull << S) - 1ull;
-  const unsigned long long r = (unsigned long long)W1 & mask;
-  const bool neg = q < 0;
-  const unsigned long long qm = neg ? (unsigned long long)(~q) + (r == 0 ? 1ull : 0ull) : (unsigned long long)q;
-  const unsigned long long rm = neg ? ((0ull - r) & mask) : r;
-  const int bl = 64 - __clzll((long long)qm);  // 0 .. 63
-  const int z = max(0, bl + S - 63);           // low bits of |N| below the 63-bit window (<= S)
-  const unsigned long long t =
-      (qm << (S - z)) | (rm >> z) | ((rm & ((1ull << z) - 1ull)) != 0 ? 1ull : 0ull);
-  const long long bits = __double_as_longlong(__ull2double_rn(t));
-  const int ex = (int)(bits >> 52) + z + E;  // biased exponent of the result
-  ok = t == 0 || (ex >= 1 && ex <= 2046);
-  const long long rb = bits + ((long long)(z + E) << 52);
-  return t == 0 ? 0.0 : __longlong_as_double(neg ? (rb | (long long)0x8000000000000000ull) : rb);
-}
-
 // Window-closing or final step of one output, given the first slot's word s0 (int64 W0 while
 // widx == 1, FP64 bits from the second window's close on) and the active window Rw after this
 // push.  Final: returns RN(N 2^E).  Closing: returns the new s0 word.
