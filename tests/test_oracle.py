@@ -488,6 +488,34 @@ def test_z3m_error_within_its_bound(s):
     assert (bim < 1e-1 * oracle.abs_product(np.abs(A.real) + np.abs(A.imag), np.abs(B.real) + np.abs(B.imag))).all()
 
 
+def test_z3m_bound_covers_an_error_of_the_sum_product_alone():
+    """A directed 3M case whose imaginary error comes from the third product only: Ar = Bi = 1,
+    Ai = Br = 2^-30 are exact in one digit each (P1 = P2 = 2^-30 exactly), while
+    Sa = Sb = 1 + 2^-30 lose their 2^-30 parts at s = 3, so P3 = 1 and Im = RN(RN(1 - 2^-30)
+    - 2^-30) = 1 - 2^-29 against the exact 1 + 2^-60.  The bound must cover that error, which
+    the other terms of the bound (each near 2^-46 here) cannot."""
+    t = 2.0 ** -30
+    A, B = np.array([[complex(1.0, t)]]), np.array([[complex(t, 1.0)]])
+    C = oracle.zgemm3m_emu(A, B, 3)
+    assert C[0, 0].imag == 1.0 - 2.0 * t and C[0, 0].real == 0.0
+    err = abs(Fraction(C[0, 0].imag) - (1 + Fraction(t) ** 2))
+    bre, bim = oracle.zgemm3m_bound(A, B, 3)
+    assert Fraction(float(bim[0, 0])) >= err > Fraction(t)
+    assert bre[0, 0] >= abs(Fraction(C[0, 0].real) - (Fraction(t) - Fraction(t)))
+
+
+def test_rel_err_metric_closed_form():
+    """max |C - C_dd| / (|alpha| |A||B| + |beta| |C0|): with A = B = 1, alpha = 4, beta = -2,
+    C0 = 3, the exact update is 4 - 6 = -2, so C = -2 + 2^-40 has error 2^-40 over the scale
+    4 + 6 = 10; a zero-scale entry with a zero difference counts 0."""
+    A, B = np.array([[1.0, 0.0]]), np.array([[1.0, 0.0], [0.0, 0.0]])
+    C0 = np.array([[3.0, 0.0]])
+    C = np.array([[-2.0 + 2.0 ** -40, 0.0]])
+    r = oracle.rel_err_vs_dd(C, A, B, alpha=4.0, beta=-2.0, C0=C0)
+    assert r == 2.0 ** -40 / 10
+    assert oracle.rel_err_vs_dd(np.array([[2.0 ** -40 + 1.0, 0.0]]), A, B) == 2.0 ** -40
+
+
 def test_kkr_kappa_variant_has_the_requested_condition_number():
     """The KKR-like stand-in's conditioned variant: the cached diagonal shift puts cond_2(A)
     within a factor 1.5 of 1e8 (SVD on the host), and B is the unshifted-workload's B."""

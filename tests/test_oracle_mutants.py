@@ -1,10 +1,12 @@
 """The oracle's pins catch plausible mistakes.  Each mutant is a copy of oracle/ozaki_oracle.c
 with one mistake planted (a dropped term, a wrong sign or index, a transposed operand, a wrong
-rounding rule), compiled on the CPU into its own library; the pin suites (tests/test_oracle.py,
-tests/test_oracle_selector.py) then run against that library in a subprocess and must fail.
-The unmodified source, compiled the same way, must pass (the control), so a failure comes from
-the planted mistake and not from the harness.  No GPU is involved."""
+rounding rule), compiled on the CPU into its own library, or a copy of the oracle package whose
+Python half (oracle/__init__.py) carries the mistake; the pin suites (tests/test_oracle.py,
+tests/test_oracle_selector.py) then run against it in a subprocess and must fail.  The
+unmodified sources, compiled and copied the same way, must pass (the controls), so a failure
+comes from the planted mistake and not from the harness.  No GPU is involved."""
 import os
+import shutil
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -15,6 +17,7 @@ import oracle
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ozaki_oracle.c")
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
 
 # (name, text in the source, replacement): each text occurs exactly once
 MUTANTS = [
@@ -66,6 +69,22 @@ MUTANTS = [
     ("a dropped dd error term in the complex reference", "        sr = dd_add(sr, two_prod(-ai, bi));\n", ""),
 ]
 
+# mistakes planted in the Python half of the oracle (oracle/__init__.py)
+PY_MUTANTS = [
+    ("3M operand Sa = Ar - Ai", "return (Ar, Ai, np.asfortranarray(Ar + Ai)), (Br, Bi, np.asfortranarray(Br + Bi))",
+     "return (Ar, Ai, np.asfortranarray(Ar - Ai)), (Br, Bi, np.asfortranarray(Br + Bi))"),
+    ("op(X) = X^T for 'C' (no conjugation)", "return np.asfortranarray(X if t in \"Nn\" else (X.T if t in \"Tt\" else X.conj().T))",
+     "return np.asfortranarray(X if t in \"Nn\" else X.T)"),
+    ("3M product P3 one slice short", "P3 = dgemm_emu(Ar, Br, s), dgemm_emu(Ai, Bi, s), dgemm_emu(Sa, Sb, s)",
+     "P3 = dgemm_emu(Ar, Br, s), dgemm_emu(Ai, Bi, s), dgemm_emu(Sa, Sb, s - 1)"),
+    ("|A||B| without the absolute values", "return dgemm_naive(np.abs(np.asarray(A)), np.abs(np.asarray(B)), transa, transb)",
+     "return dgemm_naive(np.asarray(A), np.asarray(B), transa, transb)"),
+    ("error metric ignores alpha", "scale = abs(alpha) * abs_product(A, B, transa, transb)",
+     "scale = abs_product(A, B, transa, transb)"),
+    ("3M bound without the third product's error", "im = e3 + e1 + e2 + u * (P3 + P1 + P2)",
+     "im = e1 + e2 + u * (P3 + P1 + P2)"),
+]
+
 PIN_SUITES = ["tests/test_oracle.py", "tests/test_oracle_selector.py"]
 # a workload-generator test with no oracle arithmetic, and the slowest of the suites
 DESELECT = "not kkr_kappa"
@@ -79,33 +98,57 @@ def _compile(text, out):
     return out
 
 
-def _run_pins(lib):
-    env = dict(os.environ, OZG_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+def _run_pins(job):
+    """job = (library, tree): the pin suites of `tree` (the repository, or a copy holding a mutated
+    oracle package) against the compiled oracle `library`."""
+    lib, tree = job
+    env = dict(os.environ, OZG_ORACLE_LIB=lib, OMP_NUM_THREADS="2",
+               PYTHONPATH=os.pathsep.join([ROOT, os.environ.get("PYTHONPATH", "")]))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
-                        "-k", DESELECT, *PIN_SUITES], cwd=ROOT, env=env, capture_output=True, text=True,
+                        "-k", DESELECT, *PIN_SUITES], cwd=tree, env=env, capture_output=True, text=True,
                        timeout=900)
     return r.returncode, (r.stdout + r.stderr)[-2000:]
+
+
+def _py_tree(d, text):
+    """A copy of the oracle package (with __init__.py replaced by `text`) and of the pin suites."""
+    os.makedirs(os.path.join(d, "oracle"))
+    os.makedirs(os.path.join(d, "tests"))
+    with open(os.path.join(d, "oracle", "__init__.py"), "w") as f:
+        f.write(text)
+    shutil.copy(SRC, os.path.join(d, "oracle"))
+    for name in ("conftest.py", "test_oracle.py", "test_oracle_selector.py"):
+        shutil.copy(os.path.join(ROOT, "tests", name), os.path.join(d, "tests"))
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), os.path.join(d, "tests", "golden"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), d)
+    return d
 
 
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     src = open(SRC).read()
+    py = open(PY_SRC).read()
     d = tmp_path_factory.mktemp("mutants")
-    libs = {"control": _compile(src, str(d / "control.so"))}
+    control = _compile(src, str(d / "control.so"))
+    jobs = {"control": (control, ROOT), "control (copied tree)": (control, _py_tree(str(d / "pyc"), py))}
     for idx, (name, old, new) in enumerate(MUTANTS):
         assert src.count(old) == 1, f"mutant '{name}': its text must occur exactly once"
-        libs[name] = _compile(src.replace(old, new), str(d / f"m{idx}.so"))
+        jobs[name] = (_compile(src.replace(old, new), str(d / f"m{idx}.so")), ROOT)
+    for idx, (name, old, new) in enumerate(PY_MUTANTS):
+        assert py.count(old) == 1, f"mutant '{name}': its text must occur exactly once"
+        jobs[name] = (control, _py_tree(str(d / f"py{idx}"), py.replace(old, new)))
     with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as ex:
-        res = dict(zip(libs, ex.map(_run_pins, libs.values())))
+        res = dict(zip(jobs, ex.map(_run_pins, jobs.values())))
     return res
 
 
-def test_control_copy_passes_the_pins(outcomes):
-    rc, log = outcomes["control"]
+@pytest.mark.parametrize("name", ["control", "control (copied tree)"])
+def test_control_copy_passes_the_pins(outcomes, name):
+    rc, log = outcomes[name]
     assert rc == 0, log
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS + PY_MUTANTS])
 def test_planted_mistake_fails_a_pin(outcomes, name):
     rc, log = outcomes[name]
     assert rc == 1, f"mutant '{name}' survived the pins (pytest rc {rc}):\n{log}"
