@@ -131,10 +131,12 @@ int ozg_selector_grads(ozg_ctx* ctx, const float* X, const int* y, int B, float*
 int ozg_selector_train_step(ozg_ctx* ctx, const float* X, const int* y, int B, float lr, float* loss);
 
 /* enable != 0: correctly rounded mode for single calls with s <= 13.  The group products are
- * summed exactly as 128-bit integers and each result is rounded to FP64 once (bit-identical to
- * the exact value's rounding, except in the subnormal range).  It moves twice the scratch
- * traffic of the default epilogue (FP64 partial sums, one rounding per group) and is slower.
- * Grouped calls always use the default epilogue. */
+ * summed exactly as 128-bit integers and each result is rounded to FP64 once: RN of the exact
+ * value, subnormal and overflowing results included.  The default epilogue is exact in the same
+ * way while its sum fits two int64 windows (s <= 10 at any k, s <= 12 for k <= 512) and continues
+ * in FP64 beyond that (one rounding per further window); this mode stays exact up to s = 13 at
+ * any k, moves 16 bytes of scratch per output and is slower.  Grouped calls always use the
+ * default epilogue. */
 int ozg_set_exact_epilogue(ozg_ctx* ctx, int enable);
 
 /* Human-readable text for a return code (static storage). */
