@@ -117,18 +117,32 @@ def source_hash():
     return h.hexdigest()
 
 
-def kernel_traffic(name: str):
-    """Per-launch DRAM bytes from the committed ncu summary profiles/<name>.md, or None when it is
-    missing or was taken on a different version of the kernel source."""
+def profile_traffic(name: str):
+    """(bytes, sha256 of the kernel sources it was taken on) from the committed ncu summary
+    profiles/<name>.md, or (None, None) when it is missing."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
-        return None
+        return None, None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    if not m or not h or h.group(1) != source_hash():
+    return (float(m.group(1)) if m else None), (h.group(1) if h else None)
+
+
+def kernel_traffic(name: str):
+    """Per-launch DRAM bytes of the current kernel source, or None when the summary is missing or
+    was taken on a different version of the kernel source."""
+    t, sha = profile_traffic(name)
+    return t if t is not None and sha == source_hash() else None
+
+
+def stale_traffic(name: str):
+    """The last capture's figure when it was taken on other kernel sources (reported beside the
+    null traffic, never as the traffic), else None."""
+    t, sha = profile_traffic(name)
+    if t is None or sha is None or sha == source_hash():
         return None
-    return float(m.group(1))
+    return {"bytes_per_launch": t, "source_sha256": sha, "profile": f"profiles/{name}.md"}
 
 
 def tensor_roofline(kernel, flops, ms, traffic_name):
@@ -141,6 +155,7 @@ def tensor_roofline(kernel, flops, ms, traffic_name):
     achieved = flops / (ms / 1e3) / 1e12
     return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": kernel_traffic(traffic_name),
+            "traffic_other_source": stale_traffic(traffic_name),
             "peak_src": f"{src} bf16 burst (cuBLAS); sustained {peaks.get('bf16_tflops_sustained')}",
             "frac_of_sustained": achieved / peaks.get("bf16_tflops_sustained", peak),
             "tensor_flops_per_launch": flops, "launch_ms": ms}
