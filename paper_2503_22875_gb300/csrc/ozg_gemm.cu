@@ -210,20 +210,6 @@ __device__ __forceinline__ double horner_step(void* Rp, int g, bool exact, bool 
   return 0.0;
 }
 
-// ---- integer windows (default epilogue) ----------------------------------------------------
-// The group sums enter R by Horner's rule in exact int64 arithmetic, c consecutive groups per
-// window, where c is the largest count whose worst case stays below 2^63:
-//   |G_g| <= (g - 1) * kpad * 127^2 (x2 for the complex combine) <= gmax < 2^L,
-//   |window| < gmax * 128^(c-1) * 128/127 < 2^(L + 7 (c - 1) + 1)   =>   c = (62 - L) / 7 + 1.
-// Two windows form the exact 128-bit N = W0 128^len1 + W1, rounded to FP64 once with integer
-// instructions only; a third and later window continue in FP64 (one rounding per window).
-__device__ __forceinline__ int window_len(int s, int64_t kpad, int cplx) {
-  const unsigned long long gmax = (unsigned long long)s * (unsigned long long)kpad * 16129ull * (cplx ? 2ull : 1ull);
-  const int L = 64 - __clzll((long long)gmax);
-  const int c = (62 - L) / 7 + 1;
-  return c < 1 ? 1 : c;
-}
-
 // Window-closing or final step of one output, given the first slot's word s0 (int64 W0 while
 // widx == 1, FP64 bits from the second window's close on) and the active window Rw after this
 // push.  Final: returns RN(N 2^E).  Closing: returns the new s0 word.

@@ -67,6 +67,21 @@ __device__ __forceinline__ double round_i128(int64_t hi, uint64_t lo, int E) {
   return __longlong_as_double(neg ? (rb | (long long)0x8000000000000000ull) : rb);
 }
 
+// ---- integer windows (default epilogue) ----------------------------------------------------
+// The group sums enter R by Horner's rule in exact int64 arithmetic, c consecutive groups per
+// window, where c is the largest count whose worst case stays below 2^63:
+//   |G_g| <= (g - 1) * kpad * 127^2 (x2 for the complex combine) <= gmax < 2^L,
+//   |window| <= gmax (128^c - 1) / 127 < 2^(L + 7 c) / 127 <= 2^69 / 127   with
+//   c = (62 - L) / 7 + 1, i.e. L + 7 c <= 69: below 2^62 (128/127) < 2^63 - 2^57.
+// Two windows form the exact 128-bit N = W0 128^len1 + W1, rounded to FP64 once with integer
+// instructions only; a third and later window continue in FP64 (one rounding per window).
+__device__ __forceinline__ int window_len(int s, int64_t kpad, int cplx) {
+  const unsigned long long gmax = (unsigned long long)s * (unsigned long long)kpad * 16129ull * (cplx ? 2ull : 1ull);
+  const int L = 64 - __clzll((long long)gmax);
+  const int c = (62 - L) / 7 + 1;
+  return c < 1 ? 1 : c;
+}
+
 // (a 2^sh + b) as a 128-bit two's complement integer (hi, lo), 1 <= sh <= 63.
 __device__ __forceinline__ void i128_shl_add(long long a, int sh, long long b, long long& hi, unsigned long long& lo) {
   lo = (unsigned long long)a << sh;
@@ -111,13 +126,14 @@ __device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long 
   return __longlong_as_double(neg ? (r | (long long)0x8000000000000000ull) : r);
 }
 
-// RN(N 2^E) for N = W0 2^S + W1 (S = 7 wlen in [7, 56], |W0|, |W1| < 2^62; W0 = 0 for a single
-// window) without data-dependent branches, so the outputs of a chunk interleave.  With
-// q = W0 + floor(W1 / 2^S) and r = W1 mod 2^S, N = q 2^S + r (0 <= r < 2^S) and
-// |N| = qm 2^S + rm with qm = q, rm = r for q >= 0 and qm = -q - 1, rm = 2^S - r (r > 0) or
-// qm = -q, rm = 0 (r = 0) for q < 0.  The top 63 bits of |N| with a sticky bit below them are
-// converted with one correctly rounded conversion and the power of two goes into the exponent
-// field.  `ok` is false when the result is not a normal double (the caller takes final_val).
+// RN(N 2^E) for N = W0 2^S + W1 (S = 7 wlen in [7, 56], |W0|, |W1| < 2^63 - 2^57, which the
+// windows of window_len satisfy; W0 = 0 for a single window) without data-dependent branches,
+// so the outputs of a chunk interleave.  With q = W0 + floor(W1 / 2^S) and r = W1 mod 2^S,
+// N = q 2^S + r (0 <= r < 2^S) and |N| = qm 2^S + rm with qm = q, rm = r for q >= 0 and
+// qm = -q - 1, rm = 2^S - r (r > 0) or qm = -q, rm = 0 (r = 0) for q < 0.  The top 63 bits of
+// |N| with a sticky bit below them are converted with one correctly rounded conversion and the
+// power of two goes into the exponent field.  `ok` is false when the result is not a normal
+// double (the caller then takes final_val, which rounds the 128-bit N).
 __device__ __forceinline__ double rn_windows(long long W0, long long W1, int S, int E, bool& ok) {
   const long long q = W0 + (W1 >> S);
   const unsigned long long mask = (1ull << S) - 1ull;

@@ -39,6 +39,10 @@ int main() {
       long long hi; unsigned long long lo; int E;
       if (std::scanf("%lld %llu %d", &hi, &lo, &E) != 3) return 1;
       put(ozg::round_i128(hi, lo, E));
+    } else if (mode == 'l') {  // window length
+      int sw, cplx; long long kpad;
+      if (std::scanf("%d %lld %d", &sw, &kpad, &cplx) != 3) return 1;
+      std::printf("%d\n", ozg::window_len(sw, kpad, cplx));
     } else {            // two windows, as the default epilogue takes them
       long long W0, W1; int S, E;
       if (std::scanf("%lld %lld %d %d", &W0, &W1, &S, &E) != 4) return 1;
@@ -124,10 +128,12 @@ def test_round_i128_equals_exact_rounding(harness):
 def test_two_window_rounding_equals_exact_rounding(harness):
     g = random.Random(12)
     raw = [(0, 2 ** 55 + 1, 7, -1130), (1, -1, 56, -1074 - 56), (-1, 1, 7, -1080), (2 ** 61, 2 ** 61, 56, 900)]
+    wmax = 2 ** 69 // 127        # the largest window window_len admits (see the window test)
+    raw += [(wmax, wmax, 56, 900), (-wmax, -wmax, 7, -1100), (wmax, -wmax, 49, 0)]
     for _ in range(60000):
         S = 7 * g.randint(1, 8)
-        W0 = 0 if g.random() < 0.2 else g.randint(-(2 ** 62) + 1, 2 ** 62 - 1) >> g.randint(0, 61)
-        W1 = g.randint(-(2 ** 62) + 1, 2 ** 62 - 1) >> g.randint(0, 61)
+        W0 = 0 if g.random() < 0.2 else g.randint(-wmax, wmax) >> g.randint(0, 61)
+        W1 = g.randint(-wmax, wmax) >> g.randint(0, 61)
         if g.random() < 0.2:   # a tie or zeros in W1's low bits
             k = g.randint(1, 40)
             W1 = (W1 >> k << k) | ((1 << (k - 1)) if g.random() < 0.5 else 0)
@@ -136,3 +142,20 @@ def test_two_window_rounding_equals_exact_rounding(harness):
         raw.append((W0, W1, S, pick_exponent(g, p)))
     cases = [(W0 * 2 ** S + W1, E, W0, W1, S) for W0, W1, S, E in raw]
     check(harness, cases, lambda c: f"w {c[2]} {c[3]} {c[4]} {c[1]}\n")
+
+
+def test_window_length_keeps_every_window_in_int64(harness):
+    """window_len(s, kpad, cplx) is the closed form c = (62 - L) / 7 + 1 (L the bit length of
+    gmax = s kpad 127^2, doubled for complex), and the worst-case window, gmax (128^c - 1) / 127,
+    stays below 2^69 / 127 < 2^63 - 2^57 -- the range rn_windows assumes -- over s = 1..18 and
+    k padded to 64 (small k, then every 4099th multiple of 64 up to 2^26)."""
+    params = [(s, 64 * kb, c) for c in (0, 1) for s in range(1, 19)
+              for kb in sorted(set([1, 2, 3, 7, 8, 9, 16, 17] + list(range(1, 2 ** 20 + 1, 4099)) + [2 ** 20]))]
+    got = subprocess.run([harness], input="".join(f"l {s} {k} {c}\n" for s, k, c in params), capture_output=True,
+                         text=True, check=True).stdout.split()
+    assert len(got) == len(params)
+    for (s, kpad, cplx), w in zip(params, got):
+        gmax = s * kpad * 127 * 127 * (2 if cplx else 1)
+        c = max(1, (62 - gmax.bit_length()) // 7 + 1)
+        assert int(w) == c
+        assert gmax * (128 ** c - 1) // 127 <= 2 ** 69 // 127 < 2 ** 63 - 2 ** 57
