@@ -17,6 +17,11 @@ s = 3..10, error and TFLOP/s per s), the KKR-like ZGEMM (n = 3616, s = 4..10), t
 the grouped slice-product kernel, the CPU oracle on a bounded sample, and an end-to-end number
 with the whole batch copied host -> device and the results device -> host in every step.
 
+roofline.traffic is the per-launch DRAM bytes of the committed one-pass ncu summary under
+profiles/ when it was taken on the current kernel sources (sha256 of ozg_gemm.cu,
+ozg_device.cuh, ozg_internal.h and ozg_round.cuh), else null; a figure taken on other sources
+is reported as roofline.traffic_other_source with the hash it was taken on.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ozg|reference]
 
 Under torchrun every rank runs its own batch of the same distribution (independent problems,
