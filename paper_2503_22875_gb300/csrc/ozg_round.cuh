@@ -5,7 +5,8 @@
 // one correctly rounded u64 -> f64 conversion; results outside the normal range (subnormal,
 // zero or overflow) take round_edge, which rounds onto the grid of the smallest subnormal
 // directly, so that no second rounding follows the 53-bit one.  The functions use only integer
-// and conversion intrinsics, so the unit tests also compile them for the host.
+// operations, conversion intrinsics and exact ldexp scalings, so the unit tests also compile
+// them for the host.
 #pragma once
 #include <cstdint>
 
