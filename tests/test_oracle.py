@@ -251,6 +251,20 @@ def test_emu_rounding_ties_and_subnormals():
     assert C[0, 0] == np.inf
 
 
+def test_znaive_small_integers_exact_with_complex_alpha_beta():
+    """The plain complex GEMM on small Gaussian integers with complex alpha and beta: every
+    operation is exact in FP64, so the result equals the exact complex arithmetic."""
+    rng = np.random.default_rng(41)
+    A = rng.integers(-4, 5, (3, 5)) + 1j * rng.integers(-4, 5, (3, 5))
+    B = rng.integers(-4, 5, (5, 2)) + 1j * rng.integers(-4, 5, (5, 2))
+    C0 = rng.integers(-4, 5, (3, 2)) + 1j * rng.integers(-4, 5, (3, 2))
+    al, be = 2 - 3j, 0.5 + 1j
+    C = oracle.zgemm_naive(A, B, alpha=al, beta=be, C=C0)
+    want = [[al * sum(complex(A[i, l]) * complex(B[l, j]) for l in range(5)) + be * complex(C0[i, j])
+             for j in range(2)] for i in range(3)]
+    assert (C == np.array(want)).all()
+
+
 def test_emu_single_rounding_at_the_subnormal_and_overflow_edges():
     """One rounding of the exact sum, also where a 53-bit rounding followed by a second one onto
     the subnormal grid (or past the largest finite value) would differ (s = 18 keeps every term).

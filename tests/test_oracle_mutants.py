@@ -67,6 +67,26 @@ MUTANTS = [
     ("overflow saturates at the largest finite value", "if (top > 1023) return neg ? -INFINITY : INFINITY;",
      "if (top > 1023) return neg ? -1.7976931348623157e308 : 1.7976931348623157e308;"),
     ("a dropped dd error term in the complex reference", "        sr = dd_add(sr, two_prod(-ai, bi));\n", ""),
+    ("softmax denominator off", "for (int o = 0; o < SEL_OUT; ++o) p[o] = exp(z[o] - zm) / se;",
+     "for (int o = 0; o < SEL_OUT; ++o) p[o] = exp(z[o] - zm) / (se + 1e-3);"),
+    ("loss without the max shift", "loss += (log(se) + zm - z[y[b]]) / B;", "loss += (log(se) - z[y[b]]) / B;"),
+    ("layer-2 weight gradient with the wrong activation", "grad[O_W2 + o * SEL_H + j] += dh2[o] * h1[j];",
+     "grad[O_W2 + o * SEL_H + j] += dh2[o] * h2[j];"),
+    ("inference drops the layer-1 bias", "    float a = b1[o];\n", "    float a = 0.f;\n"),
+    ("inference without the layer-1 ReLU", "h1[o] = a > 0.f ? a : 0.f;", "h1[o] = a;"),
+    ("feature log2 k off by one", "out[2] = log2f((float)k);", "out[2] = log2f((float)(k + 1));"),
+    ("B histogram normalised by m k", "out[13 + b] = (float)(hist[1][b] / ((double)n * (double)k));",
+     "out[13 + b] = (float)(hist[1][b] / ((double)m * (double)k));"),
+    ("naive complex alpha sign", "ti = alpha[0] * si + alpha[1] * sr;", "ti = alpha[0] * si - alpha[1] * sr;"),
+    ("complex split writes Im digits into the Re row",
+     "digits_of(ldexp(im, -ex), s, &D[(2 * i + 1) * k + l], R2 * k);",
+     "digits_of(ldexp(im, -ex), s, &D[(2 * i) * k + l], R2 * k);"),
+    ("row maximum from the first entry only", "      double a = fabs(op_r(trans, X, ld, i, l));\n      if (a > amax) amax = a;",
+     "      double a = fabs(op_r(trans, X, ld, i, l));\n      if (l == 0) amax = a;"),
+    ("dd addition drops the high error", "  s.lo += t.hi;\n  s = quick_two_sum(s.hi, s.lo);", "  s = quick_two_sum(s.hi, s.lo);"),
+    ("3M real part P1 + P2", "double tr = p1 - p2;", "double tr = p1 + p2;"),
+    ("rounding gives up on long tails", "if (r > 255) { /* everything", "if (r > 60) { /* everything"),
+    ("negative group products not sign-extended", "uint64_t fill = v < 0 ? ~0ull : 0ull;", "uint64_t fill = 0ull;"),
 ]
 
 # mistakes planted in the Python half of the oracle (oracle/__init__.py)
@@ -83,6 +103,11 @@ PY_MUTANTS = [
      "scale = abs_product(A, B, transa, transb)"),
     ("3M bound without the third product's error", "im = e3 + e1 + e2 + u * (P3 + P1 + P2)",
      "im = e1 + e2 + u * (P3 + P1 + P2)"),
+    ("error metric without the beta C0 term", "        scale = scale + abs(beta) * np.abs(np.asarray(C0))\n", ""),
+    ("features with the operands' transposes swapped",
+     "_load().orc_features(_b(transa), _b(transb), m, n, k,", "_load().orc_features(_b(transb), _b(transa), m, n, k,"),
+    ("inference with the threshold of a different model", "float(model[\"thr\"]), int(model[\"s_lo\"]),",
+     "float(model[\"thr\"]) * 0.5, int(model[\"s_lo\"]),"),
 ]
 
 PIN_SUITES = ["tests/test_oracle.py", "tests/test_oracle_selector.py"]

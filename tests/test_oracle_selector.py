@@ -89,6 +89,35 @@ def test_mlp_select_closed_form_decision():
     assert oracle.mlp_select(model, np.zeros(24, np.float32), 6)[0] == 6  # capped
 
 
+def test_mlp_select_closed_form_through_all_layers():
+    """A network whose decision depends on every layer: W1 = 0 with b1[0] = 1 gives h1 = e_0;
+    W2[0][0] = 1 gives h2 = e_0 (ReLU keeps it); W3[4][0] = 5 gives z = 5 e_4, so
+    p_4 = e^5 / (e^5 + 10) and the other classes 1 / (e^5 + 10): the cumulative sum first reaches
+    0.9 at class 4 (s = 2 + 4).  The input (normalised by mean and inv_std) feeds a unit that
+    ReLU cuts off (W1[1][0] = -1 with x_0 = 3) and that also enters h2_0: without the ReLU,
+    h2_0 = 1 - 3 would vanish and the decision would fall to class 9."""
+    bf = lambda v: np.array([v], np.float32).view(np.uint32)[0] >> 16   # exact BF16 bits of v
+    W1 = np.zeros(64 * 24, np.uint16)
+    W1[1 * 24 + 0] = bf(-1.0)
+    b1 = np.zeros(64, np.float32)
+    b1[0] = 1.0
+    W2 = np.zeros(64 * 64, np.uint16)
+    W2[0 * 64 + 0] = bf(1.0)
+    W2[0 * 64 + 1] = bf(1.0)                        # h2_0 = h1_0 + h1_1 = 1 + relu(-3)
+    W3 = np.zeros(11 * 64, np.uint16)
+    W3[4 * 64 + 0] = bf(5.0)
+    model = dict(mean=np.full(24, -1.0, np.float32), inv_std=np.full(24, 1.5, np.float32), W1=W1, b1=b1,
+                 W2=W2, b2=np.zeros(64, np.float32), W3=W3, b3=np.zeros(11, np.float32),
+                 thr=0.9, s_lo=2, fallback=13)
+    feat = np.zeros(24, np.float32)
+    feat[0] = 1.0                                   # x_0 = (1 - (-1)) * 1.5 = 3
+    s, probs = oracle.mlp_select(model, feat, 12)
+    want = np.full(11, 1.0 / (math.exp(5) + 10))
+    want[4] = math.exp(5) / (math.exp(5) + 10)
+    np.testing.assert_allclose(probs, want, rtol=1e-5)
+    assert s == 2 + 4
+
+
 def test_features_closed_forms():
     A = np.array([[1.0, 2.0 ** -5, 2.0 ** -40, 0.0],
                   [3.0, 3.0, 3.0, 3.0]])
