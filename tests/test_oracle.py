@@ -457,6 +457,17 @@ def test_zemu_alpha_beta_single_rounding_directed():
     assert C[0, 0].real == 2.0 ** -60 + br and C[0, 0].imag == fma_exact(x, y, 1.0 * x) + bi
 
 
+def test_zemu_beta_single_rounding_directed():
+    """beta C_old in the fma order as well: Re = RN(beta_r c_r - RN(beta_i c_i)).  With
+    beta = (1 + 2^-30) + i, C_old = (1 + 2^-30) + i (1 + 2^-29) and a zero product, the exact
+    real part is 2^-60, which rounding beta_r c_r first would lose."""
+    x, y = 1.0 + 2.0 ** -30, 1.0 + 2.0 ** -29
+    C0 = np.array([[complex(x, y)]])
+    C = oracle.zgemm_emu(np.array([[0j]]), np.array([[1.0 + 0j]]), 4, beta=complex(x, 1.0), C=C0)
+    assert C[0, 0].real == 2.0 ** -60 == fma_exact(x, x, -(1.0 * y))
+    assert C[0, 0].imag == fma_exact(x, y, 1.0 * x)
+
+
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("C", "N"), ("N", "T"), ("N", "C"), ("C", "T")])
 def test_z3m_small_integers_exact_with_alpha_beta(ta, tb):
     """3M on small integers: every emulated product, difference and alpha/beta step is exact, so

@@ -87,6 +87,18 @@ MUTANTS = [
     ("3M real part P1 + P2", "double tr = p1 - p2;", "double tr = p1 + p2;"),
     ("rounding gives up on long tails", "if (r > 255) { /* everything", "if (r > 60) { /* everything"),
     ("negative group products not sign-extended", "uint64_t fill = v < 0 ? ~0ull : 0ull;", "uint64_t fill = 0ull;"),
+    ("256-bit addition drops carries", "    c >>= 64;\n", "    c = 0;\n"),
+    ("negation without the +1", "one.w[0] = 1;", "one.w[0] = 0;"),
+    ("group weights one bit too high", "i256_from_i64_shl(&t, G[((int64_t)gi * m + i) * n + j], 7 * (top - g));",
+     "i256_from_i64_shl(&t, G[((int64_t)gi * m + i) * n + j], 7 * (top - g) + 1);"),
+    ("complex beta in two roundings",
+     "        double br = fma(beta[0], c[0], -(beta[1] * c[1]));\n        double bi = fma(beta[0], c[1], beta[1] * c[0]);\n        re += br; im += bi;\n      }\n      c[0] = re; c[1] = im;\n    }\n  free(e);",
+     "        double br = beta[0] * c[0] - beta[1] * c[1];\n        double bi = fma(beta[0], c[1], beta[1] * c[0]);\n        re += br; im += bi;\n      }\n      c[0] = re; c[1] = im;\n    }\n  free(e);"),
+    ("output gradient not averaged over the batch", "dz[o] = (p[o] - (o == y[b] ? 1.0 : 0.0)) / B;",
+     "dz[o] = (p[o] - (o == y[b] ? 1.0 : 0.0));"),
+    ("BF16 bits widened one place short", "uint32_t u = (uint32_t)h << 16;", "uint32_t u = (uint32_t)h << 15;"),
+    ("zero entries counted in the first feature bin", "        int bin = 9;\n        if (v != 0) {",
+     "        int bin = 0;\n        if (v != 0) {"),
 ]
 
 # mistakes planted in the Python half of the oracle (oracle/__init__.py)
@@ -108,6 +120,12 @@ PY_MUTANTS = [
      "_load().orc_features(_b(transa), _b(transb), m, n, k,", "_load().orc_features(_b(transb), _b(transa), m, n, k,"),
     ("inference with the threshold of a different model", "float(model[\"thr\"]), int(model[\"s_lo\"]),",
      "float(model[\"thr\"]) * 0.5, int(model[\"s_lo\"]),"),
+    ("columns of op(B) split without the flip", "return split(X, s, \"T\" if trans in \"Nn\" else \"N\")",
+     "return split(X, s, trans)"),
+    ("3M operands of B taken with op(A)'s transpose",
+     "oA, oB = _op(np.asarray(A, dtype=np.complex128), transa), _op(np.asarray(B, dtype=np.complex128), transb)",
+     "oA, oB = _op(np.asarray(A, dtype=np.complex128), transa), _op(np.asarray(B, dtype=np.complex128), transa)"),
+    ("a priori bound for one slice more", "max(B.shape[0], 1), int(s), _ptr(out))", "max(B.shape[0], 1), int(s) + 1, _ptr(out))"),
 ]
 
 PIN_SUITES = ["tests/test_oracle.py", "tests/test_oracle_selector.py"]
