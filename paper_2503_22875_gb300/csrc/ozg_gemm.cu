@@ -58,7 +58,6 @@ static_assert(CHAIN_K * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
 // -- while one per stage (6 stages) hides more load latency (large s: bigger working sets).
 template <int BN_, int SUB_>
 struct Cfg {
-  static constexpr int BN = BN_;
   static constexpr int SUB = SUB_;
   static constexpr int SK = SUB * BK;
   static constexpr int SEG = CHAIN_K / SK;  // stages per chain
