@@ -281,8 +281,9 @@ int ozg_debug_zsplit(ozg_ctx* ctx, char trans, int64_t rows, int64_t k, const do
 
 /* Exact group products G_g = sum_{p+q=g} D^A_p (D^B_q)^T of the emulated DGEMM (the integer
  * slice products of Sec. 2.2), computed by the tensor-core kernel and exported as
- * int64[s][m][n] (row-major, group g = 2..s+1 at index g-2) in device memory G_out.  Requires
- * (s) * ceil(k / 64) * 64 * 127^2 < 2^31 so that each group is one integer accumulation.
+ * int64[s][m][n] (row-major, group g = 2..s+1 at index g-2) in device memory G_out.  The kernel
+ * folds a group's int32 sum out every 64 accumulation chains of 1024 products (65,536 products);
+ * the export adds those partial sums in int64, so it holds the exact G_g at any k.
  * Synchronous. */
 int ozg_debug_group_products(ozg_ctx* ctx, char transa, char transb, int64_t m, int64_t n, int64_t k,
                              const double* A, int64_t lda, const double* B, int64_t ldb, int slices,
@@ -300,26 +301,31 @@ int ozg_debug_wait(ozg_ctx* ctx, long long cycles);
 int ozg_debug_fail_allocs(ozg_ctx* ctx, int n);
 
 /* ---- emulated DGEMM without any device allocation ----
- * No counterpart in the paper.  For callers that must not call cudaMalloc: code running while
- * its stream is captured into a CUDA graph (allocation cannot be captured), an interposed
- * dgemm_ inside a host application that owns all device memory through its own pool or a
- * fixed budget, and latency-critical paths where cudaMalloc / cudaFree would synchronise the
- * device.  Same arithmetic, kernels and results as ozg_dgemm (transa, transb in N/T; slices
- * 1..18 or -1 for native FP64), but no context: the work is queued on `stream` (a cudaStream_t,
- * NULL = legacy default stream) and all scratch lives in one fixed device array of
- * OZG_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the library's device
- * code holds until the process exits.
- *   - The problem must fit the array: about 2 s (m + n) round8(k) + 12 (m + n) bytes plus at
- *     least one 256 KiB tile of FP64 partial sums (e.g. m = n = k = 1024, s = 8 fits; 2048 does
- *     not).  Larger problems return OZG_ERR_UNSUPPORTED before any work is queued.
- *   - The first call on each device resolves the array's device address (cudaGetSymbolAddress,
- *     with that device current); make that first call before any stream capture begins.
+ * No counterpart in the paper.  For callers that must not call cudaMalloc: an interposed dgemm_
+ * inside a host application that owns all device memory through its own pool or a fixed budget
+ * (an allocation behind its back can fail or break its accounting), and latency-critical paths
+ * where cudaMalloc / cudaFree would synchronise the device.  Same arithmetic, kernels and results
+ * as ozg_dgemm (transa, transb in N/T; slices 1..18 or -1 for native FP64), but no context: the
+ * work is queued on `stream` (a cudaStream_t, NULL = legacy default stream) and all scratch lives
+ * in one fixed device array of OZG_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that
+ * loads the library's device code holds until the process exits.
+ *   - The problem must fit the array: 2 s (m + n) round8(k) bytes of digit planes plus
+ *     12 (m + n) bytes of row data (each part rounded up to 256 bytes) plus at least one
+ *     OZG_NOALLOC_TILE_BYTES tile of partial sums (128 x 256 outputs x 16 bytes); with less room
+ *     than one tile per SM the kernel runs on fewer CTAs, each looping over several tiles (e.g.
+ *     m = n = k = 1024, s = 8 fits; 2048 does not).  Larger problems return OZG_ERR_UNSUPPORTED
+ *     before any work is queued.
+ *   - The first call on each device does the set-up: it resolves the array's device address
+ *     (cudaGetSymbolAddress, with that device current).  Make that first call before any stream
+ *     capture begins.  If the device's context is destroyed and created again (cudaDeviceReset),
+ *     the next call does the set-up again.
  *   - Every call reuses the same array; each call clears what must start at zero.  Calls whose
  *     work overlaps on the GPU (other streams, unordered host threads) race on the array.
  *   - Asynchronous; device-side wait time-outs are not reported by this entry point (C is then
  *     unspecified).  Inf/NaN inputs are handled as in ozg_dgemm (native FP64 on the GPU).
  * Returns 0, a BLAS argument error -i, OZG_ERR_UNSUPPORTED (too large) or OZG_ERR_CUDA. */
 #define OZG_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define OZG_NOALLOC_TILE_BYTES (128u * 256u * 16u)
 int ozg_dgemm_noalloc(char transa, char transb, int64_t m, int64_t n, int64_t k, double alpha,
                       const double* A, int64_t lda, const double* B, int64_t ldb, double beta, double* C,
                       int64_t ldc, int slices, void* stream);

@@ -765,10 +765,15 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
             }
           }
           if (Gdbg != nullptr) {
+            // a group longer than the int32 fold interval arrives in several pushes: the export
+            // sums them in int64 (each output is written by this thread only)
 #pragma unroll 1
             for (int c = 0; c < CPT; ++c) {
               const int64_t gc = gcol0 + c;
-              if (row_ok && gc < j.cols) Gdbg[((int64_t)(g - 2) * j.rows + grow) * j.cols + gc] = Gs[c];
+              if (row_ok && gc < j.cols) {
+                int64_t* gp = Gdbg + ((int64_t)(g - 2) * j.rows + grow) * j.cols + gc;
+                *gp = first_push ? (int64_t)Gs[c] : *gp + (int64_t)Gs[c];
+              }
             }
           } else if (exact_now) {
             // correctly rounded mode: exact 128-bit Horner sum, one rounding at the end

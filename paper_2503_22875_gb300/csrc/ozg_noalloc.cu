@@ -1,13 +1,13 @@
 // ozg_dgemm_noalloc: the emulated DGEMM for callers that cannot allocate device memory.
 //
-// Some callers of a BLAS-style GEMM are not allowed to call cudaMalloc: code that runs while
-// its stream is being captured into a CUDA graph (allocation is not a capturable operation),
-// code inside an interposed dgemm_ of a host application that already owns all device memory
-// through its own pool or a fixed budget, and latency-critical paths where cudaMalloc/cudaFree
-// would synchronise the whole device.  This entry point serves them: it takes the caller's
-// inputs and output and a stream, and keeps all of its scratch (digit planes, exponents, row
-// maxima, FP64 partial sums, flags) in one file-scope device array of fixed size, so it calls no
-// cudaMalloc, cudaFree or allocating library routine.
+// Some callers of a BLAS-style GEMM are not allowed to call cudaMalloc: code inside an
+// interposed dgemm_ of a host application that already owns all device memory through its own
+// pool or a fixed budget (an allocation behind its back can fail or break its accounting), and
+// latency-critical paths where cudaMalloc/cudaFree would synchronise the whole device.  This
+// entry point serves them: it takes the caller's inputs and output and a stream, and keeps all
+// of its scratch (digit planes, exponents, row maxima, per-CTA partial-sum tiles, flags) in one
+// file-scope device array of fixed size, so it calls no cudaMalloc, cudaFree or allocating
+// library routine.
 //
 // The array is part of this library's device image: every GPU that loads it holds
 // kNoAllocScratchBytes until the process exits.  All calls share the array and it keeps the
@@ -27,17 +27,40 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};  // the context the address was resolved in
 int g_scratch_sms[kMaxDevices] = {};
 std::mutex g_setup_mu;
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
-// First call on a device (that device current): resolve the device address of the array.
-// In host code the array's name is only a host-side stand-in, never a device address.
+// The calling thread's current context (CUcontext as void*), through the driver entry point the
+// runtime exposes; null when it cannot be queried.
+void* current_context() {
+  typedef CUresult (*GetCtxFn)(CUcontext*);
+  static GetCtxFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCtxFn>(p);
+    looked = true;
+  }
+  CUcontext c = nullptr;
+  if (fn == nullptr || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return static_cast<void*>(c);
+}
+
+// Set-up, once per device (that device current): resolve the device address of the array.  In
+// host code the array's name is only a host-side stand-in, never a device address.  The address
+// belongs to the device's context; if that context was destroyed and created anew (for example
+// by cudaDeviceReset in the host application), the set-up runs again in the new one.
 int device_scratch(int dev, void** addr, int* sms) {
   if (dev < 0 || dev >= kMaxDevices) return OZG_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
+  void* ctx = current_context();
+  if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
       cudaGetLastError();
@@ -49,6 +72,7 @@ int device_scratch(int dev, void** addr, int* sms) {
       return OZG_ERR_CUDA;
     }
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = current_context();  // the runtime call above made the context current
     g_scratch_sms[dev] = n;
   }
   *addr = g_scratch_addr[dev];

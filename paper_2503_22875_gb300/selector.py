@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import struct
 import time
 
@@ -31,6 +32,9 @@ N_CLASSES = 11
 N_IN, N_H = 24, 64
 PARAMS = N_H * N_IN + N_H + N_H * N_H + N_H + N_CLASSES * N_H + N_CLASSES
 TARGETS = (1e-10, 1e-14)
+DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+# the model the benchmark and the headline tests load
+DEFAULT_MODEL = os.path.join(DATA_DIR, "selector_v1.ozgsel")
 S_MEASURE = 16  # errors are measured up to s = 16; classes stop at s = 12
 
 

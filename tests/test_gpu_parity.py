@@ -113,6 +113,81 @@ def test_group_products_max_digits_chain_boundary(ozg, ctx):
     assert np.array_equal(G.cpu().numpy(), G_o)
 
 
+# The epilogue keeps each group's running sum in int32 and folds it into the int64 window
+# every 64 accumulation chains of 1024 products (65,536 products, real) or every 32 chains
+# (complex, where Re = P_rr - P_ii doubles the magnitude).  With every digit 127 and one sign,
+# the last group of s = 4 at these k holds more than 2^31 - 1 in total, so a missing or late fold
+# overflows.  v = 1 - 2^-28 has the digits 127, 127, 127, 127 at s = 4.
+FOLD_S = 4
+FOLD_V = 1.0 - 2.0 ** -28
+
+
+def fold_operands(m, n, k, mixed_rows=8, seed=7):
+    """All-127 digits of one sign, except `mixed_rows` rows of A that mix signs and spreads (so
+    that a fold is also checked on ordinary data)."""
+    A = np.full((m, k), FOLD_V)
+    A[:mixed_rows] = wide((mixed_rows, k), 2.0, seed, zeros=False)
+    B = np.full((k, n), FOLD_V)
+    return np.asfortranarray(A), np.asfortranarray(B)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N")])
+def test_group_products_cross_int32_fold(ozg, ctx, ta, tb):
+    m, n, k, s = 40, 33, 34000, FOLD_S
+    A, B = fold_operands(m, n, k)
+    A = np.asfortranarray(A.T) if ta == "T" else A
+    G = torch.empty((s, m, n), dtype=torch.int64, device="cuda")
+    ctx.debug_group_products(ta, tb, m, n, k, dev(ozg, A), A.shape[0], dev(ozg, B), k, s, G)
+    _, DA = oracle.split(A, s, ta)
+    _, DB = oracle.split_cols(B, s)
+    G_o = oracle.group_products(DA, DB)
+    assert G_o[s - 1].max() == s * k * 127 * 127 > 2 ** 31 - 1  # the last group needs the fold
+    assert s * k > 64 * 1024                                     # it spans more than 64 chains
+    assert np.array_equal(G.cpu().numpy(), G_o)
+
+
+def test_dgemm_cross_int32_fold_bit_exact(ozg, ctx):
+    """The same operands through the emulated DGEMM (one int64 window, so the oracle's definition
+    bit for bit), single call and grouped launch, both tile widths."""
+    m, n, k, s = 40, 33, 34000, FOLD_S
+    A, B = fold_operands(m, n, k)
+    assert windows(s, k) == 1
+    E = oracle.dgemm_emu(A, B, s)
+    dA, dB = dev(ozg, A), dev(ozg, B)
+    for variant in (0, 1):
+        ctx.set_tile_variant(variant)
+        try:
+            dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+            ctx.dgemm("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dC, m, s)
+            ctx.sync()
+            assert np.array_equal(host(ozg, dC, m, n), E), variant
+            dG = torch.zeros((n, m), dtype=torch.float64, device="cuda")
+            ctx.dgemm_grouped([("N", "N", m, n, k, 1.0, dA, m, dB, k, 0.0, dG, m)], [s])
+            ctx.sync()
+            assert np.array_equal(host(ozg, dG, m, n), E), variant
+        finally:
+            ctx.set_tile_variant(-1)
+
+
+@pytest.mark.parametrize("ta", ["N", "C"])
+def test_zgemm_cross_complex_int32_fold_bit_exact(ozg, ctx, ta):
+    """Complex: Re(A) = Im(A) = v and Re(B) = -Im(B) = v make Re = P_rr - P_ii twice the largest
+    real sub-product; at k = 17000 the last group of s = 4 holds 2 * 4 * k * 127^2 > 2^31 - 1, so
+    the 32-chain complex fold is needed.  Some rows mix signs and spreads."""
+    m, n, k, s = 24, 20, 17000, FOLD_S
+    A = np.full((m, k), FOLD_V * (1 + 1j))
+    A[:4] = wide((4, k), 2.0, 31, zeros=False) + 1j * wide((4, k), 2.0, 32, zeros=False)
+    B = np.asfortranarray(np.full((k, n), FOLD_V * (1 - 1j)))
+    assert windows(s, k, cplx=True) == 1
+    assert 2 * s * k * 127 * 127 > 2 ** 31 - 1
+    Aop = np.asfortranarray(A.conj().T) if ta == "C" else np.asfortranarray(A)
+    dC = torch.zeros((n, m), dtype=torch.complex128, device="cuda")
+    ctx.zgemm(ta, "N", m, n, k, 1.0, dev(ozg, Aop), Aop.shape[0], dev(ozg, B), k, 0.0, dC, m, s)
+    ctx.sync()
+    E = oracle.zgemm_emu(Aop, B, s, ta, "N")
+    assert np.array_equal(host(ozg, dC, m, n), E)
+
+
 # ----------------------------------------------------------------------------- emulated DGEMM
 def check_dgemm(C, A, B, s, ta, tb, alpha, beta, C0):
     E = oracle.dgemm_emu(A, B, s, ta, tb, alpha, beta, C0)
@@ -286,9 +361,9 @@ def test_native_zgemm_and_slices_minus_one(ozg, ctx):
 
 # ----------------------------------------------------------------------------- full size, sampled
 def test_full_size_dgemm_sampled(ozg, ctx):
-    """The 8192^3 wide-exponent DGEMM in the benchmark's launch configuration; sampled rows and
-    columns are checked against the oracle (per-row / per-column scales make the sampled block's
-    emulation identical to the full one's)."""
+    """The 8192^3 wide-exponent DGEMM in the benchmark's launch configuration (256-wide tiles with
+    deferred pushes); sampled rows and columns equal the oracle's emulation bit for bit (per-row
+    and per-column scales make the sampled block's emulation identical to the full one's)."""
     m = n = k = 8192
     s = 7
     A, B = workloads.wide_exponent_pair(m, n, k, 0.5, seed=2)
@@ -304,7 +379,8 @@ def test_full_size_dgemm_sampled(ozg, ctx):
     Cs = dC.cpu().numpy().T[np.ix_(rows, cols)]
     As = np.asfortranarray(A[rows])
     Bs = np.asfortranarray(B[:, cols])
-    check_dgemm(Cs, As, Bs, s, "N", "N", 1.0, 0.0, None)
+    assert windows(s, k) <= 2  # two exact windows: the oracle's definition bit for bit
+    assert np.array_equal(Cs, oracle.dgemm_emu(As, Bs, s))
 
 
 # ----------------------------------------------------------------------------- sampled dd check
