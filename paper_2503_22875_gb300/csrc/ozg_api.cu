@@ -90,11 +90,6 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   // learned count: row maxima -> features -> selection -> digits up to the selected count only
   int* s_dev = at<int>(c, oSd);  // [0] chosen s, [1] 1 unless the check forced a re-run
   if (autos) sa.plane_to = s_dev;
-  {
-    cudaError_t e = autos ? ozg::launch_rowmax(sa, st) : ozg::launch_split(sa, st);
-    if (e != cudaSuccess) delete split_scope;
-    OZG_CUDA(e);
-  }
   ozg::SplitArgs sb = sa;
   sb.X = B;
   sb.ld = ldb;
@@ -105,19 +100,33 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   sb.D = at<__half>(c, oDB);
   sb.maxbits = at<unsigned long long>(c, oMB);
   sb.exps = at<int32_t>(c, oF);
+  // learned count with rows that fit a fused statistics unit: row maxima and features in one read
+  const bool fused = autos && ozg::stats_fused(sa) && ozg::stats_fused(sb);
+  unsigned long long* hist = at<unsigned long long>(c, oHist);
   {
-    cudaError_t e = autos ? ozg::launch_rowmax(sb, st) : ozg::launch_split(sb, st);
+    cudaError_t e = cudaSuccess;
+    if (fused) {
+      e = cudaMemsetAsync(hist, 0, 2 * 10 * 8, st);
+      ozg::SplitArgs ha = sa, hb = sb;
+      ha.hist = hist;
+      hb.hist = hist + 10;
+      if (e == cudaSuccess) e = ozg::launch_stats_pair(ha, hb, st);
+    } else {
+      e = autos ? ozg::launch_rowmax(sa, st) : ozg::launch_split(sa, st);
+      if (e == cudaSuccess) e = autos ? ozg::launch_rowmax(sb, st) : ozg::launch_split(sb, st);
+    }
     delete split_scope;
     OZG_CUDA(e);
   }
   if (autos) {
     PhaseScope ps(c, OZG_PHASE_SELECT);
-    unsigned long long* hist = at<unsigned long long>(c, oHist);
-    OZG_CUDA(cudaMemsetAsync(hist, 0, 2 * 10 * 8, st));
-    ozg::SplitArgs ha = sa, hb = sb;
-    ha.hist = hist;
-    hb.hist = hist + 10;
-    OZG_CUDA(ozg::launch_gap_hist_pair(ha, hb, st));
+    if (!fused) {
+      OZG_CUDA(cudaMemsetAsync(hist, 0, 2 * 10 * 8, st));
+      ozg::SplitArgs ha = sa, hb = sb;
+      ha.hist = hist;
+      hb.hist = hist + 10;
+      OZG_CUDA(ozg::launch_gap_hist_pair(ha, hb, st));
+    }
     OZG_CUDA(ozg::launch_select_single(c->dsel, hist, hist + 10, m, n, k, (float)std::log10(c->target), s, s_dev,
                                        nullptr, nullptr, st));
   }

@@ -104,6 +104,200 @@ __global__ void __launch_bounds__(256) rowmax_batched(const SplitArgs* jobs, con
   }
 }
 
+// Fused statistics of whole rows (real jobs with k <= kStatsK).  A unit is a block of rows of
+// one job; its CTA reads them once and writes their maxima (from which the split's exponents
+// come) and, for a learned call, adds the rows' within-row exponent gaps e_i - E(x_il) to the
+// selector's 10-bin histogram (bins of 4, the last holding gaps >= 36 and zeros) -- the same
+// counts as the two-pass form (row maxima, then a histogram pass over the operand again).
+// The gap needs e_i, known only once the whole row has been read.  So each element's exponent is
+// kept in shared memory as one byte, E(chunk max) - E(x) capped at 255, beside the exponent of
+// its 16-element chunk's maximum; then gap = (e_i - E(chunk max)) + byte, exactly while it is
+// below 36 and >= 36 whenever the byte was capped.
+// Only the high 32-bit word of each element is loaded: it holds the exponent field.  When the
+// chunk's maximum has a biased exponent >= 36, the biased exponents give every byte exactly
+// (a subnormal or zero element then gets a byte >= 36, its true gap being larger), and that
+// maximum's high word has the same frexp exponent as the full value.  Chunks with a smaller
+// maximum (below 2^-987) reload their full words and take the exact path.
+// Thread layout: strided jobs (adjacent rows adjacent in memory) 16 rows x 16 column phases, so
+// a warp's load covers two 128-byte column segments; contiguous jobs 8 rows (a warp each) x 32
+// phases along k.  Thread (r, ph) takes elements l = ph + P i of its row, 16 loads in flight.
+constexpr int kStatsThreads = 256, kStatsChunk = 16;
+constexpr int kStatsChunks = kStatsK / 16 / kStatsChunk;  // chunks per thread at most (strided)
+constexpr size_t kStatsHistSmem = (size_t)kStatsChunks * kStatsThreads * (sizeof(short) + kStatsChunk);
+constexpr uint32_t kFastMaxHi = 36u << 20;  // high word of 2^(36 - 1023): smallest fast-path chunk maximum
+static_assert(kStatsK % (16 * kStatsChunk) == 0, "whole chunks");
+static_assert(kStatsK / 16 < 256, "per-thread bin counts fit 8-bit fields");
+
+extern __shared__ __align__(16) uint8_t stats_smem[];
+
+// Exact path of one chunk (its maximum is subnormal, zero or below 2^-987): the full words, the
+// frexp exponents, and the chunk's bytes when hist is set.  Returns the chunk maximum's bits.
+__device__ __noinline__ uint64_t stats_chunk_exact(const uint64_t* p, int64_t step, int i0, int n_t, bool hist,
+                                                   short* cmx, uint32_t* bytes, int c, int tid) {
+  uint64_t v[kStatsChunk];
+  uint64_t cm = 0;
+#pragma unroll
+  for (int q = 0; q < kStatsChunk; ++q) {
+    v[q] = i0 + q < n_t ? (__ldg(p + (int64_t)(i0 + q) * step) & kAbsMask) : 0ull;
+    cm = v[q] > cm ? v[q] : cm;
+  }
+  if (hist) {
+    const int ecm = exponent_from_maxbits(cm);
+    cmx[c * kStatsThreads + tid] = cm ? (short)ecm : (short)-32768;  // all-zero chunk: every gap huge
+#pragma unroll
+    for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
+      uint32_t word = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const uint64_t x = v[4 * w4 + b];
+        const int d = x ? min(255, ecm - exponent_from_maxbits(x)) : 255;
+        word |= (uint32_t)d << (8 * b);
+      }
+      bytes[(4 * c + w4) * kStatsThreads + tid] = word;
+    }
+  }
+  return cm;
+}
+
+template <bool HIST>
+__device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t rb) {
+  __shared__ unsigned long long red[8][16];
+  __shared__ unsigned int sh[10];
+  __shared__ uint4 onehot[11];  // bin b -> +1 in its 8-bit field of (bins 0-3, 4-7, 8-9); 10: nothing
+  short* cmx = reinterpret_cast<short*>(stats_smem);  // [chunk][tid]: frexp exponent of the chunk max
+  uint32_t* bytes = reinterpret_cast<uint32_t*>(stats_smem + kStatsChunks * kStatsThreads * sizeof(short));  // [word][tid]
+  const int tid = threadIdx.x;
+  if (HIST && tid < 10) sh[tid] = 0;
+  if (HIST && tid < 11) {
+    uint4 o = make_uint4(0, 0, 0, 0);
+    if (tid < 4) o.x = 1u << (8 * tid);
+    else if (tid < 8) o.y = 1u << (8 * (tid - 4));
+    else if (tid < 10) o.z = 1u << (8 * (tid - 8));
+    onehot[tid] = o;
+  }
+  const bool hist = HIST && J.hist != nullptr;
+  const bool strided = J.strided != 0;
+  const int P = strided ? 16 : 32;
+  const int r = strided ? (tid & 15) : (tid >> 5);
+  const int ph = strided ? (tid >> 4) : (tid & 31);
+  const int64_t row = rb * (kStatsThreads / P) + r;
+  const bool row_ok = row < J.rows;
+  const int n_t = (row_ok && ph < J.k) ? (int)((J.k - 1 - ph) / P + 1) : 0;
+  const int nch = (n_t + kStatsChunk - 1) / kStatsChunk;
+  const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
+  const uint64_t* p = strided ? X + row + (int64_t)ph * J.ld : X + row * J.ld + ph;
+  const int64_t step = strided ? (int64_t)P * J.ld : (int64_t)P;
+  const uint32_t* phi = reinterpret_cast<const uint32_t*>(p) + 1;  // high words (little-endian)
+  uint32_t nx[kStatsChunk];
+  auto load = [&](int c) {
+    const uint32_t* a = phi + 2 * (int64_t)(kStatsChunk * c) * step;
+#pragma unroll
+    for (int q = 0; q < kStatsChunk; ++q) {
+      nx[q] = kStatsChunk * c + q < n_t ? __ldg(a) : 0u;
+      a += 2 * step;
+    }
+  };
+  if (nch > 0) load(0);
+  uint64_t mx = 0;
+  for (int c = 0; c < nch; ++c) {
+    uint32_t h[kStatsChunk];
+#pragma unroll
+    for (int q = 0; q < kStatsChunk; ++q) h[q] = nx[q] & 0x7FFFFFFFu;
+    if (c + 1 < nch) load(c + 1);  // the next chunk's loads fly while this one is processed
+    uint32_t cmh = 0;
+#pragma unroll
+    for (int q = 0; q < kStatsChunk; ++q) cmh = max(cmh, h[q]);
+    if (cmh >= kFastMaxHi) {
+      const uint64_t cm = (uint64_t)cmh << 32;  // same frexp exponent as the chunk maximum
+      mx = cm > mx ? cm : mx;
+      if (hist) {
+        const int ebm = (int)(cmh >> 20);
+        cmx[c * kStatsThreads + tid] = (short)(ebm - 1022);
+#pragma unroll
+        for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
+          uint32_t word = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b) word |= (uint32_t)min(255, ebm - (int)(h[4 * w4 + b] >> 20)) << (8 * b);
+          bytes[(4 * c + w4) * kStatsThreads + tid] = word;
+        }
+      }
+    } else {
+      const uint64_t cm = stats_chunk_exact(p, step, kStatsChunk * c, n_t, hist, cmx, bytes, c, tid);
+      mx = cm > mx ? cm : mx;
+    }
+  }
+  // row maximum over the P threads of the row
+  const int lane = tid & 31, warp = tid >> 5;
+  uint64_t rmax;
+  if (strided) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, 16);  // the warp's two phases of the row
+    mx = o > mx ? o : mx;
+    if (lane < 16) red[warp][lane] = mx;
+    __syncthreads();
+    rmax = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) rmax = red[w][r] > rmax ? red[w][r] : rmax;
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t t = __shfl_xor_sync(0xffffffffu, mx, o);
+      mx = t > mx ? t : mx;
+    }
+    rmax = mx;
+    if (HIST) __syncthreads();  // the shared counters and table are ready before their use below
+  }
+  if (row_ok && ph == 0) {
+    J.maxbits[row] = rmax;  // the unit holds the whole row: no merge needed
+    if (rmax >= kInfBits) atomicExch(J.nonfinite, 1);
+  }
+  if (!HIST) return;
+  if (hist) {
+    // per byte: bin = min(9, min(255, delta + byte) >> 2), four at a time with byte-SIMD ops;
+    // bytes past the row's end count in the empty bin 10
+    const int e_row = exponent_from_maxbits(rmax);
+    uint32_t c0 = 0, c1 = 0, c2 = 0;  // 8-bit counts of bins 0-3, 4-7, 8-9
+    for (int c = 0; c < nch; ++c) {
+      const int delta = min(255, max(0, e_row - (int)cmx[c * kStatsThreads + tid]));
+      const uint32_t d4 = (uint32_t)delta * 0x01010101u;
+#pragma unroll
+      for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
+        const uint32_t g4 = __vaddus4(bytes[(4 * c + w4) * kStatsThreads + tid], d4);
+        const uint32_t b4 = __vminu4((g4 >> 2) & 0x3F3F3F3Fu, 0x09090909u);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = kStatsChunk * c + 4 * w4 + b;
+          const uint4 o = onehot[i < n_t ? (int)((b4 >> (8 * b)) & 255u) : 10];
+          c0 += o.x;
+          c1 += o.y;
+          c2 += o.z;
+        }
+      }
+    }
+#pragma unroll
+    for (int bin = 0; bin < 10; ++bin) {
+      const uint32_t w = bin < 4 ? c0 : (bin < 8 ? c1 : c2);
+      const unsigned s = __reduce_add_sync(0xffffffffu, (w >> (8 * (bin & 3))) & 255u);
+      if (lane == 0 && s) atomicAdd(&sh[bin], s);
+    }
+  }
+  __syncthreads();
+  if (hist && tid < 10 && sh[tid]) atomicAdd(&J.hist[tid], (unsigned long long)sh[tid]);
+}
+
+template <bool HIST>
+__global__ void __launch_bounds__(kStatsThreads, 3) stats_batched(const SplitArgs* jobs, const int2* units) {
+  const int2 ur = units[blockIdx.x];
+  const SplitArgs J = jobs[ur.x];
+  stats_unit<HIST>(J, ur.y);
+}
+
+// The two operands of one call, passed by value (single calls need no device job table).
+template <bool HIST>
+__global__ void __launch_bounds__(kStatsThreads, 3) stats_pair(const SplitArgs a, const SplitArgs b, int64_t units_a) {
+  const bool first = (int64_t)blockIdx.x < units_a;
+  stats_unit<HIST>(first ? a : b, first ? (int64_t)blockIdx.x : (int64_t)blockIdx.x - units_a);
+}
+
 // Digits (real jobs: the grouped GEMM is real).  A unit is 32 rows x kDgK k, walked as 64-wide
 // sub-tiles.  Thread t computes row t/8 and the 8 consecutive k at (t%8)*8 of a sub-tile;
 // strided jobs are staged (transposed) through shared memory so that global loads stay
@@ -294,6 +488,30 @@ cudaError_t launch_save_restore_batched(const RepairJob* jobs_dev, const int64_t
   return cudaGetLastError();
 }
 
+cudaError_t launch_stats_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, int hist,
+                                 cudaStream_t st) {
+  if (units <= 0) return cudaSuccess;
+  static_assert(kStatsHistSmem <= 48 * 1024, "within the default dynamic shared-memory limit");
+  if (hist) {
+    stats_batched<true><<<(unsigned)units, kStatsThreads, kStatsHistSmem, st>>>(jobs_dev, units_dev);
+  } else {
+    stats_batched<false><<<(unsigned)units, kStatsThreads, 0, st>>>(jobs_dev, units_dev);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_pair(const SplitArgs& a, const SplitArgs& b, cudaStream_t st) {
+  const int64_t ua = stats_units_of(a), ub = stats_units_of(b);
+  if (ua + ub <= 0) return cudaSuccess;
+  if (a.hist != nullptr || b.hist != nullptr)
+    stats_pair<true><<<(unsigned)(ua + ub), kStatsThreads, kStatsHistSmem, st>>>(a, b, ua);
+  else
+    stats_pair<false><<<(unsigned)(ua + ub), kStatsThreads, 0, st>>>(a, b, ua);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rowmax_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st) {
   if (units > 0) { rowmax_batched<<<(unsigned)units, 256, 0, st>>>(jobs_dev, units_dev); note_launch(); }
   return cudaGetLastError();
@@ -304,15 +522,6 @@ cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_d
   if (units <= 0) return cudaSuccess;
   const int64_t grid = grid_cap > 0 && units > grid_cap ? grid_cap : units;
   { digits_batched<<<(unsigned)grid, 256, 0, st>>>(jobs_dev, units_dev, units, run); note_launch(); }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t rowmax_units,
-                                 const int2* digit_units_dev, int64_t digit_units, cudaStream_t st) {
-  if (rowmax_units > 0) { rowmax_batched<<<(unsigned)rowmax_units, 256, 0, st>>>(jobs_dev, rowmax_units_dev); note_launch(); }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (digit_units > 0) { digits_batched<<<(unsigned)digit_units, 256, 0, st>>>(jobs_dev, digit_units_dev, digit_units, nullptr); note_launch(); }
   return cudaGetLastError();
 }
 

@@ -21,10 +21,10 @@ struct GroupPlan {
   uint64_t key = 0, epoch = 0;
   int ncalls = 0, nsamp = 0, variant = 0, grid = 0, njobs = 0, ntiles = 0;
   long long nkernels = 0;  // kernels one replay of the captured graph launches
-  int64_t rowmax_units = 0, digit_units = 0;
+  int64_t rowmax_units = 0, digit_units = 0, stats_units = 0;
   cudaGraphExec_t exec = nullptr;
   size_t oFlags = 0, flags_bytes = 0, oMax = 0, max_bytes = 0;
-  size_t oJobs = 0, oRmTab = 0, oDgTab = 0, oCalls = 0, oTiles = 0, oNative = 0, oFlagPtrs = 0;
+  size_t oJobs = 0, oRmTab = 0, oDgTab = 0, oStTab = 0, oCalls = 0, oTiles = 0, oNative = 0, oFlagPtrs = 0;
   size_t oNList = 0, oNPre = 0, oNTot = 0, oChecks = 0, oErrs = 0, oCold = 0, oR = 0;
   std::vector<int> s_used;
   // automatic (selector) calls
@@ -86,14 +86,18 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
   // [0], [1]: tile counters of the main and the re-run launch; [2]: "some call is re-run"
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oCounter), 0, sizeof(int) * 3, st));
+  // row maxima (and, for learned calls, the selector's features in the same read): jobs whose
+  // whole rows fit a fused statistics unit take one pass; longer ones the two-pass units
+  if (P.any_auto) OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
+  OZG_CUDA(launch_stats_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oStTab), P.stats_units, P.any_auto, st));
+  OZG_CUDA(launch_rowmax_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units, st));
   if (!P.any_auto) {
-    OZG_CUDA(launch_split_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units,
-                                  gat<int2>(c, P.oDgTab), P.digit_units, st));
+    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, nullptr, 0,
+                                   st));
   } else {
-    // row maxima -> features -> selection -> digits up to each call's selected count
-    OZG_CUDA(launch_rowmax_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units, st));
-    OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
-    OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units, st));
+    // features -> selection -> digits up to each call's selected count
+    if (P.rowmax_units > 0)
+      OZG_CUDA(launch_gap_hist_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oRmTab), P.rowmax_units, st));
     OZG_CUDA(launch_select_batched(c->dsel, gat<SelectJob>(c, P.oSel), P.ncalls, (float)std::log10(c->target), st));
     OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs), gat<int2>(c, P.oDgTab), P.digit_units, nullptr, 0,
                                    st));
@@ -202,8 +206,9 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   }
   P->njobs = (int)(2 * count);
   P->oJobs = cv.take(sizeof(SplitArgs) * 2 * count);
-  // work-unit tables of the batched split (job j = 2i for A, 2i + 1 for B of call i)
-  std::vector<int2> rmtab, dgtab;
+  // work-unit tables of the batched split (job j = 2i for A, 2i + 1 for B of call i): fused
+  // statistics units for jobs whose rows fit one, two-pass row-maximum units for the others
+  std::vector<int2> rmtab, dgtab, sttab;
   for (int64_t i = 0; i < count; ++i)
     for (int side = 0; side < 2; ++side) {
       SplitArgs x;
@@ -211,11 +216,16 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
       x.k = d[i].k;
       x.strided = side ? (TB[i] == 'T') : (TA[i] == 'N');
       const int job = (int)(2 * i + side);
-      for (int64_t u = 0, nu = rowmax_units_of(x); u < nu; ++u) rmtab.push_back(make_int2(job, (int)u));
+      if (stats_fused(x)) {
+        for (int64_t u = 0, nu = stats_units_of(x); u < nu; ++u) sttab.push_back(make_int2(job, (int)u));
+      } else {
+        for (int64_t u = 0, nu = rowmax_units_of(x); u < nu; ++u) rmtab.push_back(make_int2(job, (int)u));
+      }
       for (int64_t u = 0, nu = digit_units_of(x); u < nu; ++u) dgtab.push_back(make_int2(job, (int)u));
     }
   P->oRmTab = cv.take(sizeof(int2) * std::max<size_t>(rmtab.size(), 1));
   P->oDgTab = cv.take(sizeof(int2) * std::max<size_t>(dgtab.size(), 1));
+  P->oStTab = cv.take(sizeof(int2) * std::max<size_t>(sttab.size(), 1));
   P->oCalls = cv.take(sizeof(GroupCall) * count + 64);
   P->oTiles = cv.take(sizeof(GroupTile) * tiles.size());
   P->oNative = cv.take(sizeof(NativeArgs) * count);
@@ -393,6 +403,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   }
   P->rowmax_units = (int64_t)rmtab.size();
   P->digit_units = (int64_t)dgtab.size();
+  P->stats_units = (int64_t)sttab.size();
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs), jobs.data(), sizeof(SplitArgs) * jobs.size(), cudaMemcpyHostToDevice, st));
   std::vector<SplitArgs> jobs2;
@@ -415,6 +426,9 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
                              st));
   if (!dgtab.empty())
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oDgTab), dgtab.data(), sizeof(int2) * dgtab.size(), cudaMemcpyHostToDevice,
+                             st));
+  if (!sttab.empty())
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oStTab), sttab.data(), sizeof(int2) * sttab.size(), cudaMemcpyHostToDevice,
                              st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oCalls), calls.data(), sizeof(GroupCall) * calls.size(), cudaMemcpyHostToDevice, st));
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oTiles), tiles.data(), sizeof(GroupTile) * tiles.size(), cudaMemcpyHostToDevice, st));

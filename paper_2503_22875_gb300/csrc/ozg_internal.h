@@ -167,16 +167,26 @@ cudaError_t launch_check_batched_post(const CheckArgs* calls_dev, int ncalls, in
 // job or 8 rows x kRmContigK k of a contiguous one; digit (and feature) units are 32 rows x
 // kDgK k, processed as 64-wide sub-tiles.
 constexpr int kRmStridedK = 128, kRmContigK = 1024, kDgK = 64;
+// Fused statistics units hold whole rows of real jobs with k <= kStatsK: 16 rows of a strided job,
+// 8 rows of a contiguous one.  Longer (or complex) jobs take the two-pass row-maximum units.
+constexpr int64_t kStatsK = 2048;
+inline bool stats_fused(const SplitArgs& x) { return !x.cplx && x.k >= 1 && x.k <= kStatsK; }
+inline int64_t stats_units_of(const SplitArgs& x) { return x.strided ? (x.rows + 15) / 16 : (x.rows + 7) / 8; }
 inline int64_t rowmax_units_of(const SplitArgs& x) {
   return x.strided ? ((x.rows + 31) / 32) * ((x.k + kRmStridedK - 1) / kRmStridedK)
                    : ((x.rows + 7) / 8) * ((x.k + kRmContigK - 1) / kRmContigK);
 }
 inline int64_t digit_units_of(const SplitArgs& x) { return ((x.rows + 31) / 32) * ((x.k + kDgK - 1) / kDgK); }
-cudaError_t launch_split_batched(const SplitArgs* jobs_dev, const int2* rowmax_units_dev, int64_t rowmax_units,
-                                 const int2* digit_units_dev, int64_t digit_units, cudaStream_t st);
 // the two passes separately (row maxima; digits) for batches whose slice counts are chosen
 // between them
 cudaError_t launch_rowmax_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, cudaStream_t st);
+// fused statistics over stats units (job, row block): row maxima written directly (no merge) and,
+// with hist != 0, the gap histograms of the jobs that have one, in the same read
+cudaError_t launch_stats_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, int hist,
+                                 cudaStream_t st);
+// the same for the two operands of one call (both must satisfy stats_fused); hist when either
+// operand's hist is set
+cudaError_t launch_stats_pair(const SplitArgs& a, const SplitArgs& b, cudaStream_t st);
 // run: if non-null and *run == 0 the launch does nothing; grid_cap > 0 bounds the grid (grid-stride)
 cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, const int* run,
                                   int grid_cap, cudaStream_t st);

@@ -488,13 +488,19 @@ extern "C" int ozg_selector_features(ozg_ctx* c, char transa, char transb, int64
   sb.D = at<__half>(c, oDB);
   sb.maxbits = at<unsigned long long>(c, oMB);
   sb.exps = at<int32_t>(c, oF);
-  OZG_CUDA(ozg::launch_split(sa, st));
-  OZG_CUDA(ozg::launch_split(sb, st));
   unsigned long long* hist = at<unsigned long long>(c, oH);
   OZG_CUDA(cudaMemsetAsync(hist, 0, 2 * 10 * 8, st));
-  sa.hist = hist;
-  sb.hist = hist + 10;
-  OZG_CUDA(ozg::launch_gap_hist_pair(sa, sb, st));
+  if (ozg::stats_fused(sa) && ozg::stats_fused(sb)) {  // row maxima and features in one read
+    sa.hist = hist;
+    sb.hist = hist + 10;
+    OZG_CUDA(ozg::launch_stats_pair(sa, sb, st));
+  } else {
+    OZG_CUDA(ozg::launch_rowmax(sa, st));
+    OZG_CUDA(ozg::launch_rowmax(sb, st));
+    sa.hist = hist;
+    sb.hist = hist + 10;
+    OZG_CUDA(ozg::launch_gap_hist_pair(sa, sb, st));
+  }
   const bool model = c->sel_s_hi > 0;
   OZG_CUDA(ozg::launch_select_single(model ? c->dsel : nullptr, hist, hist + 10, m, n, k,
                                      (float)std::log10(c->target), std::max(c->sel_s_hi, c->fallback_slices),

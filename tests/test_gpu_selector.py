@@ -42,6 +42,37 @@ def test_features_match_oracle(ozg, ta, tb, phi):
     ctx.close()
 
 
+@pytest.mark.parametrize("ta,tb,m,n,k", [("N", "N", 1, 1, 1), ("N", "N", 17, 9, 2048), ("T", "T", 33, 65, 2049),
+                                         ("N", "T", 200, 3, 17), ("T", "N", 16, 8, 1500)])
+def test_features_edges_match_oracle(ozg, ta, tb, m, n, k):
+    """Rows of k <= 2048 take the fused statistics kernel (row maxima and gap histogram in one
+    read, whole rows per CTA), longer rows the two-pass kernels: ragged row blocks, an all-zero
+    row, runs of zeros longer than a 16-element chunk, subnormal entries, a row scaled below
+    2^-987 (whose chunks take the kernel's exact path) and gaps across the 36-exponent edge all
+    give the oracle's histogram counts exactly."""
+    g = workloads.rng(m * 7 + n * 3 + k)
+    opA = workloads.wide_exponent((m, k), 4.0, g)
+    opB = workloads.wide_exponent((k, n), 4.0, g)
+    if m > 2:
+        opA[1, :] = 0.0
+        opA[2, : min(k, 40)] = 0.0
+        opA[2, -1] = 2.0 ** -1070
+        opA[2, 0] = 3.0
+        opA[0, : min(k, 5)] = [2.0 ** -e for e in (0, 33, 35, 36, 37)][: min(k, 5)]
+    if m > 3:
+        opA[3, :] *= 2.0 ** -1000  # maxima below 2^-987 and subnormal entries: the exact path
+    if k > 3:
+        opB[:3, 0] = [5e-324, 2.0 ** -1022, 1.0]
+    A = np.asfortranarray(opA if ta == "N" else opA.T)
+    B = np.asfortranarray(opB if tb == "N" else opB.T)
+    ctx = ozg.Context()
+    f = torch.zeros(24, dtype=torch.float32, device="cuda")
+    ctx.selector_features(ta, tb, m, n, k, ozg.to_device(A), A.shape[0], ozg.to_device(B), B.shape[0], f)
+    o = oracle.features(A, B, 1e-12, ta, tb)
+    np.testing.assert_array_equal(f.cpu().numpy()[3:23], o[3:23])
+    ctx.close()
+
+
 def test_gradients_match_oracle(ozg):
     r = np.random.default_rng(410)
     theta = (r.normal(0, 0.2, selector.PARAMS)).astype(np.float32)
