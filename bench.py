@@ -54,7 +54,9 @@ BATCH_SEED = 4
 CHECK_SAMPLES = 64
 FIXED_SWEEP = (7, 9, 10, 11, 12)
 SINGLE_PHIS = (0.5, 2.0, 4.0)
-SELECTOR_MODEL = os.path.join(ROOT, "paper_2503_22875_gb300", "data", "selector_v1.ozgsel")
+SELECTOR_MODEL = ""                 # set from --selector in main()
+LABEL_SWEEP = tuple(range(5, 14))   # fixed counts whose sampled check labels each call's minimal s
+ESCALATED_FIXED = (8, 9, 10)        # fixed counts run through the learned pipeline (same check, escalation)
 
 
 def parse():
@@ -77,7 +79,12 @@ def parse():
     ap.add_argument("--e2e-parts", type=int, default=E2E_PARTS, help="sub-batches of the pipelined end-to-end number")
     ap.add_argument("--shim-size", type=int, default=8192, help="n of the shim's n^3 DGEMM")
     ap.add_argument("--no-regions", action="store_true", help="skip the region-adaptive slice-count section")
-    return ap.parse_args()
+    ap.add_argument("--selector", default="", help="selector model file (default: the package's model)")
+    args = ap.parse_args()
+    if not args.selector:
+        from paper_2503_22875_gb300 import selector
+        args.selector = selector.DEFAULT_MODEL
+    return args
 
 
 def dist_env():
@@ -319,10 +326,68 @@ def tensor_flops(batch, slices):
 
 
 # ------------------------------------------------------------------------------------ comparisons
-def compare_section(ozg, torch, batch, calls, flops, st, steps):
-    """Fixed-slice baselines and the native FP64 kernel on the same batch."""
+def pass_products(reps, fallback):
+    """Slice products of every pass each learned call ran: the selected count, then each re-run."""
+    from paper_2503_22875_gb300 import selector
+    return [sum(x * (x + 1) / 2 for x in selector.escalation_passes(r.selected, r.repaired, fallback)) for r in reps]
+
+
+def escalated_policy(ozg, torch, calls, flops, st, steps, model_path, work):
+    """A learned-pipeline policy on the batch: CUDA-event time per step and what the check did."""
+    from paper_2503_22875_gb300 import selector
+    n = len(calls)
+    ctx = ozg.Context(stream=st)
+    ctx.load_selector(model_path)
+    ctx.set_target_error(TARGET_ERR)
+    ctx.set_check_samples(CHECK_SAMPLES)
+    ms = timed(torch, st, lambda: ctx.dgemm_grouped(calls, [0] * n), max(1, min(steps, 5)))
+    with torch.cuda.stream(st):
+        reps = ctx.dgemm_grouped(calls, [0] * n, report=True)
+    ctx.close()
+    fb = selector.read_model(model_path)["fallback"]
+    prods = pass_products(reps, fb)
+    out = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12, **report_stats(reps),
+           "reruns_1": int(sum(r.repaired == 1 for r in reps)), "reruns_2": int(sum(r.repaired >= 2 for r in reps)),
+           "tensor_products_work": float(np.dot(prods, work))}
+    return out, reps
+
+
+def compare_section(ozg, torch, batch, calls, flops, st, steps, learned_reps):
+    """Fixed-slice baselines and the native FP64 kernel on the same batch; per-call minimal counts
+    from the sampled check at fixed counts; fixed counts through the learned pipeline."""
+    from paper_2503_22875_gb300 import selector
     out = {}
     n = len(calls)
+    work = np.array([float(c.m) * c.n * c.k for c in batch.calls])
+    # per-call labels: the smallest fixed count whose 64-sample check meets the target
+    ctx = ozg.Context(stream=st)
+    ctx.set_check_samples(CHECK_SAMPLES)
+    smin = np.full(n, LABEL_SWEEP[-1] + 1)
+    for s in reversed(LABEL_SWEEP):
+        with torch.cuda.stream(st):
+            reps = ctx.dgemm_grouped(calls, [s] * n, report=True)
+        ok = np.array([r.est_err <= TARGET_ERR for r in reps])
+        smin[ok] = s
+    ctx.close()
+    out["minimal_s_hist"] = {int(v): int(c) for v, c in zip(*np.unique(smin, return_counts=True))}
+    fb = selector.read_model(SELECTOR_MODEL)["fallback"]
+    perfect = float(np.dot(work, np.minimum(smin, fb) * (np.minimum(smin, fb) + 1) / 2))
+    learned_work = float(np.dot(pass_products(learned_reps, fb), work))
+    sel_eval = selector.selector_eval([r.selected for r in learned_reps], smin, work)
+    sel_eval["labels"] = (f"per call, the smallest s in {LABEL_SWEEP[0]}..{LABEL_SWEEP[-1]} whose {CHECK_SAMPLES}-sample "
+                          f"GPU check (exact reference) meets {TARGET_ERR:g} in a fixed-count grouped run")
+    sel_eval["tensor_work_vs_perfect_choice"] = learned_work / perfect
+    esc = {}
+    with tempfile.TemporaryDirectory() as tmp:
+        for s in ESCALATED_FIXED + (fb,):
+            path = os.path.join(tmp, f"const{s}.ozgsel")
+            selector.write_constant_model(path, s, fb)
+            res, _ = escalated_policy(ozg, torch, calls, flops, st, steps, path, work)
+            res["tensor_work_vs_perfect_choice"] = res.pop("tensor_products_work") / perfect
+            esc[s] = res
+    out["fixed_escalated"] = esc
+    out["fixed_escalated_note"] = (f"fixed s through the learned pipeline (the same feature pass, {CHECK_SAMPLES}-sample "
+                                   f"check and escalation: a rejected call re-runs at min(s + 2, {fb}), then at {fb})")
     ctx = ozg.Context(stream=st)
     ms = timed(torch, st, lambda: [ctx.dgemm(*c, 7) for c in calls], max(1, min(steps, 2)))
     ctx.set_check_samples(CHECK_SAMPLES)
@@ -354,7 +419,7 @@ def compare_section(ozg, torch, batch, calls, flops, st, steps):
     ms = timed(torch, st, lambda: [ctx.native_dgemm(*c) for c in calls], 1, warm=0)
     out["native_fp64_one_at_a_time"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
     ctx.close()
-    return out
+    return out, sel_eval
 
 
 def parse_list(spec, cast):
@@ -723,10 +788,13 @@ def run_gpu(args):
     used = [r.slices_used for r in reps]
     stats["selected_hist"] = {int(v): int(c) for v, c in zip(*np.unique([r.selected for r in reps],
                                                                            return_counts=True))}
-    stats["repaired"] = int(sum(r.repaired for r in reps))
-    # tensor work of the step: every call at its selected count, plus the fallback re-runs
-    tflops_step = tensor_flops(batch, [r.selected for r in reps])
-    tflops_step += tensor_flops(batch, [u if r.repaired else 0 for r, u in zip(reps, used)])
+    stats["repaired"] = int(sum(r.repaired > 0 for r in reps))
+    stats["reruns"] = {"at_s_plus_2": int(sum(r.repaired == 1 for r in reps)),
+                       "then_at_fallback": int(sum(r.repaired >= 2 for r in reps))}
+    # tensor work of the step: every call at its selected count, plus the escalated re-runs
+    from paper_2503_22875_gb300 import selector
+    fallback = selector.read_model(SELECTOR_MODEL)["fallback"]
+    tflops_step = sum(p * 2.0 * c.m * c.n * c.k for p, c in zip(pass_products(reps, fallback), batch.calls))
 
     # the slice-product kernel's own duration: the same step without the graph, CUDA events
     # around each grouped GEMM launch on the launch stream
@@ -748,7 +816,7 @@ def run_gpu(args):
     # algorithmic DRAM bytes of the launch: each selected digit plane read once, C written once
     roof["algorithmic_bytes"] = sum(2.0 * r.selected * (c.m + c.n) * c.k + 8.0 * c.m * c.n
                                     for c, r in zip(batch.calls, reps))
-    roof["note"] = ("tensor flops = sum over calls of s(s+1)/2 * 2mnk at the selected s (plus fallback re-runs); "
+    roof["note"] = ("tensor flops = sum over calls of s(s+1)/2 * 2mnk at the selected s (plus escalated re-runs); "
                     "launch_ms = the step's grouped GEMM launches, CUDA events, without the graph")
 
     # end to end through the C ABI: every step copies the whole batch host -> device, runs it and
@@ -767,13 +835,22 @@ def run_gpu(args):
         return 0
 
     compare = None
+    sel_eval = None
     if not args.no_compare:
-        compare = compare_section(ozg, torch, batch, calls, flops, st, args.steps)
+        compare, sel_eval = compare_section(ozg, torch, batch, calls, flops, st, args.steps, reps)
         learned = value / world
         compare["learned_vs_fixed_s7_one_at_a_time"] = learned / compare["fixed_s7_one_at_a_time"]["tflops"]
         best = compare["smallest_fixed_s_meeting_target_on_all_calls"]
         if best:
             compare["learned_vs_smallest_sufficient_fixed_grouped"] = learned / compare["fixed_grouped"][best]["tflops"]
+        esc = compare["fixed_escalated"]
+        ok = {s: v for s, v in esc.items() if v["frac_le_target"] >= 1.0}
+        if ok:
+            s_best = max(ok, key=lambda s: ok[s]["tflops"])
+            compare["best_fixed_escalated"] = s_best
+            compare["learned_vs_best_fixed_escalated"] = learned / ok[s_best]["tflops"]
+        fbk = max(esc)
+        compare["learned_vs_fixed_fallback"] = learned / esc[fbk]["tflops"]
         compare["learned_vs_native_fp64"] = learned / compare["native_fp64_one_at_a_time"]["tflops"]
     del batch, calls
     torch.cuda.empty_cache()
@@ -797,6 +874,7 @@ def run_gpu(args):
                    "selector": os.path.relpath(SELECTOR_MODEL, ROOT),
                    "l2": f"inputs larger than L2 ({in_bytes / 1e9:.1f} GB of A and B per batch), no flush"},
         "accuracy": stats,
+        "selector_eval": sel_eval,
         "grouped_ms_without_graph": grouped_ms_nograph,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -816,7 +894,9 @@ def run_gpu(args):
 
 
 def main():
+    global SELECTOR_MODEL
     args = parse()
+    SELECTOR_MODEL = args.selector
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -64,8 +64,10 @@ typedef struct ozg_report {
   double est_err;         /* max over the samples of |C - C_dd| / (|alpha||A||B| + |beta||C_old|);
                              NaN when not checked or routed to native FP64 */
   int selected;           /* slice count the learned selector chose (0: the count was fixed) */
-  int repaired;           /* 1: the check rejected the selected count and the call was re-run at
-                             the fallback count (slices_used then holds the fallback) */
+  int repaired;           /* re-runs the check forced on a learned call: 0 none; in a grouped call
+                             1 = re-run at min(selected + 2, fallback), 2 = re-run again at the
+                             fallback count; in a single call 1 = re-run at the fallback count
+                             (slices_used holds the count of the last run) */
   double max_real;        /* complex calls: max over the samples of |Re C - Re C_dd| / |Re C_dd| and */
   double max_imag;        /* the same for Im: the per-part relative error of the paper's MuST study
                              (Sec. 3.2); NaN for real calls or when not checked */
@@ -100,8 +102,10 @@ int ozg_set_check_samples(ozg_ctx* ctx, int samples);
  * accumulation) on the GPU and uses the smallest s in 2..12 whose cumulative predicted
  * probability reaches the model's threshold -- all on the device, no host round trip.  The
  * sampled double-double check is always on for such calls (>= 64 samples); if its estimate
- * exceeds the target the call is recomputed at the fallback count (ozg_set_fallback_slices),
- * again on the device.  Without a model, slices = 0 means the fallback count. */
+ * exceeds the target the call is recomputed, again on the device: a call of a grouped launch at
+ * min(s + 2, fallback) and, if the check rejects that too, at the fallback count
+ * (ozg_set_fallback_slices; a count at or above the fallback is not recomputed); a single call
+ * at the fallback count.  Without a model, slices = 0 means the fallback count. */
 
 /* Load a selector model file (format in the library's selector source); also sets the
  * context's fallback count to the model's conservative count.  Returns 0 or OZG_ERR_INVALID

@@ -451,9 +451,16 @@ __global__ void repair_prep_batched(const RepairJob* jobs, int njobs, double tar
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= njobs) return;
   const RepairJob J = jobs[i];
+  const bool ran = J.ran == nullptr || *J.ran == 0;
   const double e = J.err ? *J.err : 0.0;
-  const bool bad = J.auto_mode && !(J.nonfinite && *J.nonfinite) && !(e <= target);
-  *J.skip2 = bad ? 0 : 1;
+  const int sc = J.s_cur ? *J.s_cur : 0;
+  const bool bad = J.auto_mode && ran && !(J.nonfinite && *J.nonfinite) && !(e <= target) && sc < J.s_fb;
+  if (bad) {
+    const int sn = J.s_add > 0 ? min(sc + J.s_add, J.s_fb) : J.s_fb;
+    if (J.s_next) *J.s_next = sn;
+    if (J.s_copy) *J.s_copy = sn;
+  }
+  *J.skip_next = bad ? 0 : 1;
   if (bad && any_rerun != nullptr) atomicOr(any_rerun, 1);
 }
 
@@ -462,7 +469,7 @@ __global__ void save_restore_batched(const RepairJob* jobs, const int64_t* prefi
   const int64_t unit = blockIdx.x;
   const int jb = find_job(prefix, njobs, unit);
   const RepairJob J = jobs[jb];
-  if (restore && *J.skip2) return;
+  if (restore && *J.skip_next) return;
   const int64_t e = (unit - prefix[jb]) * 256 + threadIdx.x;
   if (e >= J.m * J.n) return;
   const int64_t i = e % J.m, j = e / J.m;

@@ -31,7 +31,9 @@ struct GroupPlan {
   int any_auto = 0, s_fb = 0;
   int64_t save_units = 0;
   size_t oHist = 0, hist_bytes = 0, oSel = 0, oSused = 0, oRep = 0, oSavePre = 0, oSaved = 0;
+  // escalation stages 2 (min(s + 2, fallback)) and 3 (the fallback) of rejected learned calls
   size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0, oJobs2 = 0, oCounter = 0;
+  size_t oCalls3 = 0, oChecks3 = 0, oErrs3 = 0, oSkip3 = 0, oJobs3 = 0, oRep2 = 0, oS2 = 0;
   std::vector<char> autom;
 };
 
@@ -84,8 +86,9 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oFlags), 0, P.flags_bytes, st));
   OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oMax), 0, P.max_bytes, st));
-  // [0], [1]: tile counters of the main and the re-run launch; [2]: "some call is re-run"
-  OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oCounter), 0, sizeof(int) * 3, st));
+  // [0]: tile counter of the main launch; [1], [2]: tile counter and "some call is re-run" of
+  // escalation stage 2; [3], [4]: the same for stage 3
+  OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oCounter), 0, sizeof(int) * 5, st));
   // row maxima (and, for learned calls, the selector's features in the same read): jobs whose
   // whole rows fit a fused statistics unit take one pass; longer ones the two-pass units
   if (P.any_auto) OZG_CUDA(cudaMemsetAsync(gat<char>(c, P.oHist), 0, P.hist_bytes, st));
@@ -122,23 +125,34 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
                                  2 * c->num_sms, st));
   if (P.nsamp > 0)
     OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, P.oChecks), P.ncalls, P.nsamp, gat<double>(c, P.oErrs), st));
-  if (P.any_auto) {  // the check judges the selector: re-run rejected calls at the fallback count
-    OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, P.oRep), P.ncalls, c->target, gat<int>(c, P.oCounter) + 2,
-                                        st));
-    OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, P.oRep), gat<int64_t>(c, P.oSavePre), P.save_units,
-                                         P.ncalls, 1, st));
-    OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, P.oJobs2), gat<int2>(c, P.oDgTab), P.digit_units,
-                                   gat<int>(c, P.oCounter) + 2, 8 * c->num_sms, st));
-    GroupArgs g2 = g;
-    g2.calls = gat<GroupCall>(c, P.oCalls2);
-    g2.tile_counter = gat<int>(c, P.oCounter) + 1;
-    g2.run = gat<int>(c, P.oCounter) + 2;
-    {
-      PhaseScope ps(c, OZG_PHASE_GEMM);
-      OZG_CUDA(launch_slice_gemm_grouped(g2, P.variant, P.grid, st));
+  if (P.any_auto) {
+    // the check judges the selector: a rejected call is re-run at min(s + 2, fallback) (stage 2),
+    // and one rejected again at the fallback count (stage 3).  Each stage's launches are gated on
+    // a device flag, so they return at once when no call needs them.
+    struct Stage {
+      size_t rep, jobs, calls, checks, errs;
+      int ctr;
+    };
+    const Stage stages[2] = {{P.oRep, P.oJobs2, P.oCalls2, P.oChecks2, P.oErrs2, 1},
+                             {P.oRep2, P.oJobs3, P.oCalls3, P.oChecks3, P.oErrs3, 3}};
+    int* ctr = gat<int>(c, P.oCounter);
+    for (const Stage& S : stages) {
+      OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, S.rep), P.ncalls, c->target, ctr + S.ctr + 1, st));
+      OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, S.rep), gat<int64_t>(c, P.oSavePre), P.save_units,
+                                           P.ncalls, 1, st));
+      OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, S.jobs), gat<int2>(c, P.oDgTab), P.digit_units,
+                                     ctr + S.ctr + 1, 8 * c->num_sms, st));
+      GroupArgs gs = g;
+      gs.calls = gat<GroupCall>(c, S.calls);
+      gs.tile_counter = ctr + S.ctr;
+      gs.run = ctr + S.ctr + 1;
+      {
+        PhaseScope ps(c, OZG_PHASE_GEMM);
+        OZG_CUDA(launch_slice_gemm_grouped(gs, P.variant, P.grid, st));
+      }
+      OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, S.checks), P.ncalls, P.nsamp, gat<double>(c, S.errs),
+                                         st));
     }
-    OZG_CUDA(launch_check_batched_post(gat<CheckArgs>(c, P.oChecks2), P.ncalls, P.nsamp, gat<double>(c, P.oErrs2),
-                                       st));
   }
   return OZG_OK;
 }
@@ -237,7 +251,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->oErrs = cv.take(sizeof(double) * count);
   P->oCold = cv.take(sizeof(double) * 2 * (size_t)std::max(nsamp, 1) * count);
   P->oR = cv.take((size_t)P->grid * 128 * 256 * 16);
-  P->oCounter = cv.take(sizeof(int) * 3);  // tile counters (main, re-run) and the re-run flag
+  P->oCounter = cv.take(sizeof(int) * 5);  // tile counters and re-run flags of the stages
   std::vector<int64_t> sp(count + 1, 0);
   std::vector<size_t> oSv(count, 0);
   if (any_auto) {
@@ -252,6 +266,13 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     P->oErrs2 = cv.take(sizeof(double) * count);
     P->oSkip2 = cv.take(sizeof(int) * count);
     P->oJobs2 = cv.take(sizeof(SplitArgs) * 2 * count);
+    P->oCalls3 = cv.take(sizeof(GroupCall) * count + 64);
+    P->oChecks3 = cv.take(sizeof(CheckArgs) * count);
+    P->oErrs3 = cv.take(sizeof(double) * count);
+    P->oSkip3 = cv.take(sizeof(int) * count);
+    P->oJobs3 = cv.take(sizeof(SplitArgs) * 2 * count);
+    P->oRep2 = cv.take(sizeof(RepairJob) * count);
+    P->oS2 = cv.take(sizeof(int) * count);
     for (int64_t i = 0; i < count; ++i) {
       const bool sv = autom[i] && d[i].beta != 0.0;
       sp[i + 1] = sp[i] + (sv ? (d[i].m * d[i].n + 255) / 256 : 0);
@@ -364,15 +385,19 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   }
   c->check_seed += 1;
   std::vector<SelectJob> sel;
-  std::vector<RepairJob> rep;
-  std::vector<GroupCall> calls2;
-  std::vector<CheckArgs> chk2;
+  std::vector<RepairJob> rep, rep2;
+  std::vector<GroupCall> calls2, calls3;
+  std::vector<CheckArgs> chk2, chk3;
   if (any_auto) {
     sel.resize(count);
     rep.resize(count);
     calls2 = calls;
+    calls3 = calls;
     chk2 = chk;
+    chk3 = chk;
     GroupCall* calls_dev = gat<GroupCall>(c, P->oCalls);
+    GroupCall* calls2_dev = gat<GroupCall>(c, P->oCalls2);
+    GroupCall* calls3_dev = gat<GroupCall>(c, P->oCalls3);
     for (int64_t i = 0; i < count; ++i) {
       SelectJob& J = sel[i];
       J.histA = gat<unsigned long long>(c, P->oHist) + 20 * i;
@@ -384,21 +409,42 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
       J.s_out2 = gat<int>(c, P->oSused) + i;
       J.s_cap = planes[i];
       J.active = autom[i];
+      // stage 1 -> 2: the selected count, then min(selected + 2, fallback)
       RepairJob& R = rep[i];
       R.auto_mode = autom[i];
       R.beta_nz = d[i].beta != 0.0;
       R.err = gat<double>(c, P->oErrs) + i;
-      R.skip2 = gat<int>(c, P->oSkip2) + i;
+      R.ran = nullptr;
+      R.s_cur = &calls_dev[i].s;
+      R.s_next = &calls2_dev[i].s;
+      R.s_copy = gat<int>(c, P->oS2) + i;
+      R.s_add = 2;
+      R.s_fb = std::min(s[i], planes[i]);
+      R.skip_next = gat<int>(c, P->oSkip2) + i;
       R.nonfinite = flags + i;
       R.C = d[i].C;
       R.saved = (autom[i] && d[i].beta != 0.0) ? gat<double>(c, oSv[i]) : nullptr;
       R.m = d[i].m;
       R.n = d[i].n;
       R.ldc = d[i].ldc;
-      calls2[i].s = std::min(s[i], planes[i]);
-      calls2[i].nonfinite = R.skip2;  // the re-run launch skips every call not being re-run
+      // stage 2 -> 3: the fallback count
+      RepairJob R2 = R;
+      R2.err = gat<double>(c, P->oErrs2) + i;
+      R2.ran = R.skip_next;
+      R2.s_cur = &calls2_dev[i].s;
+      R2.s_next = &calls3_dev[i].s;
+      R2.s_copy = nullptr;
+      R2.s_add = 0;
+      R2.skip_next = gat<int>(c, P->oSkip3) + i;
+      rep2.push_back(R2);
+      calls2[i].s = R.s_fb;  // rewritten on the device for the calls that are re-run
+      calls2[i].nonfinite = R.skip_next;  // a stage's launch skips every call it does not re-run
+      calls3[i].s = R.s_fb;
+      calls3[i].nonfinite = R2.skip_next;
       chk2[i].err_out = gat<double>(c, P->oErrs2) + i;
-      chk2[i].gate = R.skip2;
+      chk2[i].gate = R.skip_next;
+      chk3[i].err_out = gat<double>(c, P->oErrs3) + i;
+      chk3[i].gate = R2.skip_next;
     }
   }
   P->rowmax_units = (int64_t)rmtab.size();
@@ -406,10 +452,12 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->stats_units = (int64_t)sttab.size();
   cudaStream_t st = c->stream;
   OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs), jobs.data(), sizeof(SplitArgs) * jobs.size(), cudaMemcpyHostToDevice, st));
-  std::vector<SplitArgs> jobs2;
+  std::vector<SplitArgs> jobs2, jobs3;
   if (any_auto) {
-    // completion of the digit planes for calls the check rejects: planes (selected, fallback]
+    // completion of the digit planes for calls the check rejects: planes (s1, s2] for stage 2
+    // and (s2, fallback] for stage 3
     jobs2 = jobs;
+    jobs3 = jobs;
     for (int64_t i = 0; i < count; ++i)
       for (int side = 0; side < 2; ++side) {
         SplitArgs& x = jobs2[2 * i + side];
@@ -417,8 +465,15 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
         x.plane_to = &gat<GroupCall>(c, P->oCalls2)[i].s;
         x.gate = gat<int>(c, P->oSkip2) + i;  // 1 unless the call is re-run
         x.hist = nullptr;
+        SplitArgs& y = jobs3[2 * i + side];
+        y.plane_from = &gat<GroupCall>(c, P->oCalls2)[i].s;
+        y.plane_to = &gat<GroupCall>(c, P->oCalls3)[i].s;
+        y.gate = gat<int>(c, P->oSkip3) + i;
+        y.hist = nullptr;
       }
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs2), jobs2.data(), sizeof(SplitArgs) * jobs2.size(),
+                             cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oJobs3), jobs3.data(), sizeof(SplitArgs) * jobs3.size(),
                              cudaMemcpyHostToDevice, st));
   }
   if (!rmtab.empty())
@@ -443,6 +498,12 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oCalls2), calls2.data(), sizeof(GroupCall) * count,
                              cudaMemcpyHostToDevice, st));
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oChecks2), chk2.data(), sizeof(CheckArgs) * count,
+                             cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oRep2), rep2.data(), sizeof(RepairJob) * count, cudaMemcpyHostToDevice,
+                             st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oCalls3), calls3.data(), sizeof(GroupCall) * count,
+                             cudaMemcpyHostToDevice, st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oChecks3), chk3.data(), sizeof(CheckArgs) * count,
                              cudaMemcpyHostToDevice, st));
   }
   OZG_CUDA(cudaStreamSynchronize(st));  // host tables are stack-owned
@@ -600,28 +661,31 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     if (rc) return rc;
   }
   if (reps) {
-    std::vector<int> fl(n), su(n, 0), sk(n, 1);
-    std::vector<double> er(n, NAN), er2(n, NAN);
+    std::vector<int> fl(n), su(n, 0), sk2(n, 1), sk3(n, 1), s2(n, 0);
+    std::vector<double> er(n, NAN), er2(n, NAN), er3(n, NAN);
     cudaStream_t st = c->stream;
     OZG_CUDA(cudaMemcpyAsync(fl.data(), gat<int>(c, P->oFlags), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
     if (P->nsamp > 0)
       OZG_CUDA(cudaMemcpyAsync(er.data(), gat<double>(c, P->oErrs), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     if (P->any_auto) {
       OZG_CUDA(cudaMemcpyAsync(su.data(), gat<int>(c, P->oSused), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-      OZG_CUDA(cudaMemcpyAsync(sk.data(), gat<int>(c, P->oSkip2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(sk2.data(), gat<int>(c, P->oSkip2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(sk3.data(), gat<int>(c, P->oSkip3), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(s2.data(), gat<int>(c, P->oS2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
       OZG_CUDA(cudaMemcpyAsync(er2.data(), gat<double>(c, P->oErrs2), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+      OZG_CUDA(cudaMemcpyAsync(er3.data(), gat<double>(c, P->oErrs3), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     }
     OZG_CUDA(cudaStreamSynchronize(st));
     for (int64_t i = 0; i < n; ++i) {
       ozg_report& r = reps[widx[i]];
       const bool au = P->any_auto && wauto[i];
-      const bool rerun = au && !fl[i] && !sk[i];
+      const int runs = (au && !fl[i]) ? (sk2[i] ? 0 : (sk3[i] ? 1 : 2)) : 0;  // escalations
       r.nonfinite = fl[i];
       r.selected = au ? su[i] : 0;
-      r.repaired = rerun ? 1 : 0;
-      r.slices_used = fl[i] ? -1 : (au ? (rerun ? ws[i] : su[i]) : ws[i]);
+      r.repaired = runs;
+      r.slices_used = fl[i] ? -1 : (au ? (runs == 0 ? su[i] : (runs == 1 ? s2[i] : ws[i])) : ws[i]);
       r.samples = (P->nsamp > 0 && !fl[i]) ? P->nsamp : 0;
-      r.est_err = r.samples ? (rerun ? er2[i] : er[i]) : NAN;
+      r.est_err = r.samples ? (runs == 0 ? er[i] : (runs == 1 ? er2[i] : er3[i])) : NAN;
     }
   }
   return OZG_OK;

@@ -190,13 +190,21 @@ cudaError_t launch_stats_pair(const SplitArgs& a, const SplitArgs& b, cudaStream
 // run: if non-null and *run == 0 the launch does nothing; grid_cap > 0 bounds the grid (grid-stride)
 cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, const int* run,
                                   int grid_cap, cudaStream_t st);
-// grouped automatic calls: after the check, skip2[c] = 0 for the calls to re-run (automatic,
-// finite, sampled error above the target), 1 otherwise; save / restore C of automatic calls
-// with beta != 0 (restore only for the calls being re-run)
+// Grouped automatic calls, check-driven escalation: after the check of a stage, a call is re-run
+// in the next stage (*skip_next = 0, else 1) when it is automatic, finite, ran in this stage
+// (ran == nullptr or *ran == 0), its sampled error is above the target and its count *s_cur is
+// below the fallback s_fb; the next count, min(*s_cur + s_add, s_fb) (s_fb when s_add == 0), is
+// written to *s_next and *s_copy.  Save / restore C of automatic calls with beta != 0 (restore
+// only for the calls being re-run).
 struct RepairJob {
   int auto_mode = 0, beta_nz = 0;
   const double* err = nullptr;
-  int* skip2 = nullptr;
+  const int* ran = nullptr;
+  const int* s_cur = nullptr;
+  int* s_next = nullptr;
+  int* s_copy = nullptr;
+  int s_add = 0, s_fb = 0;
+  int* skip_next = nullptr;
   const int* nonfinite = nullptr;
   double* C = nullptr;
   double* saved = nullptr;
