@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--shim-size", type=int, default=8192, help="n of the shim's n^3 DGEMM")
     ap.add_argument("--no-regions", action="store_true", help="skip the region-adaptive slice-count section")
     ap.add_argument("--selector", default="", help="selector model file (default: the package's model)")
+    ap.add_argument("--tile-variant", type=int, default=-1,
+                    help="force a tile variant of the slice-product kernel (default: autotuned)")
     args = ap.parse_args()
     if not args.selector:
         from paper_2503_22875_gb300 import selector
@@ -753,6 +755,8 @@ def run_gpu(args):
         c.load_selector(SELECTOR_MODEL)
         c.set_target_error(TARGET_ERR)
         c.set_check_samples(CHECK_SAMPLES)
+        if args.tile_variant >= 0:
+            c.set_tile_variant(args.tile_variant)
         return c
 
     ctx = learned_ctx()

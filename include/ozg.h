@@ -245,15 +245,19 @@ int ozg_set_graphs(ozg_ctx* ctx, int enable);
 /* Slice count used for calls that request 0 (default 7). */
 int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
 
-/* Tile variants of the slice-product kernel.  Bit 0 picks the output tile (0: 128 x 256,
- * 1: 128 x 128).  Bit 1: for 128 x 256 tiles, spread each intermediate epilogue accumulation
- * over the next chains' drains instead of running it at once (pays for long k, costs for short
- * k); for 128 x 128 tiles, stage one 64-wide k slice per pipeline stage in 6 stages instead of
- * two in 3 (deeper prefetch, more issue overhead).  All four variants give bit-identical C. */
-#define OZG_NUM_TILE_VARIANTS 4
+/* Tile variants of the slice-product kernel.  Variants 0..3: bit 0 picks the output tile (0:
+ * 128 x 256, 1: 128 x 128).  Bit 1: for 128 x 256 tiles, spread each intermediate epilogue
+ * accumulation over the next chains' drains instead of running it at once (pays for long k,
+ * costs for short k); for 128 x 128 tiles, stage one 64-wide k slice per pipeline stage in 6
+ * stages instead of two in 3 (deeper prefetch, more issue overhead).  Variant 4: grouped calls
+ * run on CTA pairs (2-CTA clusters sharing one tcgen05 MMA of 256 x 128 tiles; each CTA stages
+ * its own 128 rows of A and half of B); single calls run it as variant 1.  All variants give
+ * bit-identical C. */
+#define OZG_NUM_TILE_VARIANTS 5
 
 /* Tile-variant autotuner: enable != 0 times the four variants the first time a shape bucket
- * (rounded log2 of m, n, k and the slice count) or a grouped batch is seen, keeps the fastest,
+ * (rounded log2 of m, n, k and the slice count; variants 0..3) or a grouped batch (every variant)
+ * is seen, keeps the fastest,
  * and appends single-call choices to cache_path (may be NULL) as "bucket variant" lines that
  * later contexts read back.  Tuning runs only for calls with beta == 0 (C is then write-only);
  * other calls use the heuristic: the width that pads least; then for 128 x 256 tiles deferral
@@ -261,8 +265,9 @@ int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
  * k slices per stage. */
 int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
 
-/* Force tile variant 0..3 for every later call (single and grouped), or -1 (default) for the
- * autotuned / heuristic choice.  Returns OZG_ERR_INVALID for other values. */
+/* Force tile variant 0..4 for every later call (single and grouped), or -1 (default) for the
+ * autotuned / heuristic choice.  Returns OZG_ERR_INVALID for other values, OZG_ERR_UNSUPPORTED
+ * for variant 4 when no 2-CTA cluster of the kernel fits on the device. */
 int ozg_set_tile_variant(ozg_ctx* ctx, int variant);
 
 /* Kernel launches this library has issued in this process, written to *out (a replay of a

@@ -35,6 +35,8 @@
 // GEMM (tiles rastered in GROUP_M row bands), or a grouped list of tiles drawn from many GEMMs,
 // each with its own tensor maps, slice count and epilogue parameters (one persistent launch
 // for a whole batch of uneven problems).
+#include <climits>
+
 #include "ozg_device.cuh"
 #include "ozg_internal.h"
 #include "ozg_round.cuh"
@@ -56,15 +58,21 @@ static_assert(CHAIN_K * 127 * 127 < (1 << 24), "FP32 chain must stay exact");
 // 128-wide tiles, two per stage (3 stages) give eight MMAs per barrier round trip instead of
 // four -- one lane issuing a 128 x 128 x 64 block is slower than the tensor core executing it
 // -- while one per stage (6 stages) hides more load latency (large s: bigger working sets).
-template <int BN_, int SUB_>
+//
+// CTA pairs (PAIR, grouped launches, 128-wide): a 2-CTA cluster computes a 256 x BN tile with
+// tcgen05.mma.cta_group::2 (M = 256) issued by the even-rank CTA.  Each CTA stages its own 128
+// rows of A and BN / 2 of the B columns (the MMA reads the other half from the peer), so a stage
+// is 48 KB instead of 64 KB and four stages fit; each CTA's TMEM holds its own 128 rows of the
+// accumulator, drained by its own epilogue exactly as in a 1-CTA tile.
+template <int BN_, int SUB_, bool PAIR_ = false>
 struct Cfg {
   static constexpr int SUB = SUB_;
   static constexpr int SK = SUB * BK;
   static constexpr int SEG = CHAIN_K / SK;  // stages per chain
-  static constexpr int STAGES = BN_ == 256 ? 4 : (SUB_ == 2 ? 3 : 6);
-  static constexpr uint32_t SUBA_BYTES = BM * BK * 2, SUBB_BYTES = BN_ * BK * 2;
+  static constexpr int STAGES = PAIR_ ? 4 : (BN_ == 256 ? 4 : (SUB_ == 2 ? 3 : 6));
+  static constexpr uint32_t SUBA_BYTES = BM * BK * 2, SUBB_BYTES = (PAIR_ ? BN_ / 2 : BN_) * BK * 2;
   static constexpr uint32_t A_BYTES = SUB * SUBA_BYTES, B_BYTES = SUB * SUBB_BYTES, STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr uint32_t IDESC = umma_idesc_f16_f32(BM, BN_);
+  static constexpr uint32_t IDESC = umma_idesc_f16_f32(PAIR_ ? 2 * BM : BM, BN_);
   // two BN-column FP32 accumulators; 128-wide tiles also keep the int64 window words (two
   // columns per output) in the other half
   static constexpr uint32_t TMEM_COLS = 512;
@@ -97,7 +105,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   tn = r / gsz;
 }
 
-template <int BN_, int SUB_, bool GROUPED>
+template <int BN_, int SUB_, bool GROUPED, bool PAIR = false>
 __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* P,
                                            const GroupArgs* G) {
   TileJob j;
@@ -133,7 +141,7 @@ __device__ __forceinline__ TileJob get_job(int t, const CUtensorMap* tmA, const 
     j.tm = gt.tm;
     j.tn = gt.tn;
     j.tmA = &c->tmA;
-    j.tmB = &c->tmB;
+    j.tmB = PAIR ? &c->tmBh : &c->tmB;  // CTA pairs load half of the B columns each
     j.KB = (int)((c->k + Cfg<BN_, SUB_>::SK - 1) / Cfg<BN_, SUB_>::SK);
     j.klast = (int)((c->k - (int64_t)(j.KB - 1) * Cfg<BN_, SUB_>::SK + BK - 1) / BK);
     j.s = c->s;
@@ -417,10 +425,11 @@ __device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
-template <int BN_, int SUB_, bool GROUPED>
+template <int BN_, int SUB_, bool GROUPED, bool PAIR = false>
 __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtensorMap* tmB0, const GemmArgs* P,
                                           const GroupArgs* G) {
-  using K = Cfg<BN_, SUB_>;
+  static_assert(!PAIR || (GROUPED && BN_ == 128), "CTA pairs: grouped 128-wide tiles");
+  using K = Cfg<BN_, SUB_, PAIR>;
   constexpr int BN = BN_, STAGES = K::STAGES, CPT = K::CPT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -438,19 +447,25 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
   const int ntiles = GROUPED ? G->ntiles : (int)(((P->rows + BM - 1) / BM) * ((P->cols + BN - 1) / BN));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // CTA pairs: rank 0 (the leader) claims tiles, owns the stage-full, accumulator-empty and
+  // tile-ring-empty barriers both CTAs arrive at, and issues the pair MMAs
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
-      mbar_init(&bar_full[i], 1);
+      mbar_init(&bar_full[i], PAIR ? 2 : 1);  // pairs: each CTA's producer announces its bytes
       mbar_init(&bar_empty[i], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bar_accf[b], 1);
-      mbar_init(&bar_acce[b], EPI_WARPS);
+      mbar_init(&bar_acce[b], PAIR ? 2 * EPI_WARPS : EPI_WARPS);
     }
     mbar_init(&bar_done, 1);
     for (int i = 0; i < TRING; ++i) {
       mbar_init(&bar_tfull[i], 1);
-      mbar_init(&bar_tempty[i], 1 + EPI_WARPS);
+      // consumers of a ring slot: the MMA lane and the epilogue warps; pairs add the peer's
+      // producer and epilogue warps
+      mbar_init(&bar_tempty[i], PAIR ? 2 + 2 * EPI_WARPS : 1 + EPI_WARPS);
     }
     abort_flag = 0;
     mbar_fence_init();
@@ -459,9 +474,18 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     tma_prefetch_desc(tmA0);
     tma_prefetch_desc(tmB0);
   }
-  if (warp == 1) tmem_alloc(&tmem_slot, K::TMEM_COLS);
+  if (warp == 1) {
+    if (PAIR)
+      tmem_alloc_pair(&tmem_slot, K::TMEM_COLS);  // both CTAs of the pair, the same columns
+    else
+      tmem_alloc(&tmem_slot, K::TMEM_COLS);
+  }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) {  // the peer's barriers are initialised before any remote arrival
+    __syncwarp();
+    cluster_sync_all();
+  }
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   volatile int* abort_p = &abort_flag;
@@ -475,31 +499,53 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         long long issued = 0;
         const CUtensorMap* last_map = nullptr;
         uint32_t tslot = 0, tphase = 0;
-        int tnext = blockIdx.x;
+        // pairs: cluster c takes pair tile c first, then claims the next from the counter
+        const int nunits = PAIR ? (int)(gridDim.x / 2) : (int)gridDim.x;
+        int tnext = PAIR ? (int)(blockIdx.x / 2) : (int)blockIdx.x;
         for (;;) {
           int t;
-          if (GROUPED) {
-            if (!mbar_wait(&bar_tempty[tslot], tphase ^ 1, abort_p, status)) goto producer_done;
+          if (GROUPED && (!PAIR || leader)) {
+            // claim the next tile and pass it to this CTA's consumers (and the peer's, for pairs)
+            const bool ok = PAIR ? mbar_wait_cluster(&bar_tempty[tslot], tphase ^ 1, abort_p, status)
+                                 : mbar_wait(&bar_tempty[tslot], tphase ^ 1, abort_p, status);
+            if (!ok) goto producer_done;
             t = tnext < ntiles ? tnext : -1;
             tile_ring[tslot] = t;
             mbar_arrive(&bar_tfull[tslot]);
+            if (PAIR) {
+              st_shared_cluster(mapa_shared(&tile_ring[tslot], 1), t);
+              mbar_arrive_cluster(mapa_shared(&bar_tfull[tslot], 1));  // release: the slot write first
+            }
             if (++tslot == TRING) {
               tslot = 0;
               tphase ^= 1;
             }
-            if (t >= 0) tnext = (int)gridDim.x + atomicAdd(G->tile_counter, 1);
+            if (t >= 0) tnext = nunits + atomicAdd(G->tile_counter, 1);
+          } else if (GROUPED) {
+            // pair follower: the leader's tile, from this CTA's ring slot
+            if (!mbar_wait_cluster(&bar_tfull[tslot], tphase, abort_p, status)) goto producer_done;
+            t = tile_ring[tslot];
+            // the release of the slot depends on the value read, so it cannot overtake the load
+            if (t != INT_MIN) mbar_arrive_remote(mapa_shared(&bar_tempty[tslot], 0));
+            if (++tslot == TRING) {
+              tslot = 0;
+              tphase ^= 1;
+            }
           } else {
             t = tnext < ntiles ? tnext : -1;
             tnext += gridDim.x;
           }
           if (t < 0) break;
-          const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
+          const TileJob j = get_job<BN_, SUB_, GROUPED, PAIR>(t, tmA0, tmB0, P, G);
           if (j.skip) continue;
           if (GROUPED && j.tmA != last_map) {
             tensormap_acquire(j.tmA);
             tensormap_acquire(j.tmB);
             last_map = j.tmA;
           }
+          // pairs: this CTA's 128 rows of the 256-row tile, and its half of the B columns
+          const int arow = PAIR ? (j.tm * 2 + (int)rank) * BM : j.tm * BM;
+          const int brow = PAIR ? j.tn * BN + (int)rank * (BN / 2) : j.tn * BN;
           for (int g = 2; g <= j.s + 1; ++g)
             for (int kbi = 0; kbi < j.KB; ++kbi)
               for (int p = 1; p < g; ++p) {
@@ -507,14 +553,29 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                 if (!mbar_wait(&bar_empty[stage], phase ^ 1, abort_p, status)) goto producer_done;
                 uint8_t* sA = smem + stage * K::STAGE_BYTES;
                 const int nsub = kb == j.KB - 1 ? j.klast : K::SUB;  // an all-zero tail sub-tile is skipped
-                mbar_arrive_expect_tx(&bar_full[stage], (uint32_t)nsub * (K::SUBA_BYTES + K::SUBB_BYTES));
+                const uint32_t bytes = (uint32_t)nsub * (K::SUBA_BYTES + K::SUBB_BYTES);
+                if (PAIR) {
+                  // both CTAs' copies complete on the leader's stage barrier, which each producer
+                  // first arms with its own byte count
+                  const uint32_t fbar = mapa_shared(&bar_full[stage], 0);
+                  mbar_arrive_expect_tx_remote(fbar, bytes);
 #pragma unroll
-                for (int h = 0; h < K::SUB; ++h)
-                  if (h < nsub) {
-                    tma_load_3d(j.tmA, &bar_full[stage], sA + h * K::SUBA_BYTES, kb * K::SK + h * BK, j.tm * BM, p - 1);
-                    tma_load_3d(j.tmB, &bar_full[stage], sA + K::A_BYTES + h * K::SUBB_BYTES, kb * K::SK + h * BK,
-                                j.tn * BN, g - p - 1);
-                  }
+                  for (int h = 0; h < K::SUB; ++h)
+                    if (h < nsub) {
+                      tma_load_3d_pair(j.tmA, fbar, sA + h * K::SUBA_BYTES, kb * K::SK + h * BK, arow, p - 1);
+                      tma_load_3d_pair(j.tmB, fbar, sA + K::A_BYTES + h * K::SUBB_BYTES, kb * K::SK + h * BK, brow,
+                                       g - p - 1);
+                    }
+                } else {
+                  mbar_arrive_expect_tx(&bar_full[stage], bytes);
+#pragma unroll
+                  for (int h = 0; h < K::SUB; ++h)
+                    if (h < nsub) {
+                      tma_load_3d(j.tmA, &bar_full[stage], sA + h * K::SUBA_BYTES, kb * K::SK + h * BK, arow, p - 1);
+                      tma_load_3d(j.tmB, &bar_full[stage], sA + K::A_BYTES + h * K::SUBB_BYTES, kb * K::SK + h * BK,
+                                  brow, g - p - 1);
+                    }
+                }
                 ++issued;
                 if (++stage == STAGES) {
                   stage = 0;
@@ -524,22 +585,30 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         }
       producer_done:
         if (*abort_p) {
-          // wait (bounded) for the copies still in flight into this CTA's shared memory
-          uint32_t st = stage, ph = phase;
-          for (long long i = 0; i < STAGES && i < issued; ++i) {
-            if (st == 0) {
-              st = STAGES - 1;
-              ph ^= 1;
-            } else {
-              --st;
+          if (!PAIR || leader) {
+            // wait (bounded) for the copies still in flight into this CTA's shared memory
+            uint32_t st = stage, ph = phase;
+            for (long long i = 0; i < STAGES && i < issued; ++i) {
+              if (st == 0) {
+                st = STAGES - 1;
+                ph ^= 1;
+              } else {
+                --st;
+              }
+              drain_wait(&bar_full[st], ph);
             }
-            drain_wait(&bar_full[st], ph);
+          } else {
+            // the follower's copies complete on the leader's barriers: give them time to land
+            const long long t0 = clock64();
+            while (clock64() - t0 < 2000000ll) {
+            }
           }
         }
       }
     } else if (warp == 1) {
       // ---------------------------------------------------------------- MMA issuer
-      if (lane == 0) {
+      // (pairs: the leader's lane issues for both CTAs; the follower's lane has no work)
+      if (lane == 0 && (!PAIR || leader)) {
         uint32_t stage = 0, phase = 0;
         uint32_t acc_par = 0;  // bit b: parity of the next use of TMEM buffer b
         int buf = 0;
@@ -560,7 +629,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
             tnext += gridDim.x;
           }
           if (t < 0) break;
-          const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
+          const TileJob j = get_job<BN_, SUB_, GROUPED, PAIR>(t, tmA0, tmB0, P, G);
           if (j.skip) continue;
           for (int g = 2; g <= j.s + 1; ++g) {
             const int nblk = (g - 1) * j.KB;
@@ -570,6 +639,7 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
                 const int kb = (g & 1) ? j.KB - 1 - kbi : kbi;  // snake: each group starts where the last ended
                 const bool chain_start = (b % K::SEG) == 0;
                 if (chain_start) {
+                  // pairs: both CTAs' epilogues release the buffer
                   if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, status)) goto mma_done;
                   tc_fence_after();
                 }
@@ -582,22 +652,34 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
 #pragma unroll
                   for (int h = 0; h < K::SUB; ++h)
                     if (h < nsub) {
+                      // pairs: the descriptors name this CTA's tiles; the MMA takes the peer's
+                      // halves at the same shared-memory offsets
                       const uint64_t da = umma_desc_sw128(sA + h * K::SUBA_BYTES);
                       const uint64_t db = umma_desc_sw128(sA + K::A_BYTES + h * K::SUBB_BYTES);
 #pragma unroll
-                      for (int q = 0; q < BK / 16; ++q)
-                        umma_f16(dt, da + (uint64_t)(2 * q), db + (uint64_t)(2 * q), K::IDESC,
-                                 (!chain_start || h != 0 || q != 0) ? 1u : 0u);
+                      for (int q = 0; q < BK / 16; ++q) {
+                        const uint32_t acc = (!chain_start || h != 0 || q != 0) ? 1u : 0u;
+                        if (PAIR)
+                          umma_f16_pair(dt, da + (uint64_t)(2 * q), db + (uint64_t)(2 * q), K::IDESC, acc);
+                        else
+                          umma_f16(dt, da + (uint64_t)(2 * q), db + (uint64_t)(2 * q), K::IDESC, acc);
+                      }
                     }
                 }
-                umma_commit(&bar_empty[stage]);
+                if (PAIR)
+                  umma_commit_pair_mc(&bar_empty[stage], 3);  // the stage is free in both CTAs
+                else
+                  umma_commit(&bar_empty[stage]);
                 if (++stage == STAGES) {
                   stage = 0;
                   phase ^= 1;
                 }
                 ++b;
                 if (b % K::SEG == 0 || b == nblk) {
-                  umma_commit(&bar_accf[buf]);
+                  if (PAIR)
+                    umma_commit_pair_mc(&bar_accf[buf], 3);  // the chain is ready in both CTAs' TMEM
+                  else
+                    umma_commit(&bar_accf[buf]);
                   acc_par ^= 1u << buf;
                   buf ^= 1;
                 }
@@ -606,7 +688,10 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         }
       mma_done:
         // all MMAs issued by this thread must finish before TMEM is released
-        umma_commit(&bar_done);
+        if (PAIR)
+          umma_commit_pair_mc(&bar_done, 1);
+        else
+          umma_commit(&bar_done);
         drain_wait(&bar_done, 0);
       }
     }
@@ -639,10 +724,19 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
     for (;;) {
       int t;
       if (GROUPED) {
-        if (!mbar_wait(&bar_tfull[tslot], tphase, abort_p, status)) goto epi_done;
+        const bool ok = PAIR ? mbar_wait_cluster(&bar_tfull[tslot], tphase, abort_p, status)
+                             : mbar_wait(&bar_tfull[tslot], tphase, abort_p, status);
+        if (!ok) goto epi_done;
         t = tile_ring[tslot];
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bar_tempty[tslot]);
+        if (lane == 0) {
+          if (PAIR) {
+            // the leader's ring slot; the release depends on the value read (see the producer)
+            if (t != INT_MIN) mbar_arrive_remote(mapa_shared(&bar_tempty[tslot], 0));
+          } else {
+            mbar_arrive(&bar_tempty[tslot]);
+          }
+        }
         if (++tslot == TRING) {
           tslot = 0;
           tphase ^= 1;
@@ -652,11 +746,12 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
         tnext += gridDim.x;
       }
       if (t < 0) break;
-      const TileJob j = get_job<BN_, SUB_, GROUPED>(t, tmA0, tmB0, P, G);
+      const TileJob j = get_job<BN_, SUB_, GROUPED, PAIR>(t, tmA0, tmB0, P, G);
       if (j.skip) continue;
       const int s = j.s;
       const int push_segs = j.cplx ? 32 : 64;  // int32 group sums stay below 2^31
-      const int64_t grow = (int64_t)j.tm * BM + r;  // row of the (stacked) product
+      // row of the (stacked) product; pairs: this CTA's 128 rows of the 256-row tile
+      const int64_t grow = (int64_t)(PAIR ? j.tm * 2 + (int)rank : j.tm) * BM + r;
       const bool row_ok = grow < j.rows;
       const int64_t orow = j.cplx ? (grow >> 1) : grow;
       const int e_row = (row_ok && j.e != nullptr) ? j.e[orow] : 0;
@@ -703,7 +798,12 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&bar_acce[buf]);
+          if (lane == 0) {
+            if (PAIR)
+              mbar_arrive_remote(mapa_shared(&bar_acce[buf], 0));  // the leader's MMA lane waits on it
+            else
+              mbar_arrive(&bar_acce[buf]);
+          }
           acc_par ^= 1u << buf;
           buf ^= 1;
           const bool group_end = (seg == nseg - 1);
@@ -831,9 +931,18 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
 
   tc_fence_before();
   __syncthreads();
+  // pairs: neither CTA leaves (or frees TMEM) while the peer may still reach its shared memory
+  // or the leader's MMAs its TMEM
+  if (PAIR) {
+    __syncwarp();
+    cluster_sync_all();
+  }
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, K::TMEM_COLS);
+    if (PAIR)
+      tmem_dealloc_pair(tmem, K::TMEM_COLS);
+    else
+      tmem_dealloc(tmem, K::TMEM_COLS);
   }
 }
 
@@ -849,6 +958,13 @@ template <int BN_, int SUB_>
 __global__ void __launch_bounds__(THREADS, 1) slice_gemm_grouped_kernel(const GroupArgs G) {
   if (G.run != nullptr && *G.run == 0) return;  // a re-run launch with nothing to re-run
   gemm_body<BN_, SUB_, true>(nullptr, nullptr, nullptr, &G);
+}
+
+// CTA pairs: 2-CTA clusters over 256 x 128 pair tiles.  Both CTAs read the same run flag, so a
+// gated launch returns from both before either touches the other.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1) slice_gemm_pair_kernel(const GroupArgs G) {
+  if (G.run != nullptr && *G.run == 0) return;
+  gemm_body<128, 2, true, true>(nullptr, nullptr, nullptr, &G);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -880,7 +996,33 @@ cudaError_t set_smem_once(Kern k, size_t bytes, bool& done) {
 
 int slice_gemm_tile_m() { return BM; }
 int slice_gemm_tile_n() { return 256; }
-int slice_gemm_tile_n_of(int variant) { return (variant & 1) ? 128 : 256; }
+int slice_gemm_tile_n_of(int variant) { return ((variant & 1) || variant == kPairVariant) ? 128 : 256; }
+int slice_gemm_tile_m_of(int variant) { return variant == kPairVariant ? 2 * BM : BM; }
+
+// CTAs of the pair variant that can be resident at once (2 per cluster), queried once per process.
+int pair_max_ctas() {
+  static int n = -1;
+  if (n < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Cfg<128, 2, true>::SMEM;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, slice_gemm_pair_kernel, &cfg) != cudaSuccess || clusters <= 0) {
+      cudaGetLastError();
+      clusters = 0;
+    }
+    n = 2 * clusters;
+  }
+  return n;
+}
 size_t slice_gemm_smem_bytes() { return Cfg<256, 1>::SMEM; }
 
 // Tensor map of a digit-plane set.  Half of the groups sweep k backwards, so a promotion wider
@@ -935,6 +1077,9 @@ cudaError_t launch_variant(int variant, const CUtensorMap* tmA, const CUtensorMa
 // Shared-memory opt-in for every kernel instance, once per process (outside any graph capture).
 cudaError_t prepare_kernels() {
   cudaError_t e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Cfg<128, 2, true>::SMEM)) != cudaSuccess)
+    return e;
   if ((e = cudaFuncSetAttribute(slice_gemm_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<256, 1>::SMEM)) != cudaSuccess)
     return e;
@@ -961,6 +1106,15 @@ cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, co
 
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st) {
   if (grid <= 0 || g.ntiles <= 0) return cudaSuccess;
+  if (variant == kPairVariant) {
+    if (grid % 2) return cudaErrorInvalidValue;  // whole clusters
+    static bool done = false;
+    cudaError_t e = set_smem_once(slice_gemm_pair_kernel, Cfg<128, 2, true>::SMEM, done);
+    if (e != cudaSuccess) return e;
+    slice_gemm_pair_kernel<<<grid, THREADS, Cfg<128, 2, true>::SMEM, st>>>(g);
+    note_launch();
+    return cudaGetLastError();
+  }
   return launch_variant<true>(variant, nullptr, nullptr, nullptr, &g, grid, st);
 }
 

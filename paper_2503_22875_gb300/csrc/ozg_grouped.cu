@@ -62,10 +62,10 @@ std::vector<GroupTile> ordered_tiles(const ozg_gemm_desc* d, const std::vector<i
     double cost;
     GroupTile t;
   };
-  const int BN = tile_n_of(variant & 1);
+  const int BN = tile_n_of(variant), BMv = slice_gemm_tile_m_of(variant);
   std::vector<T> all;
   for (int64_t c = 0; c < count; ++c) {
-    const int64_t tm = (d[c].m + 127) / 128, tn = (d[c].n + BN - 1) / BN;
+    const int64_t tm = (d[c].m + BMv - 1) / BMv, tn = (d[c].n + BN - 1) / BN;
     // per tile, the same for all tiles of a call (they stay together): slice products x k
     // (in 16-wide steps) plus the epilogue's per-group work, times the call's mean valid tile
     // width (16-column steps) -- an estimate that orders measurably better than the padded width
@@ -194,9 +194,12 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   P->variant = variant;
   P->s_used = s;
   int64_t total_tiles = 0;
-  const int BN = tile_n_of(variant);
-  for (int64_t i = 0; i < count; ++i) total_tiles += ((d[i].m + 127) / 128) * ((d[i].n + BN - 1) / BN);
-  P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->num_sms, total_tiles));
+  const int BN = tile_n_of(variant), BMv = slice_gemm_tile_m_of(variant);
+  for (int64_t i = 0; i < count; ++i) total_tiles += ((d[i].m + BMv - 1) / BMv) * ((d[i].n + BN - 1) / BN);
+  if (variant == kPairVariant)  // whole 2-CTA clusters, as many as can be resident, one per pair tile
+    P->grid = (int)(2 * std::max<int64_t>(1, std::min<int64_t>(pair_max_ctas() / 2, total_tiles)));
+  else
+    P->grid = (int)std::max<int64_t>(1, std::min<int64_t>(c->num_sms, total_tiles));
   std::vector<GroupTile> tiles = ordered_tiles(d, s, count, variant);
   P->ntiles = (int)tiles.size();
 
@@ -327,6 +330,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     GroupCall& g = calls[i];
     OZG_CUDA(make_digit_tmap(&g.tmA, a.D, d[i].k, d[i].m, Kp, planes[i], 128));
     OZG_CUDA(make_digit_tmap(&g.tmB, b.D, d[i].k, d[i].n, Kp, planes[i], BN));
+    OZG_CUDA(make_digit_tmap(&g.tmBh, b.D, d[i].k, d[i].n, Kp, planes[i], BN / 2));
     g.rows = d[i].m;
     g.cols = d[i].n;
     g.m = d[i].m;
@@ -605,7 +609,8 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
       variant = tuned->second;
     } else if (c->autotune && all_beta_zero) {
       float best = 1e30f;
-      for (int v = 0; v < 4; ++v) {
+      const int nvar = ozg::pair_max_ctas() >= 2 ? OZG_NUM_TILE_VARIANTS : ozg::kPairVariant;
+      for (int v = 0; v < nvar; ++v) {
         std::unique_ptr<GroupPlan, PlanDeleter> T(new GroupPlan());
         int rc = build_plan(c, n, work.data(), ws, wa, wb, wauto, v, T.get());
         if (rc) return rc;
@@ -754,6 +759,7 @@ extern "C" int ozg_dgemm_regions(ozg_ctx* c, char transa, char transb, int64_t m
 
 extern "C" int ozg_set_tile_variant(ozg_ctx* c, int variant) {
   if (!c || variant < -1 || variant >= OZG_NUM_TILE_VARIANTS) return OZG_ERR_INVALID;
+  if (variant == ozg::kPairVariant && ozg::pair_max_ctas() < 2) return OZG_ERR_UNSUPPORTED;  // no 2-CTA cluster fits
   c->force_variant = variant;
   c->plan.reset();  // a cached grouped plan may hold another variant
   return OZG_OK;

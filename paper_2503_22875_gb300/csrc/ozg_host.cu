@@ -143,7 +143,8 @@ static int heuristic_variant(int64_t rows, int64_t cols, int64_t k, int s) {
 }
 
 int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s) {
-  if (c->force_variant >= 0) return c->force_variant;
+  // single calls have no CTA-pair kernel: a forced pair variant runs as the 1-CTA 128-wide one
+  if (c->force_variant >= 0) return c->force_variant == kPairVariant ? 1 : c->force_variant;
   tune_load(c);
   auto it = c->tune.find(shape_bucket(rows, cols, k, s));
   if (it != c->tune.end()) return it->second;

@@ -74,6 +74,7 @@ struct GemmArgs {
 // Grouped (batched) GEMM: one persistent launch over the tiles of many independent problems.
 struct GroupCall {
   CUtensorMap tmA, tmB;         // digit planes of this call (64-byte aligned inside the struct)
+  CUtensorMap tmBh;             // B planes with half-height boxes (the CTA-pair variant)
   int64_t rows = 0, cols = 0, m = 0, n = 0, k = 0;
   int s = 0, cplx = 0, beta_zero = 1, pad = 0;
   const int32_t* e = nullptr;
@@ -97,7 +98,12 @@ struct GroupArgs {
   double* Rws = nullptr;
   int defer = 0;  // as GemmArgs::defer
 };
+// Tile variant 4: grouped launches on CTA pairs (2-CTA clusters, tcgen05.mma.cta_group::2 over
+// 256 x 128 pair tiles; GroupTile::tm counts 256-row tiles).  Single calls take variant 1 instead.
+constexpr int kPairVariant = 4;
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st);
+int slice_gemm_tile_m_of(int variant);
+int pair_max_ctas();  // resident CTAs of the pair variant (0 if the query fails)
 // deferred epilogue pushes apply to 256-wide tiles only (128-wide tiles keep R in TMEM)
 inline int variant_defers(int variant) { return (variant & 3) == 2 ? 1 : 0; }
 // set the kernels' dynamic shared-memory limits (once per process, before any stream capture)

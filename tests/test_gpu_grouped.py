@@ -159,8 +159,9 @@ def test_single_call_autotune_cache_and_bits(ozg, tmp_path):
 
 
 def test_tile_variants_bit_identical(ozg):
-    """The four tile variants (128 x 256 / 128 x 128 tiles, immediate / deferred epilogue pushes)
-    give the same bits: single real and complex calls with beta != 0, and a grouped batch."""
+    """The tile variants (128 x 256 / 128 x 128 tiles, immediate / deferred epilogue pushes, and
+    CTA pairs on 256 x 128 tiles) give the same bits: single real and complex calls with
+    beta != 0, and a grouped batch."""
     m, n, k, s = 200, 300, 2100, 8   # ragged tiles, several k-segments per pair
     A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=340)
     C0 = np.asfortranarray(workloads.rng(341).uniform(-1, 1, (m, n)))
@@ -171,7 +172,7 @@ def test_tile_variants_bit_identical(ozg):
     batch = make_batch(ozg, 12, seed=345)
     dA, dB, dAz, dBz = (ozg.to_device(x) for x in (A, B, Az, Bz))
     res = []
-    for v in range(4):
+    for v in range(5):  # variant 4 (CTA pairs) runs the grouped batch on 2-CTA clusters
         ctx = ozg.Context()
         ctx.set_tile_variant(v)
         dC, dZ = ozg.to_device(C0), ozg.to_device(Z0)
@@ -193,14 +194,14 @@ def test_tile_variants_bit_identical(ozg):
     Ez = oracle.zgemm_emu(Az, Bz, 6, "N", "N", 0.5 - 2j, 1.5 + 0.25j, Z0)
     assert np.array_equal(ozg.from_device(res[0][1], mz, nz), Ez)
     with pytest.raises(ozg.OzgError):
-        ozg.Context().set_tile_variant(4)
+        ozg.Context().set_tile_variant(5)
 
 
 NARROW_SHAPES = [(130, 1, 17), (33, 17, 1), (97, 40, 70), (1, 65, 33), (130, 161, 130), (65, 304, 47),
                  (200, 100, 1000), (129, 48, 16)]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_narrow_tiles_ragged_k_bit_exact(ozg, variant):
     """Narrow last column tiles (1 .. 48 valid columns of a 128- or 256-wide tile), k ending
     inside a 16-wide step or a 64-wide TMA box, and row tiles with one to a few valid rows: in
@@ -242,3 +243,38 @@ def test_narrow_tiles_ragged_k_bit_exact(ozg, variant):
             assert np.array_equal(ozg.from_device(dC, m, n), E), (m, n, k)
     finally:
         ctx.close()
+
+
+def test_pair_tiles_bit_exact_and_replay(ozg):
+    """CTA pairs (variant 4): a batch whose calls give pair tiles with both halves full, a ragged
+    second half, an all-padding second half (m <= 128), one column and many pair tiles, with
+    alpha / beta, a call skipped for a NaN, fewer CTAs than pair tiles (the persistent loop) and a
+    graph replay; every finite call equals the oracle bit for bit."""
+    shapes = [(256, 128, 300), (300, 129, 64), (100, 250, 1000), (513, 1, 17), (700, 900, 129), (128, 128, 2100),
+              (257, 384, 640), (1200, 1100, 333)]
+    st = torch.cuda.Stream()
+    ctx = ozg.Context(stream=st)
+    ctx.set_tile_variant(4)
+    batch = []
+    for i, (m, n, k) in enumerate(shapes):
+        g = workloads.rng(1300 + i)
+        A = np.asfortranarray(workloads.wide_exponent((m, k), 2.0, g))
+        B = np.asfortranarray(workloads.wide_exponent((k, n), 2.0, g))
+        C0 = np.asfortranarray(g.uniform(-1, 1, (m, n)))
+        alpha, beta = (1.0, 0.0) if i % 2 == 0 else (-0.5, 0.75)
+        batch.append(dict(ta="N", tb="N", m=m, n=n, k=k, s=7 + i % 3, alpha=alpha, beta=beta, A=A, B=B, C0=C0,
+                          dA=ozg.to_device(A), dB=ozg.to_device(B), dC=ozg.to_device(C0)))
+    bad = batch[3]
+    bad["A"][5, 0] = np.nan
+    bad["dA"].copy_(ozg.to_device(bad["A"]))
+    torch.cuda.synchronize()
+    for rep in range(2):  # plan + capture, then a replay with the same buffers
+        for b in batch:
+            b["dC"].copy_(ozg.to_device(b["C0"]))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            reps = ctx.dgemm_grouped(calls_of(batch), [b["s"] for b in batch], report=True)
+        assert reps[3].nonfinite == 1
+        assert all(r.status == 0 for r in reps)
+        check_batch(ozg, [b for i, b in enumerate(batch) if i != 3])
+    ctx.close()

@@ -5,7 +5,7 @@ A seeded sample of 64 calls of the headline batch (2048 DGEMMs, m, n, k log-unif
 and k, calls with k in (1024, 2048], and random ones.  They run as one grouped call with
 slices = 0 (the selector picks s per call for 1e-12; the sampled check judges every call and
 escalates rejected ones: s + 2, then the fallback), on a non-default stream so that the sequence is graph-captured, in the
-128-wide tile variant the headline uses and in the 256-wide one.
+128-wide tile variant, in the 256-wide one and on CTA pairs (256 x 128 pair tiles).
 
 Per call: the selector's decision equals the oracle's features + MLP decision (up to a
 cumulative probability within 1e-5 of the threshold); C equals the oracle's emulation at the
@@ -71,7 +71,7 @@ def sample():
     return out
 
 
-@pytest.mark.parametrize("variant", [1, 0])
+@pytest.mark.parametrize("variant", [1, 0, 4])
 def test_learned_grouped_headline_calls_match_oracle(ozg, sample, variant):
     model = selector.read_model(selector.DEFAULT_MODEL)
     s_cap = max(model["s_lo"] + 10, model["fallback"])
