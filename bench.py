@@ -417,6 +417,17 @@ def compare_section(ozg, torch, batch, calls, flops, st, steps, learned_reps):
     ok_99 = [s for s in FIXED_SWEEP if fixed[s]["frac_le_target"] >= 0.99]
     out["smallest_fixed_s_meeting_target_on_all_calls"] = min(ok_all) if ok_all else None
     out["smallest_fixed_s_meeting_target_on_99pct"] = min(ok_99) if ok_99 else None
+    # the learned step with each tile variant forced, against the autotuned choice
+    tv = {}
+    for v in range(5):
+        ctx = ozg.Context(stream=st)
+        ctx.load_selector(SELECTOR_MODEL)
+        ctx.set_target_error(TARGET_ERR)
+        ctx.set_check_samples(CHECK_SAMPLES)
+        ctx.set_tile_variant(v)
+        tv[v] = timed(torch, st, lambda: ctx.dgemm_grouped(calls, [0] * n), max(1, min(steps, 5)))
+        ctx.close()
+    out["learned_ms_by_tile_variant"] = tv
     ctx = ozg.Context(stream=st)
     ms = timed(torch, st, lambda: [ctx.native_dgemm(*c) for c in calls], 1, warm=0)
     out["native_fp64_one_at_a_time"] = {"ms": ms, "tflops": flops / (ms / 1e3) / 1e12}
@@ -713,6 +724,50 @@ def e2e_pipelined(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=E
             "pipeline": f"{len(parts)} sub-batches, H2D / compute / D2H overlapped on separate streams"}
 
 
+def e2e_host_abi(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=E2E_PARTS):
+    """End to end through the host-memory C ABI: the batch lives in pinned host memory (each
+    call's A, B and C back to back in three buffers) and every step is one synchronous
+    ozg_dgemm_grouped_host call -- the library copies the inputs in, computes the learned grouped
+    emulation in pipelined parts and copies C out.  Wall-clock per call (the call returns when C
+    is on the host), after one untimed call that builds the parts' plans."""
+    calls = batch.calls
+    n = len(calls)
+    sz = {"A": [c.m * c.k for c in calls], "B": [c.k * c.n for c in calls], "C": [c.m * c.n for c in calls]}
+    host, offs = {}, {}
+    for key, dev in (("A", batch.A), ("B", batch.B), ("C", batch.C)):
+        o = np.concatenate([[0], np.cumsum(sz[key])]).astype(np.int64)
+        offs[key] = o
+        host[key] = torch.empty(int(o[-1]), dtype=torch.float64, pin_memory=True)
+        if key != "C":
+            src = {"A": batch.offA, "B": batch.offB}[key]
+            packed = torch.cat([dev[src[i]:src[i] + sz[key][i]] for i in range(n)])
+            host[key].copy_(packed)
+            del packed
+    torch.cuda.empty_cache()
+    ptr = {key: host[key].data_ptr() for key in host}
+    descs = [("N", "N", c.m, c.n, c.k, 1.0, ptr["A"] + 8 * int(offs["A"][i]), c.m, ptr["B"] + 8 * int(offs["B"][i]),
+              c.k, 0.0, ptr["C"] + 8 * int(offs["C"][i]), c.m) for i, c in enumerate(calls)]
+    ctx = make_ctx()
+    ctx.set_host_parts(nparts)
+    ctx.dgemm_grouped_host(descs, [0] * n)  # plans and graphs of the parts
+    e2e_steps = max(2, steps // 2)
+    if pg is not None:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.dgemm_grouped_host(descs, [0] * n)
+    ms = world_max(pg, (time.perf_counter() - t0) * 1e3 / e2e_steps, "cuda")
+    reps = ctx.dgemm_grouped_host(descs, [0] * n, report=True)
+    ctx.close()
+    out = {"value": weak_value(flops, world, ms), "unit": "TFLOP/s",
+           "h2d_bytes_per_step": 8 * (int(offs["A"][-1]) + int(offs["B"][-1])),
+           "d2h_bytes_per_step": 8 * int(offs["C"][-1]), "ms_per_step": ms,
+           "api": f"ozg_dgemm_grouped_host (host pointers in, C on the host out; {nparts} pipelined parts)",
+           "frac_le_target": float(np.mean([r.est_err <= TARGET_ERR for r in reps]))}
+    del host
+    return out
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -757,15 +812,18 @@ def run_gpu(args):
         c.set_check_samples(CHECK_SAMPLES)
         if args.tile_variant >= 0:
             c.set_tile_variant(args.tile_variant)
+        else:
+            c.set_autotune(True)  # the batch's tile variant, timed once per batch and cached
         return c
 
     ctx = learned_ctx()
     auto = [0] * n
     with torch.cuda.stream(st):
-        ctx.dgemm_grouped(calls, auto)  # plan, digit workspace, graph capture
+        ctx.dgemm_grouped(calls, auto)  # plan (tile variant autotuned), digit workspace, graph capture
         for _ in range(args.warmup):
             ctx.dgemm_grouped(calls, auto)
     torch.cuda.synchronize()
+    tile_variant = ctx.tile_variant()
     clocks = ClockSampler(local)
     if pg is not None:
         pg.barrier()
@@ -823,12 +881,14 @@ def run_gpu(args):
     roof["note"] = ("tensor flops = sum over calls of s(s+1)/2 * 2mnk at the selected s (plus escalated re-runs); "
                     "launch_ms = the step's grouped GEMM launches, CUDA events, without the graph")
 
-    # end to end through the C ABI: every step copies the whole batch host -> device, runs it and
-    # copies C back.  The batch is cut into E2E_PARTS contiguous sub-batches (one context, stream
-    # and graph each) so that copies of one part overlap the emulation of another.
+    # end to end through the host-memory C ABI (ozg_dgemm_grouped_host): every step copies the
+    # whole batch host -> device, runs it and copies C back, pipelined in E2E_PARTS parts inside
+    # the library; beside it, the same with torch copies into device buffers and the device entry
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_pipelined(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops, args.e2e_parts)
+        e2e = e2e_host_abi(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops, args.e2e_parts)
+        e2e["device_buffer_pipeline"] = e2e_pipelined(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops,
+                                                      args.e2e_parts)
     ctx.close()
     if pg is not None:
         pg.barrier()
@@ -875,6 +935,8 @@ def run_gpu(args):
                                 f"phi~U(0,4) per call, beta=0), slices chosen per call by the selector MLP for "
                                 f"{TARGET_ERR:g}, one graph-replayed ozg_dgemm_grouped call per step"),
                    "calls": n, "target": TARGET_ERR, "check_samples": CHECK_SAMPLES,
+                   "tile_variant": tile_variant,
+                   "tile_variant_choice": "forced" if args.tile_variant >= 0 else "autotuned (timed once per batch)",
                    "selector": os.path.relpath(SELECTOR_MODEL, ROOT),
                    "l2": f"inputs larger than L2 ({in_bytes / 1e9:.1f} GB of A and B per batch), no flush"},
         "accuracy": stats,

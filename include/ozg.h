@@ -208,6 +208,23 @@ typedef struct ozg_gemm_desc {
 int ozg_dgemm_grouped(ozg_ctx* ctx, int64_t count, const ozg_gemm_desc* descs, const int* slices,
                       ozg_report* reps);
 
+/* The grouped emulated DGEMM on matrices in HOST memory: the descriptors' A, B and C are host
+ * (CPU) pointers, everything else is as for ozg_dgemm_grouped (slices, reports, the selector, the
+ * check and its escalation).  Synchronous: on return C holds the results and the reports are
+ * final.  The library stages the matrices in device memory it owns (grown with cudaMalloc) and
+ * cuts the batch into parts of about equal work (ozg_set_host_parts, default 4): a part's inputs
+ * are copied in while earlier parts compute and their results are copied out, each part on its
+ * own internal stream and CUDA graph.  Matrices whose host regions touch or overlap move as one
+ * copy; C is written back only where the calls write it (rows 0..m-1 of each column; C is read
+ * only when beta != 0).  Page-locked (pinned) host memory lets the copies run at full rate and
+ * overlap the computation; pageable memory works too.  Returns OZG_ERR_INVALID if any
+ * descriptor is invalid (nothing is copied), else 0 or a runtime error. */
+int ozg_dgemm_grouped_host(ozg_ctx* ctx, int64_t count, const ozg_gemm_desc* descs, const int* slices,
+                           ozg_report* reps);
+
+/* Parts of the pipeline of ozg_dgemm_grouped_host (1..64; -2 for other values). */
+int ozg_set_host_parts(ozg_ctx* ctx, int parts);
+
 /* 3M (Karatsuba) ZGEMM: the same contract as ozg_zgemm, computed from three real emulated
  * products instead of four real sub-products.  With Ar, Ai the real and imaginary parts of op(A)
  * (conjugated for 'C'), Sa = RN(Ar + Ai) and the same for op(B):
@@ -269,6 +286,10 @@ int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
  * autotuned / heuristic choice.  Returns OZG_ERR_INVALID for other values, OZG_ERR_UNSUPPORTED
  * for variant 4 when no 2-CTA cluster of the kernel fits on the device. */
 int ozg_set_tile_variant(ozg_ctx* ctx, int variant);
+
+/* Tile variant of the context's most recent grouped call (the autotuned, heuristic or forced
+ * choice), or -1 when it has made none; written to *variant. */
+int ozg_get_tile_variant(ozg_ctx* ctx, int* variant);
 
 /* Kernel launches this library has issued in this process, written to *out (a replay of a
  * captured grouped call counts every kernel it replays).  For launch accounting in benchmarks. */

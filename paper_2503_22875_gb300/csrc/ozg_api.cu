@@ -416,6 +416,15 @@ int ozg_destroy(ozg_ctx* c) {
   c->plan.reset();
   if (c->gws) cudaFree(c->gws);
   if (c->z3ws) cudaFree(c->z3ws);
+  for (ozg_ctx* s : c->hsub) {  // host-memory batch parts
+    cudaStream_t st = s->stream;
+    ozg_destroy(s);
+    if (st) cudaStreamDestroy(st);
+  }
+  for (cudaEvent_t e : c->hev) cudaEventDestroy(e);
+  if (c->h2d) cudaStreamDestroy(c->h2d);
+  if (c->d2h) cudaStreamDestroy(c->d2h);
+  if (c->hstage) cudaFree(c->hstage);
   delete c;
   return OZG_OK;
 }

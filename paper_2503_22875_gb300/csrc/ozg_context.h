@@ -65,6 +65,20 @@ struct ozg_ctx {
   // 3M complex products: the real operands and products
   void* z3ws = nullptr;
   size_t z3ws_cap = 0;
+  // a grouped call whose reports are read after its work finished (host-memory batches)
+  struct DeferredReports {
+    std::vector<int> widx, ws;
+    std::vector<char> wauto;
+    int64_t n = 0;
+    ozg_report* reps = nullptr;
+  } deferred;
+  // grouped calls on host memory: device staging, copy streams and one sub-context per part
+  void* hstage = nullptr;
+  size_t hstage_cap = 0;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  std::vector<ozg_ctx*> hsub;
+  std::vector<cudaEvent_t> hev;  // [2 per part]: inputs staged, part computed
+  int host_parts = 4;
 };
 
 namespace ozg {
@@ -117,6 +131,11 @@ T* gat(ozg_ctx* c, size_t off) {
 // tile variant for one GEMM shape (bit 0: BN = 128, bit 1: deferred pushes): the autotuned
 // choice if known, else the heuristic (least padding; deferral for k >= 2048)
 int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s);
+// grouped calls (ozg_grouped.cu): with sync_reports == false the reports are filled in by
+// grouped_collect_reports once the work has finished
+int grouped_call(ozg_ctx* c, int64_t count, const ozg_gemm_desc* descs, const int* slices, ozg_report* reps,
+                 bool sync_reports);
+int grouped_collect_reports(ozg_ctx* c);
 uint64_t shape_bucket(int64_t rows, int64_t cols, int64_t k, int s);
 void tune_store(ozg_ctx* c, uint64_t bucket, int variant);
 

@@ -520,9 +520,52 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
 
 using namespace ozg::host;
 
-extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc* descs, const int* slices,
-                                 ozg_report* reps) {
+namespace ozg {
+namespace host {
+namespace {
+
+// Per-call reports of the context's current plan: read the flags, selections, escalation skips
+// and sampled errors back from the device (synchronises the stream).
+int read_reports(ozg_ctx* c, int64_t n, const std::vector<int>& widx, const std::vector<int>& ws,
+                 const std::vector<char>& wauto, ozg_report* reps) {
+  GroupPlan* P = c->plan.get();
+  std::vector<int> fl(n), su(n, 0), sk2(n, 1), sk3(n, 1), s2(n, 0);
+  std::vector<double> er(n, NAN), er2(n, NAN), er3(n, NAN);
+  cudaStream_t st = c->stream;
+  OZG_CUDA(cudaMemcpyAsync(fl.data(), gat<int>(c, P->oFlags), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  if (P->nsamp > 0)
+    OZG_CUDA(cudaMemcpyAsync(er.data(), gat<double>(c, P->oErrs), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  if (P->any_auto) {
+    OZG_CUDA(cudaMemcpyAsync(su.data(), gat<int>(c, P->oSused), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    OZG_CUDA(cudaMemcpyAsync(sk2.data(), gat<int>(c, P->oSkip2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    OZG_CUDA(cudaMemcpyAsync(sk3.data(), gat<int>(c, P->oSkip3), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    OZG_CUDA(cudaMemcpyAsync(s2.data(), gat<int>(c, P->oS2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+    OZG_CUDA(cudaMemcpyAsync(er2.data(), gat<double>(c, P->oErrs2), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    OZG_CUDA(cudaMemcpyAsync(er3.data(), gat<double>(c, P->oErrs3), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  }
+  OZG_CUDA(cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < n; ++i) {
+    ozg_report& r = reps[widx[i]];
+    const bool au = P->any_auto && wauto[i];
+    const int runs = (au && !fl[i]) ? (sk2[i] ? 0 : (sk3[i] ? 1 : 2)) : 0;  // escalations
+    r.nonfinite = fl[i];
+    r.selected = au ? su[i] : 0;
+    r.repaired = runs;
+    r.slices_used = fl[i] ? -1 : (au ? (runs == 0 ? su[i] : (runs == 1 ? s2[i] : ws[i])) : ws[i]);
+    r.samples = (P->nsamp > 0 && !fl[i]) ? P->nsamp : 0;
+    r.est_err = r.samples ? (runs == 0 ? er[i] : (runs == 1 ? er2[i] : er3[i])) : NAN;
+  }
+  return OZG_OK;
+}
+
+}  // namespace
+
+// The grouped call.  With sync_reports == false and reps set, the reports are initialised and the
+// call returns once its work is queued; grouped_collect_reports fills them in later.
+int grouped_call(ozg_ctx* c, int64_t count, const ozg_gemm_desc* descs, const int* slices, ozg_report* reps,
+                 bool sync_reports) {
   if (!c || count < 0 || (count > 0 && !descs)) return OZG_ERR_INVALID;
+  c->deferred.reps = nullptr;
   if (count == 0) return OZG_OK;
   if (count > (1 << 20)) return OZG_ERR_UNSUPPORTED;
   std::vector<char> TA(count), TB(count), autom_all(count, 0);
@@ -666,34 +709,30 @@ extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc*
     if (rc) return rc;
   }
   if (reps) {
-    std::vector<int> fl(n), su(n, 0), sk2(n, 1), sk3(n, 1), s2(n, 0);
-    std::vector<double> er(n, NAN), er2(n, NAN), er3(n, NAN);
-    cudaStream_t st = c->stream;
-    OZG_CUDA(cudaMemcpyAsync(fl.data(), gat<int>(c, P->oFlags), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-    if (P->nsamp > 0)
-      OZG_CUDA(cudaMemcpyAsync(er.data(), gat<double>(c, P->oErrs), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    if (P->any_auto) {
-      OZG_CUDA(cudaMemcpyAsync(su.data(), gat<int>(c, P->oSused), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-      OZG_CUDA(cudaMemcpyAsync(sk2.data(), gat<int>(c, P->oSkip2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-      OZG_CUDA(cudaMemcpyAsync(sk3.data(), gat<int>(c, P->oSkip3), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-      OZG_CUDA(cudaMemcpyAsync(s2.data(), gat<int>(c, P->oS2), sizeof(int) * n, cudaMemcpyDeviceToHost, st));
-      OZG_CUDA(cudaMemcpyAsync(er2.data(), gat<double>(c, P->oErrs2), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-      OZG_CUDA(cudaMemcpyAsync(er3.data(), gat<double>(c, P->oErrs3), sizeof(double) * n, cudaMemcpyDeviceToHost, st));
-    }
-    OZG_CUDA(cudaStreamSynchronize(st));
-    for (int64_t i = 0; i < n; ++i) {
-      ozg_report& r = reps[widx[i]];
-      const bool au = P->any_auto && wauto[i];
-      const int runs = (au && !fl[i]) ? (sk2[i] ? 0 : (sk3[i] ? 1 : 2)) : 0;  // escalations
-      r.nonfinite = fl[i];
-      r.selected = au ? su[i] : 0;
-      r.repaired = runs;
-      r.slices_used = fl[i] ? -1 : (au ? (runs == 0 ? su[i] : (runs == 1 ? s2[i] : ws[i])) : ws[i]);
-      r.samples = (P->nsamp > 0 && !fl[i]) ? P->nsamp : 0;
-      r.est_err = r.samples ? (runs == 0 ? er[i] : (runs == 1 ? er2[i] : er3[i])) : NAN;
-    }
+    if (sync_reports) return read_reports(c, n, widx, ws, wauto, reps);
+    c->deferred.widx = widx;
+    c->deferred.ws = ws;
+    c->deferred.wauto = wauto;
+    c->deferred.n = n;
+    c->deferred.reps = reps;
   }
   return OZG_OK;
+}
+
+int grouped_collect_reports(ozg_ctx* c) {
+  if (c->deferred.reps == nullptr) return OZG_OK;
+  ozg_report* reps = c->deferred.reps;
+  c->deferred.reps = nullptr;
+  return read_reports(c, c->deferred.n, c->deferred.widx, c->deferred.ws, c->deferred.wauto, reps);
+}
+
+}  // namespace host
+}  // namespace ozg
+
+extern "C" int ozg_dgemm_grouped(ozg_ctx* c, int64_t count, const ozg_gemm_desc* descs, const int* slices,
+                                 ozg_report* reps) {
+  if (!c) return OZG_ERR_INVALID;
+  return grouped_call(c, count, descs, slices, reps, true);
 }
 
 extern "C" int ozg_set_graphs(ozg_ctx* c, int enable) {
@@ -762,6 +801,12 @@ extern "C" int ozg_set_tile_variant(ozg_ctx* c, int variant) {
   if (variant == ozg::kPairVariant && ozg::pair_max_ctas() < 2) return OZG_ERR_UNSUPPORTED;  // no 2-CTA cluster fits
   c->force_variant = variant;
   c->plan.reset();  // a cached grouped plan may hold another variant
+  return OZG_OK;
+}
+
+extern "C" int ozg_get_tile_variant(ozg_ctx* c, int* variant) {
+  if (!c || !variant) return OZG_ERR_INVALID;
+  *variant = c->plan ? c->plan->variant : -1;
   return OZG_OK;
 }
 

@@ -78,6 +78,8 @@ def load():
     L.ozg_phase_times.argtypes = [vp, vp, vp]
     L.ozg_dgemm_noalloc.argtypes = [ch, ch, i64, i64, i64, dbl, vp, i64, vp, i64, dbl, vp, i64, i32, vp]
     L.ozg_dgemm_grouped.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_dgemm_grouped_host.argtypes = [vp, i64, vp, vp, vp]
+    L.ozg_set_host_parts.argtypes = [vp, i32]
     L.ozg_zgemm3m.argtypes = [vp, ch, ch, i64, i64, i64, vp, vp, i64, vp, i64, vp, vp, i64, i32, vp]
     L.ozg_debug_wait.argtypes = [vp, ctypes.c_longlong]
     L.ozg_debug_fail_allocs.argtypes = [vp, i32]
@@ -93,6 +95,7 @@ def load():
     L.ozg_set_fallback_slices.argtypes = [vp, i32]
     L.ozg_set_autotune.argtypes = [vp, i32, ctypes.c_char_p]
     L.ozg_set_tile_variant.argtypes = [vp, i32]
+    L.ozg_get_tile_variant.argtypes = [vp, ctypes.POINTER(i32)]
     L.ozg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
     L.ozg_debug_group_products.argtypes = [vp, ch, ch, i64, i64, i64, vp, i64, vp, i64, i32, vp]
     _lib = L
@@ -119,6 +122,17 @@ def _p(x) -> int:
         return 0
     if isinstance(x, int):
         return x
+    return int(x.data_ptr())
+
+
+def _hp(x) -> int:
+    """Address of a host buffer: an int, a CPU torch tensor or a numpy array."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
     return int(x.data_ptr())
 
 
@@ -227,6 +241,23 @@ class Context:
         _check(rc, "ozg_dgemm_grouped")
         return list(reps) if report else None
 
+    def dgemm_grouped_host(self, calls, slices=None, report=False):
+        """ozg_dgemm_grouped_host: like dgemm_grouped, but A, B and C are host memory (raw
+        addresses as ints, or CPU tensors / numpy arrays, passed by address).  Synchronous."""
+        n = len(calls)
+        arr = (GemmDesc * n)()
+        for i, c in enumerate(calls):
+            ta, tb, m, nn, k, al, A, lda, B, ldb, be, C, ldc = c
+            arr[i] = GemmDesc(ta.encode(), tb.encode(), b"", m, nn, k, float(al), float(be), _hp(A), lda, _hp(B), ldb,
+                              _hp(C), ldc)
+        sl = (ctypes.c_int * n)(*([0] * n if slices is None else [int(x) for x in slices]))
+        reps = (Report * n)() if report else None
+        _check(load().ozg_dgemm_grouped_host(self._h, n, arr, sl, reps), "ozg_dgemm_grouped_host")
+        return list(reps) if report else None
+
+    def set_host_parts(self, parts: int):
+        _check(load().ozg_set_host_parts(self._h, int(parts)), "ozg_set_host_parts")
+
     def dgemm_regions(self, transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, row_blocks, col_blocks,
                       report=False):
         """C = alpha op(A) op(B) + beta C as row_blocks x col_blocks regions, each with the slice
@@ -253,6 +284,12 @@ class Context:
         """Force tile variant 0..3 (bit 0: 128-wide tiles, bit 1: deferred epilogue pushes), or -1
         for the autotuned / heuristic choice."""
         _check(load().ozg_set_tile_variant(self._h, int(variant)), "ozg_set_tile_variant")
+
+    def tile_variant(self) -> int:
+        """Tile variant of the most recent grouped call (-1: none yet)."""
+        v = ctypes.c_int(-1)
+        _check(load().ozg_get_tile_variant(self._h, ctypes.byref(v)), "ozg_get_tile_variant")
+        return int(v.value)
 
     # ---- learned slice selector
     def load_selector(self, path: str):
