@@ -76,7 +76,8 @@ def parse():
     ap.add_argument("--no-zgemm", action="store_true", help="skip the KKR-like ZGEMM section")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end number")
     ap.add_argument("--no-shim", action="store_true", help="skip the BLAS shim data-strategy section")
-    ap.add_argument("--e2e-parts", type=int, default=E2E_PARTS, help="sub-batches of the pipelined end-to-end number")
+    ap.add_argument("--e2e-parts", type=int, default=E2E_PARTS, help="sub-batches of the device-buffer pipeline")
+    ap.add_argument("--host-parts", type=int, default=HOST_PARTS, help="parts of the host-memory entry point")
     ap.add_argument("--shim-size", type=int, default=8192, help="n of the shim's n^3 DGEMM")
     ap.add_argument("--no-regions", action="store_true", help="skip the region-adaptive slice-count section")
     ap.add_argument("--selector", default="", help="selector model file (default: the package's model)")
@@ -655,7 +656,8 @@ def zgemm_section(ozg, torch, steps):
     return out
 
 
-E2E_PARTS = 4
+E2E_PARTS = 4        # parts of the device-buffer pipeline (cross-step overlap)
+HOST_PARTS = 16      # parts of ozg_dgemm_grouped_host (a synchronous call: fill and drain per step)
 
 
 def e2e_pipelined(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=E2E_PARTS):
@@ -724,7 +726,7 @@ def e2e_pipelined(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=E
             "pipeline": f"{len(parts)} sub-batches, H2D / compute / D2H overlapped on separate streams"}
 
 
-def e2e_host_abi(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=E2E_PARTS):
+def e2e_host_abi(ozg, torch, batch, make_ctx, steps, pg, world, flops, nparts=HOST_PARTS):
     """End to end through the host-memory C ABI: the batch lives in pinned host memory (each
     call's A, B and C back to back in three buffers) and every step is one synchronous
     ozg_dgemm_grouped_host call -- the library copies the inputs in, computes the learned grouped
@@ -882,11 +884,11 @@ def run_gpu(args):
                     "launch_ms = the step's grouped GEMM launches, CUDA events, without the graph")
 
     # end to end through the host-memory C ABI (ozg_dgemm_grouped_host): every step copies the
-    # whole batch host -> device, runs it and copies C back, pipelined in E2E_PARTS parts inside
+    # whole batch host -> device, runs it and copies C back, pipelined in HOST_PARTS parts inside
     # the library; beside it, the same with torch copies into device buffers and the device entry
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_host_abi(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops, args.e2e_parts)
+        e2e = e2e_host_abi(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops, args.host_parts)
         e2e["device_buffer_pipeline"] = e2e_pipelined(ozg, torch, batch, learned_ctx, args.steps, pg, world, flops,
                                                       args.e2e_parts)
     ctx.close()

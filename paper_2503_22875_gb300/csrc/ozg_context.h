@@ -78,7 +78,7 @@ struct ozg_ctx {
   cudaStream_t h2d = nullptr, d2h = nullptr;
   std::vector<ozg_ctx*> hsub;
   std::vector<cudaEvent_t> hev;  // [2 per part]: inputs staged, part computed
-  int host_parts = 4;
+  int host_parts = 16;
 };
 
 namespace ozg {
