@@ -126,7 +126,9 @@ constexpr int kStatsChunks = kStatsK / 16 / kStatsChunk;  // chunks per thread a
 constexpr size_t kStatsHistSmem = (size_t)kStatsChunks * kStatsThreads * (sizeof(short) + kStatsChunk);
 constexpr uint32_t kFastMaxHi = 36u << 20;  // high word of 2^(36 - 1023): smallest fast-path chunk maximum
 static_assert(kStatsK % (16 * kStatsChunk) == 0, "whole chunks");
-static_assert(kStatsK / 16 < 256, "per-thread bin counts fit 8-bit fields");
+// a thread counts at most ceil(k / 16) elements in each of stats_blocks_per_unit(k) blocks of a
+// unit: at most 128 for k <= kStatsK, and 1024 / k * ceil(k / 16) <= 128 below
+static_assert(kStatsK / 16 < 256 && 2 * kStatsBlockElems / 16 < 256, "per-thread bin counts fit 8-bit fields");
 
 extern __shared__ __align__(16) uint8_t stats_smem[];
 
@@ -160,7 +162,7 @@ __device__ __noinline__ uint64_t stats_chunk_exact(const uint64_t* p, int64_t st
 }
 
 template <bool HIST>
-__device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t rb) {
+__device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t unit) {
   __shared__ unsigned long long red[8][16];
   __shared__ unsigned int sh[10];
   __shared__ uint4 onehot[11];  // bin b -> +1 in its 8-bit field of (bins 0-3, 4-7, 8-9); 10: nothing
@@ -178,106 +180,116 @@ __device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t rb) {
   const bool hist = HIST && J.hist != nullptr;
   const bool strided = J.strided != 0;
   const int P = strided ? 16 : 32;
+  const int R = kStatsThreads / P;  // rows per block
   const int r = strided ? (tid & 15) : (tid >> 5);
   const int ph = strided ? (tid >> 4) : (tid & 31);
-  const int64_t row = rb * (kStatsThreads / P) + r;
-  const bool row_ok = row < J.rows;
-  const int n_t = (row_ok && ph < J.k) ? (int)((J.k - 1 - ph) / P + 1) : 0;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int n_t = ph < J.k ? (int)((J.k - 1 - ph) / P + 1) : 0;  // elements of a full row per thread
   const int nch = (n_t + kStatsChunk - 1) / kStatsChunk;
-  const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
-  const uint64_t* p = strided ? X + row + (int64_t)ph * J.ld : X + row * J.ld + ph;
   const int64_t step = strided ? (int64_t)P * J.ld : (int64_t)P;
-  const uint32_t* phi = reinterpret_cast<const uint32_t*>(p) + 1;  // high words (little-endian)
-  uint32_t nx[kStatsChunk];
-  auto load = [&](int c) {
-    const uint32_t* a = phi + 2 * (int64_t)(kStatsChunk * c) * step;
+  const int64_t nrb = (J.rows + R - 1) / R, G = stats_blocks_per_unit(J.k);
+  const int64_t rb_end = min(nrb, (unit + 1) * G);
+  uint32_t c0 = 0, c1 = 0, c2 = 0;  // this thread's 8-bit counts of bins 0-3, 4-7, 8-9 over the unit
+  if (HIST) __syncthreads();  // the shared counters and table are ready before their first use
+  for (int64_t rb = unit * G; rb < rb_end; ++rb) {
+    const int64_t row = rb * R + r;
+    const bool row_ok = row < J.rows;
+    const int nt = row_ok ? n_t : 0;
+    const int nc = row_ok ? nch : 0;
+    const uint64_t* X = reinterpret_cast<const uint64_t*>(J.X);
+    const uint64_t* p = strided ? X + row + (int64_t)ph * J.ld : X + row * J.ld + ph;
+    const uint32_t* phi = reinterpret_cast<const uint32_t*>(p) + 1;  // high words (little-endian)
+    uint32_t nx[kStatsChunk];
+    auto load = [&](int c) {
+      const uint32_t* a = phi + 2 * (int64_t)(kStatsChunk * c) * step;
 #pragma unroll
-    for (int q = 0; q < kStatsChunk; ++q) {
-      nx[q] = kStatsChunk * c + q < n_t ? __ldg(a) : 0u;
-      a += 2 * step;
+      for (int q = 0; q < kStatsChunk; ++q) {
+        nx[q] = kStatsChunk * c + q < nt ? __ldg(a) : 0u;
+        a += 2 * step;
+      }
+    };
+    if (nc > 0) load(0);
+    uint64_t mx = 0;
+    for (int c = 0; c < nc; ++c) {
+      uint32_t h[kStatsChunk];
+#pragma unroll
+      for (int q = 0; q < kStatsChunk; ++q) h[q] = nx[q] & 0x7FFFFFFFu;
+      if (c + 1 < nc) load(c + 1);  // the next chunk's loads fly while this one is processed
+      uint32_t cmh = 0;
+#pragma unroll
+      for (int q = 0; q < kStatsChunk; ++q) cmh = max(cmh, h[q]);
+      if (cmh >= kFastMaxHi) {
+        const uint64_t cm = (uint64_t)cmh << 32;  // same frexp exponent as the chunk maximum
+        mx = cm > mx ? cm : mx;
+        if (hist) {
+          const int ebm = (int)(cmh >> 20);
+          cmx[c * kStatsThreads + tid] = (short)(ebm - 1022);
+#pragma unroll
+          for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) word |= (uint32_t)min(255, ebm - (int)(h[4 * w4 + b] >> 20)) << (8 * b);
+            bytes[(4 * c + w4) * kStatsThreads + tid] = word;
+          }
+        }
+      } else {
+        const uint64_t cm = stats_chunk_exact(p, step, kStatsChunk * c, nt, hist, cmx, bytes, c, tid);
+        mx = cm > mx ? cm : mx;
+      }
     }
-  };
-  if (nch > 0) load(0);
-  uint64_t mx = 0;
-  for (int c = 0; c < nch; ++c) {
-    uint32_t h[kStatsChunk];
+    // row maximum over the P threads of the row
+    uint64_t rmax;
+    if (strided) {
+      const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, 16);  // the warp's two phases of the row
+      mx = o > mx ? o : mx;
+      if (lane < 16) red[warp][lane] = mx;
+      __syncthreads();
+      rmax = 0;
 #pragma unroll
-    for (int q = 0; q < kStatsChunk; ++q) h[q] = nx[q] & 0x7FFFFFFFu;
-    if (c + 1 < nch) load(c + 1);  // the next chunk's loads fly while this one is processed
-    uint32_t cmh = 0;
+      for (int w = 0; w < 8; ++w) rmax = red[w][r] > rmax ? red[w][r] : rmax;
+      __syncthreads();  // every thread has read red before the next block writes it
+    } else {
 #pragma unroll
-    for (int q = 0; q < kStatsChunk; ++q) cmh = max(cmh, h[q]);
-    if (cmh >= kFastMaxHi) {
-      const uint64_t cm = (uint64_t)cmh << 32;  // same frexp exponent as the chunk maximum
-      mx = cm > mx ? cm : mx;
-      if (hist) {
-        const int ebm = (int)(cmh >> 20);
-        cmx[c * kStatsThreads + tid] = (short)(ebm - 1022);
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t t = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = t > mx ? t : mx;
+      }
+      rmax = mx;
+    }
+    if (row_ok && ph == 0) {
+      J.maxbits[row] = rmax;  // the unit holds the whole row: no merge needed
+      if (rmax >= kInfBits) atomicExch(J.nonfinite, 1);
+    }
+    if (hist) {
+      // per byte: bin = min(9, min(255, delta + byte) >> 2), four at a time with byte-SIMD ops;
+      // bytes past the row's end count in the empty bin 10
+      const int e_row = exponent_from_maxbits(rmax);
+      for (int c = 0; c < nc; ++c) {
+        const int delta = min(255, max(0, e_row - (int)cmx[c * kStatsThreads + tid]));
+        const uint32_t d4 = (uint32_t)delta * 0x01010101u;
 #pragma unroll
         for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
-          uint32_t word = 0;
+          const uint32_t g4 = __vaddus4(bytes[(4 * c + w4) * kStatsThreads + tid], d4);
+          const uint32_t b4 = __vminu4((g4 >> 2) & 0x3F3F3F3Fu, 0x09090909u);
 #pragma unroll
-          for (int b = 0; b < 4; ++b) word |= (uint32_t)min(255, ebm - (int)(h[4 * w4 + b] >> 20)) << (8 * b);
-          bytes[(4 * c + w4) * kStatsThreads + tid] = word;
+          for (int b = 0; b < 4; ++b) {
+            const int i = kStatsChunk * c + 4 * w4 + b;
+            const uint4 o = onehot[i < nt ? (int)((b4 >> (8 * b)) & 255u) : 10];
+            c0 += o.x;
+            c1 += o.y;
+            c2 += o.z;
+          }
         }
       }
-    } else {
-      const uint64_t cm = stats_chunk_exact(p, step, kStatsChunk * c, n_t, hist, cmx, bytes, c, tid);
-      mx = cm > mx ? cm : mx;
     }
-  }
-  // row maximum over the P threads of the row
-  const int lane = tid & 31, warp = tid >> 5;
-  uint64_t rmax;
-  if (strided) {
-    const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, 16);  // the warp's two phases of the row
-    mx = o > mx ? o : mx;
-    if (lane < 16) red[warp][lane] = mx;
-    __syncthreads();
-    rmax = 0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) rmax = red[w][r] > rmax ? red[w][r] : rmax;
-  } else {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const uint64_t t = __shfl_xor_sync(0xffffffffu, mx, o);
-      mx = t > mx ? t : mx;
-    }
-    rmax = mx;
-    if (HIST) __syncthreads();  // the shared counters and table are ready before their use below
-  }
-  if (row_ok && ph == 0) {
-    J.maxbits[row] = rmax;  // the unit holds the whole row: no merge needed
-    if (rmax >= kInfBits) atomicExch(J.nonfinite, 1);
   }
   if (!HIST) return;
   if (hist) {
-    // per byte: bin = min(9, min(255, delta + byte) >> 2), four at a time with byte-SIMD ops;
-    // bytes past the row's end count in the empty bin 10
-    const int e_row = exponent_from_maxbits(rmax);
-    uint32_t c0 = 0, c1 = 0, c2 = 0;  // 8-bit counts of bins 0-3, 4-7, 8-9
-    for (int c = 0; c < nch; ++c) {
-      const int delta = min(255, max(0, e_row - (int)cmx[c * kStatsThreads + tid]));
-      const uint32_t d4 = (uint32_t)delta * 0x01010101u;
-#pragma unroll
-      for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
-        const uint32_t g4 = __vaddus4(bytes[(4 * c + w4) * kStatsThreads + tid], d4);
-        const uint32_t b4 = __vminu4((g4 >> 2) & 0x3F3F3F3Fu, 0x09090909u);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int i = kStatsChunk * c + 4 * w4 + b;
-          const uint4 o = onehot[i < n_t ? (int)((b4 >> (8 * b)) & 255u) : 10];
-          c0 += o.x;
-          c1 += o.y;
-          c2 += o.z;
-        }
-      }
-    }
 #pragma unroll
     for (int bin = 0; bin < 10; ++bin) {
       const uint32_t w = bin < 4 ? c0 : (bin < 8 ? c1 : c2);
-      const unsigned s = __reduce_add_sync(0xffffffffu, (w >> (8 * (bin & 3))) & 255u);
-      if (lane == 0 && s) atomicAdd(&sh[bin], s);
+      const unsigned v = __reduce_add_sync(0xffffffffu, (w >> (8 * (bin & 3))) & 255u);
+      if (lane == 0 && v) atomicAdd(&sh[bin], v);
     }
   }
   __syncthreads();
@@ -370,6 +382,44 @@ __global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, con
   if (run != nullptr && *run == 0) return;  // nothing to do in this pass
   for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {
     digits_unit(jobs, units[unit]);
+    __syncthreads();  // the next unit reuses the staging tile
+  }
+}
+
+// Gated digit passes (escalation stages): usually few jobs are re-run, so one CTA first lists
+// the jobs whose gate is open (their unit ranges in the batch's job-major unit table), then the
+// pass walks only those units instead of testing the gate of every unit of the batch.
+__global__ void __launch_bounds__(1024) digits_compact(const SplitArgs* jobs, int njobs, const int64_t* unit_start,
+                                                       const int* run, int* list, int64_t* prefix, int64_t* total) {
+  __shared__ int n_sh;
+  if (threadIdx.x == 0) n_sh = 0;
+  __syncthreads();
+  const bool go = run == nullptr || *run != 0;
+  if (go)
+    for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
+      const int* gate = jobs[j].gate;
+      if ((gate == nullptr || *gate == 0) && unit_start[j + 1] > unit_start[j]) list[atomicAdd(&n_sh, 1)] = j;
+    }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int n = n_sh;
+  int64_t acc = 0;
+  for (int i = 0; i < n; ++i) {
+    prefix[i] = acc;
+    acc += unit_start[list[i] + 1] - unit_start[list[i]];
+  }
+  prefix[n] = acc;
+  total[0] = acc;
+  total[1] = n;
+}
+
+__global__ void __launch_bounds__(256) digits_listed(const SplitArgs* jobs, const int* list, const int64_t* prefix,
+                                                     const int64_t* total) {
+  const int64_t nunits = total[0];
+  const int n = (int)total[1];
+  for (int64_t w = blockIdx.x; w < nunits; w += gridDim.x) {
+    const int li = find_job(prefix, n, w);
+    digits_unit(jobs, make_int2(list[li], (int)(w - prefix[li])));
     __syncthreads();  // the next unit reuses the staging tile
   }
 }
@@ -529,6 +579,14 @@ cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_d
   if (units <= 0) return cudaSuccess;
   const int64_t grid = grid_cap > 0 && units > grid_cap ? grid_cap : units;
   { digits_batched<<<(unsigned)grid, 256, 0, st>>>(jobs_dev, units_dev, units, run); note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_digits_gated(const SplitArgs* jobs_dev, int njobs, const int64_t* unit_start_dev, const int* run,
+                                int* list_dev, int64_t* prefix_dev, int64_t* total_dev, int grid, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  { digits_compact<<<1, 1024, 0, st>>>(jobs_dev, njobs, unit_start_dev, run, list_dev, prefix_dev, total_dev); note_launch(); }
+  { digits_listed<<<grid, 256, 0, st>>>(jobs_dev, list_dev, prefix_dev, total_dev); note_launch(); }
   return cudaGetLastError();
 }
 

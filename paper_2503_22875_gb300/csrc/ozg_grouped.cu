@@ -34,6 +34,8 @@ struct GroupPlan {
   // escalation stages 2 (min(s + 2, fallback)) and 3 (the fallback) of rejected learned calls
   size_t oCalls2 = 0, oChecks2 = 0, oErrs2 = 0, oSkip2 = 0, oJobs2 = 0, oCounter = 0;
   size_t oCalls3 = 0, oChecks3 = 0, oErrs3 = 0, oSkip3 = 0, oJobs3 = 0, oRep2 = 0, oS2 = 0;
+  // gated digit passes: per-job starts in the digit unit table, and the device-built job list
+  size_t oDgStart = 0, oDgList = 0, oDgPre = 0, oDgTot = 0;
   std::vector<char> autom;
 };
 
@@ -140,8 +142,9 @@ int enqueue(ozg_ctx* c, const GroupPlan& P) {
       OZG_CUDA(launch_repair_prep_batched(gat<RepairJob>(c, S.rep), P.ncalls, c->target, ctr + S.ctr + 1, st));
       OZG_CUDA(launch_save_restore_batched(gat<RepairJob>(c, S.rep), gat<int64_t>(c, P.oSavePre), P.save_units,
                                            P.ncalls, 1, st));
-      OZG_CUDA(launch_digits_batched(gat<SplitArgs>(c, S.jobs), gat<int2>(c, P.oDgTab), P.digit_units,
-                                     ctr + S.ctr + 1, 8 * c->num_sms, st));
+      OZG_CUDA(launch_digits_gated(gat<SplitArgs>(c, S.jobs), P.njobs, gat<int64_t>(c, P.oDgStart), ctr + S.ctr + 1,
+                                   gat<int>(c, P.oDgList), gat<int64_t>(c, P.oDgPre), gat<int64_t>(c, P.oDgTot),
+                                   8 * c->num_sms, st));
       GroupArgs gs = g;
       gs.calls = gat<GroupCall>(c, S.calls);
       gs.tile_counter = ctr + S.ctr;
@@ -226,6 +229,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
   // work-unit tables of the batched split (job j = 2i for A, 2i + 1 for B of call i): fused
   // statistics units for jobs whose rows fit one, two-pass row-maximum units for the others
   std::vector<int2> rmtab, dgtab, sttab;
+  std::vector<int64_t> dgstart(2 * count + 1, 0);  // job j's digit units: [dgstart[j], dgstart[j + 1])
   for (int64_t i = 0; i < count; ++i)
     for (int side = 0; side < 2; ++side) {
       SplitArgs x;
@@ -239,6 +243,7 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
         for (int64_t u = 0, nu = rowmax_units_of(x); u < nu; ++u) rmtab.push_back(make_int2(job, (int)u));
       }
       for (int64_t u = 0, nu = digit_units_of(x); u < nu; ++u) dgtab.push_back(make_int2(job, (int)u));
+      dgstart[job + 1] = (int64_t)dgtab.size();
     }
   P->oRmTab = cv.take(sizeof(int2) * std::max<size_t>(rmtab.size(), 1));
   P->oDgTab = cv.take(sizeof(int2) * std::max<size_t>(dgtab.size(), 1));
@@ -276,6 +281,10 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
     P->oJobs3 = cv.take(sizeof(SplitArgs) * 2 * count);
     P->oRep2 = cv.take(sizeof(RepairJob) * count);
     P->oS2 = cv.take(sizeof(int) * count);
+    P->oDgStart = cv.take(sizeof(int64_t) * (2 * count + 1));
+    P->oDgList = cv.take(sizeof(int) * 2 * count);
+    P->oDgPre = cv.take(sizeof(int64_t) * (2 * count + 1));
+    P->oDgTot = cv.take(sizeof(int64_t) * 2);
     for (int64_t i = 0; i < count; ++i) {
       const bool sv = autom[i] && d[i].beta != 0.0;
       sp[i + 1] = sp[i] + (sv ? (d[i].m * d[i].n + 255) / 256 : 0);
@@ -505,6 +514,8 @@ int build_plan(ozg_ctx* c, int64_t count, const ozg_gemm_desc* d, const std::vec
                              cudaMemcpyHostToDevice, st));
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oRep2), rep2.data(), sizeof(RepairJob) * count, cudaMemcpyHostToDevice,
                              st));
+    OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oDgStart), dgstart.data(), sizeof(int64_t) * dgstart.size(),
+                             cudaMemcpyHostToDevice, st));
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oCalls3), calls3.data(), sizeof(GroupCall) * count,
                              cudaMemcpyHostToDevice, st));
     OZG_CUDA(cudaMemcpyAsync(gat<void>(c, P->oChecks3), chk3.data(), sizeof(CheckArgs) * count,

@@ -176,8 +176,18 @@ constexpr int kRmStridedK = 128, kRmContigK = 1024, kDgK = 64;
 // Fused statistics units hold whole rows of real jobs with k <= kStatsK: 16 rows of a strided job,
 // 8 rows of a contiguous one.  Longer (or complex) jobs take the two-pass row-maximum units.
 constexpr int64_t kStatsK = 2048;
+// Short rows: one unit takes several consecutive row blocks (about kStatsBlockElems elements per
+// row of the unit), so a CTA's fixed costs (job lookup, reductions, histogram flush) are shared.
+constexpr int64_t kStatsBlockElems = 1024;
+__host__ __device__ inline int64_t stats_blocks_per_unit(int64_t k) {
+  return k >= kStatsBlockElems ? 1 : kStatsBlockElems / (k > 0 ? k : 1);
+}
 inline bool stats_fused(const SplitArgs& x) { return !x.cplx && x.k >= 1 && x.k <= kStatsK; }
-inline int64_t stats_units_of(const SplitArgs& x) { return x.strided ? (x.rows + 15) / 16 : (x.rows + 7) / 8; }
+inline int64_t stats_units_of(const SplitArgs& x) {
+  const int64_t blocks = x.strided ? (x.rows + 15) / 16 : (x.rows + 7) / 8;
+  const int64_t g = stats_blocks_per_unit(x.k);
+  return (blocks + g - 1) / g;
+}
 inline int64_t rowmax_units_of(const SplitArgs& x) {
   return x.strided ? ((x.rows + 31) / 32) * ((x.k + kRmStridedK - 1) / kRmStridedK)
                    : ((x.rows + 7) / 8) * ((x.k + kRmContigK - 1) / kRmContigK);
@@ -196,6 +206,12 @@ cudaError_t launch_stats_pair(const SplitArgs& a, const SplitArgs& b, cudaStream
 // run: if non-null and *run == 0 the launch does nothing; grid_cap > 0 bounds the grid (grid-stride)
 cudaError_t launch_digits_batched(const SplitArgs* jobs_dev, const int2* units_dev, int64_t units, const int* run,
                                   int grid_cap, cudaStream_t st);
+// Gated digit pass of an escalation stage: the jobs whose gate is open (unit_start: njobs + 1
+// entries, job j's units at [unit_start[j], unit_start[j+1]) of the job-major unit table) are
+// listed on the device (list, prefix, total: njobs, njobs + 1 and 2 entries of scratch), then only
+// their units are processed; nothing when *run == 0.
+cudaError_t launch_digits_gated(const SplitArgs* jobs_dev, int njobs, const int64_t* unit_start_dev, const int* run,
+                                int* list_dev, int64_t* prefix_dev, int64_t* total_dev, int grid, cudaStream_t st);
 // Grouped automatic calls, check-driven escalation: after the check of a stage, a call is re-run
 // in the next stage (*skip_next = 0, else 1) when it is automatic, finite, ran in this stage
 // (ran == nullptr or *ran == 0), its sampled error is above the target and its count *s_cur is

@@ -43,10 +43,12 @@ def test_features_match_oracle(ozg, ta, tb, phi):
 
 
 @pytest.mark.parametrize("ta,tb,m,n,k", [("N", "N", 1, 1, 1), ("N", "N", 17, 9, 2048), ("T", "T", 33, 65, 2049),
-                                         ("N", "T", 200, 3, 17), ("T", "N", 16, 8, 1500)])
+                                         ("N", "T", 200, 3, 17), ("T", "N", 16, 8, 1500), ("N", "N", 1000, 700, 100),
+                                         ("T", "T", 999, 333, 37)])
 def test_features_edges_match_oracle(ozg, ta, tb, m, n, k):
     """Rows of k <= 2048 take the fused statistics kernel (row maxima and gap histogram in one
-    read, whole rows per CTA), longer rows the two-pass kernels: ragged row blocks, an all-zero
+    read, whole rows per CTA; short rows several row blocks per CTA, the last unit partial),
+    longer rows the two-pass kernels: ragged row blocks, an all-zero
     row, runs of zeros longer than a 16-element chunk, subnormal entries, a row scaled below
     2^-987 (whose chunks take the kernel's exact path) and gaps across the 36-exponent edge all
     give the oracle's histogram counts exactly."""
