@@ -173,5 +173,9 @@ def test_threshold_choice_minimises_expected_work():
     best, table = S.choose_threshold(probs, s_min, work, 13)
     costs = {t: v["cost"] for t, v in table.items()}
     assert costs[best] == min(costs.values())
-    # at thr <= 0.92 every GEMM runs at s = 7 and one re-runs at 13; above, all run at s = 8
-    assert table[0.9]["cost"] == 4 * 28 + 91 and table[0.95]["cost"] == 4 * 36
+    # at thr <= 0.92 every GEMM runs at s = 7 and the one that needs 8 is rejected by the check
+    # and re-runs at s + 2 = 9 (45 products); above, all run at s = 8
+    assert table[0.9]["cost"] == 4 * 28 + 45 and table[0.95]["cost"] == 4 * 36
+    # with a fallback of 8 the re-run stops at the fallback (36 products)
+    _, table8 = S.choose_threshold(probs, s_min, work, 8)
+    assert table8[0.9]["cost"] == 4 * 28 + 36
