@@ -268,9 +268,14 @@ int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
  * costs for short k); for 128 x 128 tiles, stage one 64-wide k slice per pipeline stage in 6
  * stages instead of two in 3 (deeper prefetch, more issue overhead).  Variant 4: grouped calls
  * run on CTA pairs (2-CTA clusters sharing one tcgen05 MMA of 256 x 128 tiles; each CTA stages
- * its own 128 rows of A and half of B); single calls run it as variant 1.  All variants give
- * bit-identical C. */
-#define OZG_NUM_TILE_VARIANTS 5
+ * its own 128 rows of A and half of B); single calls run it as variant 1.  Variant 5: 128 x 128
+ * tiles over which the slice groups are taken two at a time (groups g and g + 1 share their
+ * digit planes: one pass loads A_1..A_g and B_1..B_g once and issues one N = 256 MMA per plane
+ * pair), up to 16 slices; a call with more slices, the exact epilogue or the group-product
+ * export runs as variant 1.  All variants give bit-identical C while the exact sum needs at most
+ * two int64 windows (s <= 10 at any k); beyond that the FP64 continuation may round differently
+ * in the last bits between the 256- and 128-wide families. */
+#define OZG_NUM_TILE_VARIANTS 6
 
 /* Tile-variant autotuner: enable != 0 times the four variants the first time a shape bucket
  * (rounded log2 of m, n, k and the slice count; variants 0..3) or a grouped batch (every variant)
@@ -282,7 +287,7 @@ int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
  * k slices per stage. */
 int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
 
-/* Force tile variant 0..4 for every later call (single and grouped), or -1 (default) for the
+/* Force tile variant 0..5 for every later call (single and grouped), or -1 (default) for the
  * autotuned / heuristic choice.  Returns OZG_ERR_INVALID for other values, OZG_ERR_UNSUPPORTED
  * for variant 4 when no 2-CTA cluster of the kernel fits on the device. */
 int ozg_set_tile_variant(ozg_ctx* ctx, int variant);

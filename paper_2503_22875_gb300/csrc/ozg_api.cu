@@ -171,10 +171,11 @@ int emu_gemm(ozg_ctx* c, bool cplx, char ta, char tb, int64_t m, int64_t n, int6
   if (c->autotune && c->force_variant < 0 && !Gdbg && ga.beta_zero && !autos) {
     const uint64_t bucket = shape_bucket(prA, prB, k, s);
     if (c->tune.find(bucket) == c->tune.end()) {
-      // time the four variants (two widths x stage shape or deferred pushes) on this call (C
-      // is write-only here and every variant gives the same bits)
+      // time the 1-CTA variants (two widths x stage shape or deferred pushes, and the stacked
+      // group pairs) on this call (C is write-only here and every variant gives the same bits)
       float best = 1e30f;
-      for (int v = 0; v < 4; ++v) {
+      for (int v : {0, 1, 2, 3, ozg::kStackedVariant}) {
+        if (v == ozg::kStackedVariant && (s > ozg::stacked_max_slices() || c->exact)) continue;
         ozg::GemmArgs gt = ga;
         gt.variant = v;
         gt.defer = ozg::variant_defers(v);

@@ -278,6 +278,10 @@ __device__ __forceinline__ void prefetch_close(const PushArgs& a, const TileJob&
 }
 
 template <int NCH, bool TMR, bool PRE = false>
+__device__ __forceinline__ void window_out(const long long* rw, int o0, const PushArgs& a, const TileJob& j,
+                                           const long long* s0_pre, const int* fe_pre);
+
+template <int NCH, bool TMR, bool PRE = false>
 __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushArgs& a, const TileJob& j,
                                            const long long* s0_pre = nullptr, const int* fe_pre = nullptr) {
   static_assert(!TMR || NCH == 16, "TMEM chunks are 32 columns");
@@ -311,6 +315,15 @@ __device__ __forceinline__ void push_chunk(const int* vals, int o0, const PushAr
 #pragma unroll
     for (int i = 0; i < NCH; ++i) rw[i] = vv[i];
   }
+  window_out<NCH, TMR, PRE>(rw, o0, a, j, s0_pre, fe_pre);
+}
+
+// The part of a push after the window value: store the active window (plain), spill the first
+// window (spill), close a later window into the FP64 partial (close), or round and write C
+// (final), for outputs o0 .. o0+NCH-1 whose window values are rw.
+template <int NCH, bool TMR, bool PRE>
+__device__ __forceinline__ void window_out(const long long* rw, int o0, const PushArgs& a, const TileJob& j,
+                                           const long long* s0_pre, const int* fe_pre) {
   if (a.kind == kPlain) {
     if (TMR) {
       uint32_t t[32];
@@ -946,6 +959,404 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
   }
 }
 
+// ------------------------------------------------------------------------ stacked group pairs
+// Variant 5 (128 x 128 output tiles): the groups are taken two at a time.  For groups g and
+// g + 1 every plane pair shares a plane with a neighbour: A_p meets B_{g-p} (group g) and
+// B_{g+1-p} (group g + 1).  So one k sub-tile of a pass loads A_1 .. A_g and B_g .. B_1 once
+// each and issues, for p = 1 .. g - 1, one N = 256 MMA whose B operand is the two consecutive
+// B tiles [B_{g+1-p}; B_{g-p}] -- accumulator columns 0 .. 127 collect group g + 1, columns
+// 128 .. 255 group g -- and, for p = g, an N = 128 MMA (A_g B_1, group g + 1).  Against the
+// one-group schedule this halves the shared-memory fill (L2 -> SM bytes) and the MMA
+// instructions per product.  The stage ring holds one A and one B sub-tile (64 k) per entry;
+// a B tile is used by its own stage and the next, so the commit after a stage frees the entry
+// of the stage before it.  Where the two B tiles straddle the end of the ring the MMA is issued
+// as two N = 128 halves.  A window with an odd number of groups starts with a lone group
+// (one N = 128 MMA per plane pair, into columns 128 .. 255).
+//
+// The two 256-column accumulators fill TMEM, so the int64 windows live in the epilogue's
+// registers, and every drained chain is added into them directly: the window is linear in the
+// group sums, W = sum_g 128^(gend - g) G_g, and a chain of groups g, g + 1 adds
+// 128^(gend - g - 1) (128 c_g + c_{g+1}) exactly.  A chain covers whole k sweeps, at most
+// 1024 products in each accumulator column.
+namespace stk {
+constexpr int NE = 6;                      // stage ring entries
+constexpr uint32_t SLOT = BM * BK * 2;     // one 128-row x 64-k fp16 sub-tile (16 KB, one TMA box)
+constexpr uint32_t A_OFF = 0, B_OFF = NE * SLOT;
+constexpr size_t SMEM = (size_t)2 * NE * SLOT + 1024;
+constexpr uint32_t IDESC2 = umma_idesc_f16_f32(BM, 256), IDESC1 = umma_idesc_f16_f32(BM, 128);
+constexpr int CHAIN_STAGES = CHAIN_K / BK;  // 64-k MMA stages per accumulator column and chain
+constexpr int MAX_S = CHAIN_STAGES;          // a two-group sweep of g stages must fit one chain
+constexpr int NOUT = 64;                     // outputs per epilogue thread (real; complex: 32)
+static_assert(SMEM <= 227 * 1024, "stage ring");
+}  // namespace stk
+
+// Pass q of the window [wstart, wstart + wlen): the groups ga, ga + 1, or the lone group ga
+// (first pass of a window with an odd count).
+__device__ __forceinline__ void stk_pass(int wstart, int wlen, int q, int& ga, bool& two) {
+  if (wlen & 1) {
+    two = q > 0;
+    ga = q == 0 ? wstart : wstart + 1 + 2 * (q - 1);
+  } else {
+    two = true;
+    ga = wstart + 2 * q;
+  }
+}
+// k sweeps per chain: a sweep adds ga (two groups) or ga - 1 (lone group) 64-k MMA stages to
+// the accumulator columns that collect the most
+__device__ __forceinline__ int stk_sweeps(int ga, bool two) { return stk::CHAIN_STAGES / (two ? ga : ga - 1); }
+
+template <bool GROUPED>
+__device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUtensorMap* tmB0, const GemmArgs* P,
+                                             const GroupArgs* G) {
+  using namespace stk;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_full[NE], bar_empty[NE], bar_accf[2], bar_acce[2], bar_done;
+  __shared__ __align__(8) uint64_t bar_tfull[TRING], bar_tempty[TRING];
+  __shared__ int tile_ring[TRING];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+
+  int* status = GROUPED ? G->status : P->status;
+  double* Rws = GROUPED ? G->Rws : P->Rws;
+  const int ntiles = GROUPED ? G->ntiles : (int)(((P->rows + BM - 1) / BM) * ((P->cols + 127) / 128));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NE; ++i) {
+      mbar_init(&bar_full[i], 1);
+      mbar_init(&bar_empty[i], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_accf[b], 1);
+      mbar_init(&bar_acce[b], EPI_WARPS);
+    }
+    mbar_init(&bar_done, 1);
+    for (int i = 0; i < TRING; ++i) {
+      mbar_init(&bar_tfull[i], 1);
+      mbar_init(&bar_tempty[i], 1 + EPI_WARPS);
+    }
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (!GROUPED && warp == 0 && lane == 0) {
+    tma_prefetch_desc(tmA0);
+    tma_prefetch_desc(tmB0);
+  }
+  if (warp == 1) tmem_alloc(&tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* abort_p = &abort_flag;
+
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_PRODUCER));
+    if (warp == 0) {
+      // ---------------------------------------------------------------- TMA producer
+      if (lane == 0) {
+        uint32_t e = 0, eph = 0;
+        long long issued = 0;
+        const CUtensorMap* last_map = nullptr;
+        uint32_t tslot = 0, tphase = 0;
+        int tnext = blockIdx.x;
+        for (;;) {
+          int t;
+          if (GROUPED) {
+            if (!mbar_wait(&bar_tempty[tslot], tphase ^ 1, abort_p, status)) goto producer_done;
+            t = tnext < ntiles ? tnext : -1;
+            tile_ring[tslot] = t;
+            mbar_arrive(&bar_tfull[tslot]);
+            if (++tslot == TRING) {
+              tslot = 0;
+              tphase ^= 1;
+            }
+            if (t >= 0) tnext = (int)gridDim.x + atomicAdd(G->tile_counter, 1);
+          } else {
+            t = tnext < ntiles ? tnext : -1;
+            tnext += gridDim.x;
+          }
+          if (t < 0) break;
+          const TileJob j = get_job<128, 2, GROUPED>(t, tmA0, tmB0, P, G);
+          if (j.skip) continue;
+          if (GROUPED && j.tmA != last_map) {
+            tensormap_acquire(j.tmA);
+            tensormap_acquire(j.tmB);
+            last_map = j.tmA;
+          }
+          const int KB = (j.KB - 1) * 2 + j.klast;  // 64-wide k sub-tiles
+          const int arow = j.tm * BM, brow = j.tn * 128;
+          const int win = window_len(j.s, (int64_t)j.KB * 128, j.cplx);
+          int pc = 0;
+          for (int wstart = 2; wstart <= j.s + 1; wstart += win) {
+            const int wlen = min(win, j.s + 2 - wstart);
+            for (int q = 0; q < (wlen + 1) / 2; ++q, ++pc) {
+              int ga;
+              bool two;
+              stk_pass(wstart, wlen, q, ga, two);
+              for (int kbi = 0; kbi < KB; ++kbi) {
+                const int kb = (pc & 1) ? KB - 1 - kbi : kbi;  // snake: a pass starts where the last ended
+                // stage i: A_i (i >= 1) and B_{ga-i} (i <= ga - 1); a lone group has no stage 0
+                for (int i = two ? 0 : 1; i <= (two ? ga : ga - 1); ++i) {
+                  if (!mbar_wait(&bar_empty[e], eph ^ 1, abort_p, status)) goto producer_done;
+                  const bool hasA = i >= 1, hasB = i <= ga - 1;
+                  mbar_arrive_expect_tx(&bar_full[e], (hasA ? SLOT : 0u) + (hasB ? SLOT : 0u));
+                  if (hasA) tma_load_3d(j.tmA, &bar_full[e], smem + A_OFF + e * SLOT, kb * BK, arow, i - 1);
+                  if (hasB) tma_load_3d(j.tmB, &bar_full[e], smem + B_OFF + e * SLOT, kb * BK, brow, ga - i - 1);
+                  ++issued;
+                  if (++e == NE) {
+                    e = 0;
+                    eph ^= 1;
+                  }
+                }
+              }
+            }
+          }
+        }
+      producer_done:
+        if (*abort_p) {
+          uint32_t st = e, ph = eph;
+          for (long long i = 0; i < NE && i < issued; ++i) {
+            if (st == 0) {
+              st = NE - 1;
+              ph ^= 1;
+            } else {
+              --st;
+            }
+            drain_wait(&bar_full[st], ph);
+          }
+        }
+      }
+    } else if (warp == 1) {
+      // ---------------------------------------------------------------- MMA issuer
+      if (lane == 0) {
+        uint32_t e = 0, eph = 0;
+        int eprev = -1;  // ring entry of the previous stage (freed by the next commit)
+        uint32_t acc_par = 0;
+        int buf = 0;
+        uint32_t tslot = 0, tphase = 0;
+        int tnext = blockIdx.x;
+        for (;;) {
+          int t;
+          if (GROUPED) {
+            if (!mbar_wait(&bar_tfull[tslot], tphase, abort_p, status)) goto mma_done;
+            t = tile_ring[tslot];
+            mbar_arrive(&bar_tempty[tslot]);
+            if (++tslot == TRING) {
+              tslot = 0;
+              tphase ^= 1;
+            }
+          } else {
+            t = tnext < ntiles ? tnext : -1;
+            tnext += gridDim.x;
+          }
+          if (t < 0) break;
+          const TileJob j = get_job<128, 2, GROUPED>(t, tmA0, tmB0, P, G);
+          if (j.skip) continue;
+          const int KB = (j.KB - 1) * 2 + j.klast;
+          const int win = window_len(j.s, (int64_t)j.KB * 128, j.cplx);
+          for (int wstart = 2; wstart <= j.s + 1; wstart += win) {
+            const int wlen = min(win, j.s + 2 - wstart);
+            for (int q = 0; q < (wlen + 1) / 2; ++q) {
+              int ga;
+              bool two;
+              stk_pass(wstart, wlen, q, ga, two);
+              const int spc = stk_sweeps(ga, two);
+              bool fresh = false;  // the next MMA starts a chain (overwrites the accumulator)
+              for (int kbi = 0; kbi < KB; ++kbi) {
+                if (kbi % spc == 0) {
+                  if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, status)) goto mma_done;
+                  tc_fence_after();
+                  fresh = true;
+                }
+                const uint32_t dt = tmem + (uint32_t)(buf * 256);
+                for (int i = two ? 0 : 1; i <= (two ? ga : ga - 1); ++i) {
+                  if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
+                  tc_fence_after();
+                  const uint64_t da = umma_desc_sw128(smem + A_OFF + e * SLOT);
+                  const uint64_t db = umma_desc_sw128(smem + B_OFF + e * SLOT);
+                  if (!two) {
+                    // lone group: A_i B_{ga-i} into columns 128 .. 255
+#pragma unroll
+                    for (int k16 = 0; k16 < BK / 16; ++k16)
+                      umma_f16(dt + 128, da + (uint64_t)(2 * k16), db + (uint64_t)(2 * k16), IDESC1,
+                               (fresh && k16 == 0) ? 0u : 1u);
+                    fresh = false;
+                  } else if (i >= 1) {
+                    const uint64_t dbp = umma_desc_sw128(smem + B_OFF + (uint32_t)eprev * SLOT);
+                    if (i == ga) {
+                      // A_ga B_1 (group ga + 1 only): columns 0 .. 127
+#pragma unroll
+                      for (int k16 = 0; k16 < BK / 16; ++k16)
+                        umma_f16(dt, da + (uint64_t)(2 * k16), dbp + (uint64_t)(2 * k16), IDESC1,
+                                 (fresh && k16 == 0) ? 0u : 1u);
+                    } else if (eprev + 1 == (int)e) {
+                      // [B_{ga+1-i}; B_{ga-i}] are adjacent slots: one N = 256 operand
+#pragma unroll
+                      for (int k16 = 0; k16 < BK / 16; ++k16)
+                        umma_f16(dt, da + (uint64_t)(2 * k16), dbp + (uint64_t)(2 * k16), IDESC2,
+                                 (fresh && k16 == 0) ? 0u : 1u);
+                    } else {
+                      // the pair straddles the end of the ring: two N = 128 halves
+#pragma unroll
+                      for (int k16 = 0; k16 < BK / 16; ++k16) {
+                        umma_f16(dt, da + (uint64_t)(2 * k16), dbp + (uint64_t)(2 * k16), IDESC1,
+                                 (fresh && k16 == 0) ? 0u : 1u);
+                        umma_f16(dt + 128, da + (uint64_t)(2 * k16), db + (uint64_t)(2 * k16), IDESC1,
+                                 (fresh && k16 == 0) ? 0u : 1u);
+                      }
+                    }
+                    fresh = false;
+                  }
+                  // the previous stage's entry (its A used there, its B last used here) is free
+                  if (eprev >= 0) umma_commit(&bar_empty[eprev]);
+                  eprev = (int)e;
+                  if (++e == NE) {
+                    e = 0;
+                    eph ^= 1;
+                  }
+                }
+                if ((kbi + 1) % spc == 0 || kbi == KB - 1) {
+                  umma_commit(&bar_accf[buf]);
+                  acc_par ^= 1u << buf;
+                  buf ^= 1;
+                }
+              }
+            }
+          }
+        }
+      mma_done:
+        umma_commit(&bar_done);
+        drain_wait(&bar_done, 0);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_EPILOGUE));
+    const int ew = warp - 4;
+    const int quad = warp & 3;
+    const int chalf = ew >> 2;
+    const int r = quad * 32 + lane;
+    uint32_t acc_par = 0;
+    int buf = 0;
+    double* Rbase = Rws + (size_t)blockIdx.x * BM * 128 * 2;
+    const bool odd = (lane & 1) != 0;
+    uint32_t tslot = 0, tphase = 0;
+    int tnext = blockIdx.x;
+    for (;;) {
+      int t;
+      if (GROUPED) {
+        if (!mbar_wait(&bar_tfull[tslot], tphase, abort_p, status)) goto epi_done;
+        t = tile_ring[tslot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_tempty[tslot]);
+        if (++tslot == TRING) {
+          tslot = 0;
+          tphase ^= 1;
+        }
+      } else {
+        t = tnext < ntiles ? tnext : -1;
+        tnext += gridDim.x;
+      }
+      if (t < 0) break;
+      const TileJob j = get_job<128, 2, GROUPED>(t, tmA0, tmB0, P, G);
+      if (j.skip) continue;
+      const int s = j.s;
+      const int KB = (j.KB - 1) * 2 + j.klast;
+      const int64_t grow = (int64_t)j.tm * BM + r;
+      const bool row_ok = grow < j.rows;
+      const int64_t orow = j.cplx ? (grow >> 1) : grow;
+      const int e_row = (row_ok && j.e != nullptr) ? j.e[orow] : 0;
+      const int win = window_len(s, (int64_t)j.KB * 128, j.cplx);
+      const int nout = j.cplx ? NOUT / 2 : NOUT;
+      PushArgs pa;
+      pa.S0 = reinterpret_cast<long long*>(Rbase) + (size_t)(j.cplx ? chalf * NOUT / 2 : chalf * NOUT) * BM + r;
+      pa.gcol0 = (int64_t)j.tn * 128 + chalf * NOUT;
+      pa.orow = orow;
+      pa.row_ok = row_ok;
+      pa.unit_ab = j.beta_zero && j.a0 == 1.0 && j.a1 == 0.0;
+      pa.odd = odd;
+      pa.ebase = e_row - 7 * (s + 1);
+      const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(chalf * NOUT);
+      int widx = 0;
+      for (int wstart = 2; wstart <= s + 1; wstart += win, ++widx) {
+        const int wlen = min(win, s + 2 - wstart);
+        const int gend = wstart + wlen - 1;
+        long long W[NOUT];
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) W[c] = 0;
+        for (int q = 0; q < (wlen + 1) / 2; ++q) {
+          int ga;
+          bool two;
+          stk_pass(wstart, wlen, q, ga, two);
+          const int spc = stk_sweeps(ga, two);
+          const int nch = (KB + spc - 1) / spc;
+          const int sh = 7 * (gend - ga - (two ? 1 : 0));
+          for (int ch = 0; ch < nch; ++ch) {
+            if (!mbar_wait(&bar_accf[buf], (acc_par >> buf) & 1, abort_p, status)) goto epi_done;
+            tc_fence_after();
+            const uint32_t ta = tl + (uint32_t)(buf * 256);
+#pragma unroll
+            for (int cc = 0; cc < NOUT / 16; ++cc) {
+              uint32_t h1[16], h0[16];
+              tmem_ld16(ta + 128 + cc * 16, h1);  // group ga
+              if (two) tmem_ld16(ta + cc * 16, h0);  // group ga + 1
+              tmem_ld_wait();
+              if (!j.cplx) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const long long v1 = __float2int_rn(__uint_as_float(h1[i]));
+                  const long long v = two ? v1 * 128 + __float2int_rn(__uint_as_float(h0[i])) : v1;
+                  W[cc * 16 + i] += (long long)((unsigned long long)v << sh);
+                }
+              } else {
+                // (Re, Im) of 8 outputs: even lanes Re = P_rr - P_ii, odd lanes Im = P_ir + P_ri
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  const int a1 = __float2int_rn(__uint_as_float(h1[2 * i]));
+                  const int b1 = __shfl_xor_sync(0xffffffffu, __float2int_rn(__uint_as_float(h1[2 * i + 1])), 1);
+                  const long long v1 = odd ? (long long)a1 + b1 : (long long)a1 - b1;
+                  long long v = v1;
+                  if (two) {
+                    const int a0 = __float2int_rn(__uint_as_float(h0[2 * i]));
+                    const int b0 = __shfl_xor_sync(0xffffffffu, __float2int_rn(__uint_as_float(h0[2 * i + 1])), 1);
+                    v = v1 * 128 + (odd ? (long long)a0 + b0 : (long long)a0 - b0);
+                  }
+                  W[cc * 8 + i] += (long long)((unsigned long long)v << sh);
+                }
+              }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_acce[buf]);
+            acc_par ^= 1u << buf;
+            buf ^= 1;
+          }
+        }
+        // the window is complete: spill the first one, close a later one into the FP64
+        // partial, or round the last one and write C (chunks of 8 outputs, the array rotated
+        // after each so every index stays a compile-time constant)
+        pa.widx = widx;
+        pa.wlen = wlen;
+        pa.kind = gend == s + 1 ? kFinal : widx == 0 ? kSpill : kClose;
+#pragma unroll 1
+        for (int o = 0; o < nout; o += 8) {
+          window_out<8, false>(W, o, pa, j, nullptr, nullptr);
+#pragma unroll
+          for (int c = 0; c < NOUT - 8; ++c) W[c] = W[c + 8];
+        }
+      }
+    }
+  epi_done:;
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 template <int BN_, int SUB_>
 __global__ void __launch_bounds__(THREADS, 1)
     slice_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -965,6 +1376,18 @@ __global__ void __launch_bounds__(THREADS, 1) slice_gemm_grouped_kernel(const Gr
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1) slice_gemm_pair_kernel(const GroupArgs G) {
   if (G.run != nullptr && *G.run == 0) return;
   gemm_body<128, 2, true, true>(nullptr, nullptr, nullptr, &G);
+}
+
+// Stacked group pairs (variant 5), one GEMM or a grouped list of tiles.
+__global__ void __launch_bounds__(THREADS, 1)
+    slice_gemm_stacked_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                              const GemmArgs P) {
+  if (P.nonfinite != nullptr && *P.nonfinite) return;
+  stacked_body<false>(&tmA, &tmB, &P, nullptr);
+}
+__global__ void __launch_bounds__(THREADS, 1) slice_gemm_grouped_stacked_kernel(const GroupArgs G) {
+  if (G.run != nullptr && *G.run == 0) return;
+  stacked_body<true>(nullptr, nullptr, nullptr, &G);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -998,6 +1421,7 @@ int slice_gemm_tile_m() { return BM; }
 int slice_gemm_tile_n() { return 256; }
 int slice_gemm_tile_n_of(int variant) { return ((variant & 1) || variant == kPairVariant) ? 128 : 256; }
 int slice_gemm_tile_m_of(int variant) { return variant == kPairVariant ? 2 * BM : BM; }
+int stacked_max_slices() { return stk::MAX_S; }
 
 // CTAs of the pair variant that can be resident at once (2 per cluster), queried once per process.
 int pair_max_ctas() {
@@ -1066,8 +1490,24 @@ cudaError_t launch_one(const CUtensorMap* tmA, const CUtensorMap* tmB, const Gem
   return cudaGetLastError();
 }
 template <bool GROUPED>
+cudaError_t launch_stacked(const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* a, const GroupArgs* g,
+                           int grid, cudaStream_t st) {
+  static bool done = false;
+  cudaError_t e;
+  if (GROUPED) {
+    if ((e = set_smem_once(slice_gemm_grouped_stacked_kernel, stk::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_grouped_stacked_kernel<<<grid, THREADS, stk::SMEM, st>>>(*g);
+  } else {
+    if ((e = set_smem_once(slice_gemm_stacked_kernel, stk::SMEM, done)) != cudaSuccess) return e;
+    slice_gemm_stacked_kernel<<<grid, THREADS, stk::SMEM, st>>>(*tmA, *tmB, *a);
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+template <bool GROUPED>
 cudaError_t launch_variant(int variant, const CUtensorMap* tmA, const CUtensorMap* tmB, const GemmArgs* a,
                            const GroupArgs* g, int grid, cudaStream_t st) {
+  if (variant == kStackedVariant) return launch_stacked<GROUPED>(tmA, tmB, a, g, grid, st);
   if (!(variant & 1)) return launch_one<GROUPED, 256, 1>(tmA, tmB, a, g, grid, st);
   if (variant & 2) return launch_one<GROUPED, 128, 1>(tmA, tmB, a, g, grid, st);
   return launch_one<GROUPED, 128, 2>(tmA, tmB, a, g, grid, st);
@@ -1079,6 +1519,12 @@ cudaError_t prepare_kernels() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(slice_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<128, 2, true>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_stacked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stk::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(slice_gemm_grouped_stacked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)stk::SMEM)) != cudaSuccess)
     return e;
   if ((e = cudaFuncSetAttribute(slice_gemm_kernel<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Cfg<256, 1>::SMEM)) != cudaSuccess)
@@ -1101,7 +1547,11 @@ cudaError_t prepare_kernels() {
 
 cudaError_t launch_slice_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& a, cudaStream_t st) {
   if (a.grid <= 0) return cudaSuccess;
-  return launch_variant<false>(a.variant, &tmA, &tmB, &a, nullptr, a.grid, st);
+  // the stacked kernel has no exact 128-bit mode and no group-product export; both, and slice
+  // counts above its limit, run on the 128-wide one-group kernel (same tiles, same bits)
+  const int v = (a.variant == kStackedVariant && (a.exact || a.Gdbg != nullptr || a.s > stacked_max_slices()))
+                    ? 1 : a.variant;
+  return launch_variant<false>(v, &tmA, &tmB, &a, nullptr, a.grid, st);
 }
 
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st) {

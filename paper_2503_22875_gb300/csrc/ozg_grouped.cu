@@ -652,19 +652,26 @@ int grouped_call(ozg_ctx* c, int64_t count, const ozg_gemm_desc* descs, const in
       all_beta_zero = all_beta_zero && work[i].beta == 0.0;
     }
     (void)wsum;
+    // the stacked kernel takes batches whose largest slice count (automatic calls: up to the
+    // selector's top class or the fallback) is within its limit
+    int smax = 0;
+    const int s_hi = std::max(c->sel_s_hi, c->fallback_slices);
+    for (int64_t i = 0; i < n; ++i) smax = std::max(smax, wauto[i] ? s_hi : ws[i]);
+    const bool stacked_ok = smax <= ozg::stacked_max_slices();
     if (pad1 < pad0)
       variant = 1;
     else
       variant = (w > 0 && wk >= 2048.0 * w) ? 2 : 0;
     auto tuned = c->tune.find(key);
     if (c->force_variant >= 0) {
-      variant = c->force_variant;
+      variant = (c->force_variant == ozg::kStackedVariant && !stacked_ok) ? 1 : c->force_variant;
     } else if (tuned != c->tune.end()) {
       variant = tuned->second;
     } else if (c->autotune && all_beta_zero) {
       float best = 1e30f;
-      const int nvar = ozg::pair_max_ctas() >= 2 ? OZG_NUM_TILE_VARIANTS : ozg::kPairVariant;
-      for (int v = 0; v < nvar; ++v) {
+      const bool pair_ok = ozg::pair_max_ctas() >= 2;
+      for (int v = 0; v < OZG_NUM_TILE_VARIANTS; ++v) {
+        if ((v == ozg::kPairVariant && !pair_ok) || (v == ozg::kStackedVariant && !stacked_ok)) continue;
         std::unique_ptr<GroupPlan, PlanDeleter> T(new GroupPlan());
         int rc = build_plan(c, n, work.data(), ws, wa, wb, wauto, v, T.get());
         if (rc) return rc;

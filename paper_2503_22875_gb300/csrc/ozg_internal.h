@@ -101,6 +101,10 @@ struct GroupArgs {
 // Tile variant 4: grouped launches on CTA pairs (2-CTA clusters, tcgen05.mma.cta_group::2 over
 // 256 x 128 pair tiles; GroupTile::tm counts 256-row tiles).  Single calls take variant 1 instead.
 constexpr int kPairVariant = 4;
+// Tile variant 5: 128 x 128 tiles over which the groups are taken two at a time (one N = 256 MMA
+// for both), up to stacked_max_slices() slices; other calls of that variant run as variant 1.
+constexpr int kStackedVariant = 5;
+int stacked_max_slices();
 cudaError_t launch_slice_gemm_grouped(const GroupArgs& g, int variant, int grid, cudaStream_t st);
 int slice_gemm_tile_m_of(int variant);
 int pair_max_ctas();  // resident CTAs of the pair variant (0 if the query fails)

@@ -1,6 +1,5 @@
 """Grouped emulated DGEMM (one persistent launch over many uneven GEMMs, CUDA-graph replay,
-tile-variant autotuner) against the oracle, call by call; the four tile variants agree bit for
-bit."""
+tile-variant autotuner) against the oracle, call by call; the tile variants agree bit for bit."""
 import numpy as np
 import pytest
 
@@ -42,10 +41,12 @@ def calls_of(batch):
              b["B"].shape[0], b["beta"], b["dC"], b["m"]) for b in batch]
 
 
-def windows(s, k):
-    """Exact int64 windows of the default epilogue (real): the largest group count c with
-    (s k_pad 127^2) 128^(c-1) 128/127 < 2^63, and ceil(s / c) windows."""
-    gmax = s * (-(-k // 64) * 64) * 127 * 127
+def windows(s, k, cplx=False):
+    """Exact int64 windows of the default epilogue: the largest group count c with
+    (s k_pad 127^2 [x2 complex]) 128^(c-1) 128/127 < 2^63, and ceil(s / c) windows.  k_pad is k
+    rounded up to 128 (the 128-wide kernels' padding; the 256-wide ones pad to 64, which never
+    needs more windows)."""
+    gmax = s * (-(-k // 128) * 128) * 127 * 127 * (2 if cplx else 1)
     c = max(1, (62 - gmax.bit_length()) // 7 + 1)
     return -(-s // c)
 
@@ -159,8 +160,8 @@ def test_single_call_autotune_cache_and_bits(ozg, tmp_path):
 
 
 def test_tile_variants_bit_identical(ozg):
-    """The tile variants (128 x 256 / 128 x 128 tiles, immediate / deferred epilogue pushes, and
-    CTA pairs on 256 x 128 tiles) give the same bits: single real and complex calls with
+    """The tile variants (128 x 256 / 128 x 128 tiles, immediate / deferred epilogue pushes, CTA
+    pairs on 256 x 128 tiles, and group pairs stacked into N = 256 MMAs) give the same bits: single real and complex calls with
     beta != 0, and a grouped batch."""
     m, n, k, s = 200, 300, 2100, 8   # ragged tiles, several k-segments per pair
     A, B = workloads.wide_exponent_pair(m, n, k, 1.0, seed=340)
@@ -172,7 +173,7 @@ def test_tile_variants_bit_identical(ozg):
     batch = make_batch(ozg, 12, seed=345)
     dA, dB, dAz, dBz = (ozg.to_device(x) for x in (A, B, Az, Bz))
     res = []
-    for v in range(5):  # variant 4 (CTA pairs) runs the grouped batch on 2-CTA clusters
+    for v in range(6):  # variant 4 (CTA pairs) runs the grouped batch on 2-CTA clusters
         ctx = ozg.Context()
         ctx.set_tile_variant(v)
         dC, dZ = ozg.to_device(C0), ozg.to_device(Z0)
@@ -194,14 +195,14 @@ def test_tile_variants_bit_identical(ozg):
     Ez = oracle.zgemm_emu(Az, Bz, 6, "N", "N", 0.5 - 2j, 1.5 + 0.25j, Z0)
     assert np.array_equal(ozg.from_device(res[0][1], mz, nz), Ez)
     with pytest.raises(ozg.OzgError):
-        ozg.Context().set_tile_variant(5)
+        ozg.Context().set_tile_variant(6)
 
 
 NARROW_SHAPES = [(130, 1, 17), (33, 17, 1), (97, 40, 70), (1, 65, 33), (130, 161, 130), (65, 304, 47),
                  (200, 100, 1000), (129, 48, 16)]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_narrow_tiles_ragged_k_bit_exact(ozg, variant):
     """Narrow last column tiles (1 .. 48 valid columns of a 128- or 256-wide tile), k ending
     inside a 16-wide step or a 64-wide TMA box, and row tiles with one to a few valid rows: in
@@ -243,6 +244,58 @@ def test_narrow_tiles_ragged_k_bit_exact(ozg, variant):
             assert np.array_equal(ozg.from_device(dC, m, n), E), (m, n, k)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("s", [1, 2, 3, 5, 8, 10, 11, 13, 16, 17])
+def test_stacked_group_pairs_match_one_group_kernel(ozg, s):
+    """Stacked group pairs (variant 5): windows with an odd group count (a lone first group),
+    one to three windows, k sweeps over several chains and ragged k; single real and complex
+    calls with alpha / beta and a grouped batch give the bits of the one-group 128-wide kernel
+    (variant 1), and the oracle's where the exact sum needs at most two windows.  s = 17 is above
+    the stacked kernel's limit and runs as variant 1."""
+    shapes = [(200, 130, 2100), (129, 257, 1000), (64, 64, 64), (130, 70, 129)]
+    res = {}
+    for v in (1, 5):
+        ctx = ozg.Context()
+        ctx.set_tile_variant(v)
+        try:
+            out = []
+            batch = []
+            for i, (m, n, k) in enumerate(shapes):
+                g = workloads.rng(1500 + i)
+                A = np.asfortranarray(workloads.wide_exponent((m, k), 1.5, g))
+                B = np.asfortranarray(workloads.wide_exponent((k, n), 1.5, g))
+                C0 = np.asfortranarray(g.uniform(-1, 1, (m, n)))
+                dC = ozg.to_device(C0)
+                ctx.dgemm("N", "N", m, n, k, -0.5, ozg.to_device(A), m, ozg.to_device(B), k, 0.75, dC, m, s)
+                ctx.sync()
+                out.append(ozg.from_device(dC, m, n))
+                if windows(s, k) <= 2:
+                    assert np.array_equal(out[-1], oracle.dgemm_emu(A, B, s, "N", "N", -0.5, 0.75, C0)), (m, n, k)
+                batch.append(dict(ta="N", tb="N", m=m, n=n, k=k, s=s, alpha=1.0, beta=0.0, A=A, B=B, C0=C0,
+                                  dA=ozg.to_device(A), dB=ozg.to_device(B), dC=ozg.to_device(C0)))
+            ctx.dgemm_grouped(calls_of(batch), [s] * len(batch))
+            ctx.sync()
+            for b in batch:
+                out.append(ozg.from_device(b["dC"], b["m"], b["n"]))
+                if windows(s, b["k"]) <= 2:
+                    assert np.array_equal(out[-1], oracle.dgemm_emu(b["A"], b["B"], s)), (b["m"], b["n"], b["k"])
+            m, n, k = 45, 70, 333
+            g = workloads.rng(1600)
+            A = np.asfortranarray(workloads.wide_exponent((m, k), 1.0, g) + 1j * workloads.wide_exponent((m, k), 1.0, g))
+            B = np.asfortranarray(workloads.wide_exponent((k, n), 1.0, g) + 1j * workloads.wide_exponent((k, n), 1.0, g))
+            C0 = np.asfortranarray(g.normal(size=(m, n)) + 1j * g.normal(size=(m, n)))
+            dC = ozg.to_device(C0)
+            ctx.zgemm("N", "N", m, n, k, 0.5 - 2j, ozg.to_device(A), m, ozg.to_device(B), k, 1.5 + 0.25j, dC, m, s)
+            ctx.sync()
+            out.append(ozg.from_device(dC, m, n))
+            if windows(s, k, cplx=True) <= 2:
+                assert np.array_equal(out[-1], oracle.zgemm_emu(A, B, s, "N", "N", 0.5 - 2j, 1.5 + 0.25j, C0))
+            res[v] = out
+        finally:
+            ctx.close()
+    for x, y in zip(res[1], res[5]):
+        assert np.array_equal(x, y)
 
 
 def test_pair_tiles_bit_exact_and_replay(ozg):

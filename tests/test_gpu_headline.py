@@ -71,7 +71,7 @@ def sample():
     return out
 
 
-@pytest.mark.parametrize("variant", [1, 0, 4])
+@pytest.mark.parametrize("variant", [1, 5, 0, 4])
 def test_learned_grouped_headline_calls_match_oracle(ozg, sample, variant):
     model = selector.read_model(selector.DEFAULT_MODEL)
     s_cap = max(model["s_lo"] + 10, model["fallback"])

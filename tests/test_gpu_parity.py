@@ -148,13 +148,14 @@ def test_group_products_cross_int32_fold(ozg, ctx, ta, tb):
 
 def test_dgemm_cross_int32_fold_bit_exact(ozg, ctx):
     """The same operands through the emulated DGEMM (one int64 window, so the oracle's definition
-    bit for bit), single call and grouped launch, both tile widths and CTA pairs."""
+    bit for bit), single call and grouped launch, both tile widths, CTA pairs and stacked group
+    pairs (whose chains go straight into int64 windows, with no int32 fold)."""
     m, n, k, s = 40, 33, 34000, FOLD_S
     A, B = fold_operands(m, n, k)
     assert windows(s, k) == 1
     E = oracle.dgemm_emu(A, B, s)
     dA, dB = dev(ozg, A), dev(ozg, B)
-    for variant in (0, 1, 4):
+    for variant in (0, 1, 4, 5):
         ctx.set_tile_variant(variant)
         try:
             dC = torch.zeros((n, m), dtype=torch.float64, device="cuda")
