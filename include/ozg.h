@@ -277,9 +277,9 @@ int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
  * in the last bits between the 256- and 128-wide families. */
 #define OZG_NUM_TILE_VARIANTS 6
 
-/* Tile-variant autotuner: enable != 0 times the four variants the first time a shape bucket
- * (rounded log2 of m, n, k and the slice count; variants 0..3) or a grouped batch (every variant)
- * is seen, keeps the fastest,
+/* Tile-variant autotuner: enable != 0 times the variants the first time a shape bucket
+ * (rounded log2 of m, n, k and the slice count; variants 0..3 and 5) or a grouped batch (every
+ * variant) is seen, keeps the fastest,
  * and appends single-call choices to cache_path (may be NULL) as "bucket variant" lines that
  * later contexts read back.  Tuning runs only for calls with beta == 0 (C is then write-only);
  * other calls use the heuristic: the width that pads least; then for 128 x 256 tiles deferral

@@ -118,7 +118,9 @@ static void tune_load(ozg_ctx* c) {
   while (std::getline(in, line)) {
     unsigned long long b = 0;
     int v = 0;
-    if (std::sscanf(line.c_str(), "%llx %d", &b, &v) == 2 && v >= 0 && v <= 3) c->tune[b] = v;
+    // single-call variants: 0 .. 3 and the stacked group pairs (no CTA pairs for single calls)
+    if (std::sscanf(line.c_str(), "%llx %d", &b, &v) == 2 && ((v >= 0 && v <= 3) || v == kStackedVariant))
+      c->tune[b] = v;
   }
 }
 
