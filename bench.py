@@ -133,34 +133,43 @@ def source_hash():
 
 
 def profile_traffic(name: str):
-    """(bytes, sha256 of the kernel sources it was taken on) from the committed ncu summary
-    profiles/<name>.md, or (None, None) when it is missing."""
+    """(bytes, sha256 of the kernel sources it was taken on, tile variant or None) from the
+    committed ncu summary profiles/<name>.md, or (None, None, None) when it is missing."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
-        return None, None
+        return None, None, None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    return (float(m.group(1)) if m else None), (h.group(1) if h else None)
+    v = re.search(r"tile_variant:\s*(\d+)", txt)
+    return (float(m.group(1)) if m else None), (h.group(1) if h else None), (int(v.group(1)) if v else None)
 
 
-def kernel_traffic(name: str):
-    """Per-launch DRAM bytes of the current kernel source, or None when the summary is missing or
-    was taken on a different version of the kernel source."""
-    t, sha = profile_traffic(name)
+def kernel_traffic(name: str, variant=None):
+    """Per-launch DRAM bytes of the current kernel source, or None when the summary is missing,
+    was taken on a different version of the kernel source or on another tile variant."""
+    t, sha, v = profile_traffic(name)
+    if variant is not None and v is not None and v != variant:
+        return None
     return t if t is not None and sha == source_hash() else None
 
 
-def stale_traffic(name: str):
-    """The last capture's figure when it was taken on other kernel sources (reported beside the
-    null traffic, never as the traffic), else None."""
-    t, sha = profile_traffic(name)
-    if t is None or sha is None or sha == source_hash():
+def stale_traffic(name: str, variant=None):
+    """The last capture's figure when it was taken on other kernel sources or another tile
+    variant (reported beside the null traffic, never as the traffic), else None."""
+    t, sha, v = profile_traffic(name)
+    if t is None or sha is None or (sha == source_hash() and (variant is None or v is None or v == variant)):
         return None
-    return {"bytes_per_launch": t, "source_sha256": sha, "profile": f"profiles/{name}.md"}
+    return {"bytes_per_launch": t, "source_sha256": sha, "tile_variant": v, "profile": f"profiles/{name}.md"}
 
 
-def tensor_roofline(kernel, flops, ms, traffic_name):
+# slice-product kernel of a grouped launch, by tile variant
+GROUPED_KERNELS = {0: "slice_gemm_grouped_kernel<256, 1>", 1: "slice_gemm_grouped_kernel<128, 2>",
+                   2: "slice_gemm_grouped_kernel<256, 1>", 3: "slice_gemm_grouped_kernel<128, 1>",
+                   4: "slice_gemm_pair_kernel", 5: "slice_gemm_grouped_stacked_kernel"}
+
+
+def tensor_roofline(kernel, flops, ms, traffic_name, variant=None):
     """Roofline of a slice-product kernel: algorithmic tensor flops (s(s+1)/2 FP16 products of
     2 m n k each) over its CUDA-event duration, against the measured dense bf16 peak (FP16
     operands run at the same nominal rate).  The burst peak: each timed launch lasts well under
@@ -169,8 +178,8 @@ def tensor_roofline(kernel, flops, ms, traffic_name):
     peak = peaks.get("bf16_tflops")
     achieved = flops / (ms / 1e3) / 1e12
     return {"bound": "tensor", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": kernel_traffic(traffic_name),
-            "traffic_other_source": stale_traffic(traffic_name),
+            "frac": achieved / peak, "traffic": kernel_traffic(traffic_name, variant),
+            "traffic_other_source": stale_traffic(traffic_name, variant),
             "peak_src": f"{src} bf16 burst (cuBLAS); sustained {peaks.get('bf16_tflops_sustained')}",
             "frac_of_sustained": achieved / peaks.get("bf16_tflops_sustained", peak),
             "tensor_flops_per_launch": flops, "launch_ms": ms}
@@ -420,7 +429,7 @@ def compare_section(ozg, torch, batch, calls, flops, st, steps, learned_reps):
     out["smallest_fixed_s_meeting_target_on_99pct"] = min(ok_99) if ok_99 else None
     # the learned step with each tile variant forced, against the autotuned choice
     tv = {}
-    for v in range(5):
+    for v in range(6):
         ctx = ozg.Context(stream=st)
         ctx.load_selector(SELECTOR_MODEL)
         ctx.set_target_error(TARGET_ERR)
@@ -876,7 +885,8 @@ def run_gpu(args):
     pctx.close()
     gemm_ms = ph["gemm"][0] / rsteps
     grouped_ms_nograph = ph["grouped"][0] / max(ph["grouped"][1], 1)
-    roof = tensor_roofline("slice_gemm_grouped_kernel", tflops_step, gemm_ms, f"slice_gemm_grouped_learned_{n}")
+    roof = tensor_roofline(GROUPED_KERNELS.get(tile_variant, "slice_gemm_grouped_kernel"), tflops_step, gemm_ms,
+                           f"slice_gemm_grouped_learned_{n}", tile_variant)
     # algorithmic DRAM bytes of the launch: each selected digit plane read once, C written once
     roof["algorithmic_bytes"] = sum(2.0 * r.selected * (c.m + c.n) * c.k + 8.0 * c.m * c.n
                                     for c, r in zip(batch.calls, reps))

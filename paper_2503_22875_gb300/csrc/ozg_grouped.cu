@@ -658,8 +658,10 @@ int grouped_call(ozg_ctx* c, int64_t count, const ozg_gemm_desc* descs, const in
     const int s_hi = std::max(c->sel_s_hi, c->fallback_slices);
     for (int64_t i = 0; i < n; ++i) smax = std::max(smax, wauto[i] ? s_hi : ws[i]);
     const bool stacked_ok = smax <= ozg::stacked_max_slices();
+    // 128-wide tiles take the stacked group pairs when the batch's slice counts allow them
+    // (measured faster than the one-group kernel on grouped batches of short and medium k)
     if (pad1 < pad0)
-      variant = 1;
+      variant = stacked_ok ? ozg::kStackedVariant : 1;
     else
       variant = (w > 0 && wk >= 2048.0 * w) ? 2 : 0;
     auto tuned = c->tune.find(key);
