@@ -987,8 +987,18 @@ constexpr uint32_t IDESC2 = umma_idesc_f16_f32(BM, 256), IDESC1 = umma_idesc_f16
 constexpr int CHAIN_STAGES = CHAIN_K / BK;  // 64-k MMA stages per accumulator column and chain
 constexpr int MAX_S = CHAIN_STAGES;          // a two-group sweep of g stages must fit one chain
 constexpr int NOUT = 64;                     // outputs per epilogue thread (real; complex: 32)
+constexpr uint64_t DSLOT = SLOT >> 4;         // descriptor start-address units per ring entry
 static_assert(SMEM <= 227 * 1024, "stage ring");
+static_assert(SMEM < (1u << 18), "descriptor start addresses stay within their 14-bit field");
 }  // namespace stk
+
+// The four K = 16 MMAs of one 64-wide k sub-tile; the first overwrites the accumulator when it
+// starts a chain.
+__device__ __forceinline__ void stk_mma4(uint32_t dt, uint64_t da, uint64_t db, uint32_t idesc, bool fresh) {
+  umma_f16(dt, da, db, idesc, fresh ? 0u : 1u);
+#pragma unroll
+  for (int k16 = 1; k16 < BK / 16; ++k16) umma_f16(dt, da + (uint64_t)(2 * k16), db + (uint64_t)(2 * k16), idesc, 1u);
+}
 
 // Pass q of the window [wstart, wstart + wlen): the groups ga, ga + 1, or the lone group ga
 // (first pass of a window with an odd count).
@@ -1131,6 +1141,7 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
       if (lane == 0) {
         uint32_t e = 0, eph = 0;
         int eprev = -1;  // ring entry of the previous stage (freed by the next commit)
+        const uint64_t dA0 = umma_desc_sw128(smem + A_OFF), dB0 = umma_desc_sw128(smem + B_OFF);
         uint32_t acc_par = 0;
         int buf = 0;
         uint32_t tslot = 0, tphase = 0;
@@ -1169,46 +1180,56 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                   fresh = true;
                 }
                 const uint32_t dt = tmem + (uint32_t)(buf * 256);
-                for (int i = two ? 0 : 1; i <= (two ? ga : ga - 1); ++i) {
+                // descriptors advance by SLOT >> 4 per ring entry (the start-address field)
+                if (!two) {
+                  // lone group: A_i B_{ga-i} into columns 128 .. 255
+                  for (int i = 1; i < ga; ++i) {
+                    if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
+                    tc_fence_after();
+                    stk_mma4(dt + 128, dA0 + e * DSLOT, dB0 + e * DSLOT, IDESC1, fresh);
+                    fresh = false;
+                    if (eprev >= 0) umma_commit(&bar_empty[eprev]);
+                    eprev = (int)e;
+                    if (++e == NE) {
+                      e = 0;
+                      eph ^= 1;
+                    }
+                  }
+                } else {
+                  // stage 0: B_ga only, no MMA; it frees the previous stage's entry
                   if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
                   tc_fence_after();
-                  const uint64_t da = umma_desc_sw128(smem + A_OFF + e * SLOT);
-                  const uint64_t db = umma_desc_sw128(smem + B_OFF + e * SLOT);
-                  if (!two) {
-                    // lone group: A_i B_{ga-i} into columns 128 .. 255
-#pragma unroll
-                    for (int k16 = 0; k16 < BK / 16; ++k16)
-                      umma_f16(dt + 128, da + (uint64_t)(2 * k16), db + (uint64_t)(2 * k16), IDESC1,
-                               (fresh && k16 == 0) ? 0u : 1u);
-                    fresh = false;
-                  } else if (i >= 1) {
-                    const uint64_t dbp = umma_desc_sw128(smem + B_OFF + (uint32_t)eprev * SLOT);
-                    if (i == ga) {
-                      // A_ga B_1 (group ga + 1 only): columns 0 .. 127
-#pragma unroll
-                      for (int k16 = 0; k16 < BK / 16; ++k16)
-                        umma_f16(dt, da + (uint64_t)(2 * k16), dbp + (uint64_t)(2 * k16), IDESC1,
-                                 (fresh && k16 == 0) ? 0u : 1u);
-                    } else if (eprev + 1 == (int)e) {
+                  if (eprev >= 0) umma_commit(&bar_empty[eprev]);
+                  eprev = (int)e;
+                  if (++e == NE) {
+                    e = 0;
+                    eph ^= 1;
+                  }
+                  for (int i = 1; i < ga; ++i) {
+                    if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
+                    tc_fence_after();
+                    const uint64_t da = dA0 + e * DSLOT, dbp = dB0 + (uint32_t)eprev * DSLOT;
+                    if (e != 0) {
                       // [B_{ga+1-i}; B_{ga-i}] are adjacent slots: one N = 256 operand
-#pragma unroll
-                      for (int k16 = 0; k16 < BK / 16; ++k16)
-                        umma_f16(dt, da + (uint64_t)(2 * k16), dbp + (uint64_t)(2 * k16), IDESC2,
-                                 (fresh && k16 == 0) ? 0u : 1u);
+                      stk_mma4(dt, da, dbp, IDESC2, fresh);
                     } else {
                       // the pair straddles the end of the ring: two N = 128 halves
-#pragma unroll
-                      for (int k16 = 0; k16 < BK / 16; ++k16) {
-                        umma_f16(dt, da + (uint64_t)(2 * k16), dbp + (uint64_t)(2 * k16), IDESC1,
-                                 (fresh && k16 == 0) ? 0u : 1u);
-                        umma_f16(dt + 128, da + (uint64_t)(2 * k16), db + (uint64_t)(2 * k16), IDESC1,
-                                 (fresh && k16 == 0) ? 0u : 1u);
-                      }
+                      stk_mma4(dt, da, dbp, IDESC1, fresh);
+                      stk_mma4(dt + 128, da, dB0, IDESC1, fresh);
                     }
                     fresh = false;
+                    umma_commit(&bar_empty[eprev]);  // the previous entry's B was last used here
+                    eprev = (int)e;
+                    if (++e == NE) {
+                      e = 0;
+                      eph ^= 1;
+                    }
                   }
-                  // the previous stage's entry (its A used there, its B last used here) is free
-                  if (eprev >= 0) umma_commit(&bar_empty[eprev]);
+                  // stage ga: A_ga B_1 (group ga + 1 only) into columns 0 .. 127
+                  if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
+                  tc_fence_after();
+                  stk_mma4(dt, dA0 + e * DSLOT, dB0 + (uint32_t)eprev * DSLOT, IDESC1, false);
+                  umma_commit(&bar_empty[eprev]);
                   eprev = (int)e;
                   if (++e == NE) {
                     e = 0;
