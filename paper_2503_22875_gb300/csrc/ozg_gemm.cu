@@ -1173,11 +1173,13 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
               stk_pass(wstart, wlen, q, ga, two);
               const int spc = stk_sweeps(ga, two);
               bool fresh = false;  // the next MMA starts a chain (overwrites the accumulator)
+              int left = 0;        // k sweeps left in the current chain
               for (int kbi = 0; kbi < KB; ++kbi) {
-                if (kbi % spc == 0) {
+                if (left == 0) {
                   if (!mbar_wait(&bar_acce[buf], ((acc_par >> buf) & 1) ^ 1, abort_p, status)) goto mma_done;
                   tc_fence_after();
                   fresh = true;
+                  left = spc;
                 }
                 const uint32_t dt = tmem + (uint32_t)(buf * 256);
                 // descriptors advance by SLOT >> 4 per ring entry (the start-address field)
@@ -1236,10 +1238,11 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                     eph ^= 1;
                   }
                 }
-                if ((kbi + 1) % spc == 0 || kbi == KB - 1) {
+                if (--left == 0 || kbi == KB - 1) {
                   umma_commit(&bar_accf[buf]);
                   acc_par ^= 1u << buf;
                   buf ^= 1;
+                  left = 0;
                 }
               }
             }
