@@ -965,7 +965,8 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
 // B_{g+1-p} (group g + 1).  So one k sub-tile of a pass loads A_1 .. A_g and B_g .. B_1 once
 // each and issues, for p = 1 .. g - 1, one N = 256 MMA whose B operand is the two consecutive
 // B tiles [B_{g+1-p}; B_{g-p}] -- accumulator columns 0 .. 127 collect group g + 1, columns
-// 128 .. 255 group g -- and, for p = g, an N = 128 MMA (A_g B_1, group g + 1).  Against the
+// 128 .. 255 group g -- and, for p = g, an N = 128 MMA (A_g B_1, group g + 1); that last stage
+// also loads the next k sub-tile's B_g, so only a pass's first stage issues no MMA.  Against the
 // one-group schedule this halves the shared-memory fill (L2 -> SM bytes) and the MMA
 // instructions per product.  The stage ring holds one A and one B sub-tile (64 k) per entry;
 // a B tile is used by its own stage and the next, so the commit after a stage frees the entry
@@ -1105,13 +1106,19 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
               stk_pass(wstart, wlen, q, ga, two);
               for (int kbi = 0; kbi < KB; ++kbi) {
                 const int kb = (pc & 1) ? KB - 1 - kbi : kbi;  // snake: a pass starts where the last ended
-                // stage i: A_i (i >= 1) and B_{ga-i} (i <= ga - 1); a lone group has no stage 0
-                for (int i = two ? 0 : 1; i <= (two ? ga : ga - 1); ++i) {
+                const int kbn = (pc & 1) ? kb - 1 : kb + 1;    // the sweep's next k block
+                // stage i: A_i (i >= 1) and B_{ga-i} (i <= ga - 1); with two groups, stage ga also
+                // carries B_ga of the next k block, so only the pass's first sweep has a stage 0;
+                // a lone group has none
+                for (int i = (two && kbi == 0) ? 0 : 1; i <= (two ? ga : ga - 1); ++i) {
                   if (!mbar_wait(&bar_empty[e], eph ^ 1, abort_p, status)) goto producer_done;
-                  const bool hasA = i >= 1, hasB = i <= ga - 1;
+                  const bool last = i == ga;  // two groups only
+                  const bool hasA = i >= 1, hasB = last ? kbi + 1 < KB : true;
                   mbar_arrive_expect_tx(&bar_full[e], (hasA ? SLOT : 0u) + (hasB ? SLOT : 0u));
                   if (hasA) tma_load_3d(j.tmA, &bar_full[e], smem + A_OFF + e * SLOT, kb * BK, arow, i - 1);
-                  if (hasB) tma_load_3d(j.tmB, &bar_full[e], smem + B_OFF + e * SLOT, kb * BK, brow, ga - i - 1);
+                  if (hasB)
+                    tma_load_3d(j.tmB, &bar_full[e], smem + B_OFF + e * SLOT, (last ? kbn : kb) * BK, brow,
+                                last ? ga - 1 : ga - i - 1);
                   ++issued;
                   if (++e == NE) {
                     e = 0;
@@ -1198,14 +1205,16 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                     }
                   }
                 } else {
-                  // stage 0: B_ga only, no MMA; it frees the previous stage's entry
-                  if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
-                  tc_fence_after();
-                  if (eprev >= 0) umma_commit(&bar_empty[eprev]);
-                  eprev = (int)e;
-                  if (++e == NE) {
-                    e = 0;
-                    eph ^= 1;
+                  if (kbi == 0) {
+                    // the pass's stage 0: B_ga only, no MMA; it frees the previous stage's entry
+                    if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
+                    tc_fence_after();
+                    if (eprev >= 0) umma_commit(&bar_empty[eprev]);
+                    eprev = (int)e;
+                    if (++e == NE) {
+                      e = 0;
+                      eph ^= 1;
+                    }
                   }
                   for (int i = 1; i < ga; ++i) {
                     if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
@@ -1227,7 +1236,8 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                       eph ^= 1;
                     }
                   }
-                  // stage ga: A_ga B_1 (group ga + 1 only) into columns 0 .. 127
+                  // stage ga: A_ga B_1 (group ga + 1 only) into columns 0 .. 127; its B slot holds
+                  // the next sweep's B_ga
                   if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
                   tc_fence_after();
                   stk_mma4(dt, dA0 + e * DSLOT, dB0 + (uint32_t)eprev * DSLOT, IDESC1, false);
