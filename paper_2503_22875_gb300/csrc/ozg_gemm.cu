@@ -1311,6 +1311,18 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
       pa.odd = odd;
       pa.ebase = e_row - 7 * (s + 1);
       const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(chalf * NOUT);
+      // the column exponents of this warp's outputs, loaded now (their latency hides behind the
+      // drains) one or two per lane and handed out by shuffles when C is written
+      int fcol[2];
+      {
+        const int64_t c0 = j.cplx ? (pa.gcol0 >> 1) : pa.gcol0;
+        const int64_t climit = j.cplx ? j.n : j.cols;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int64_t c = c0 + h * 32 + lane;
+          fcol[h] = (c < climit && (h == 0 || !j.cplx)) ? __ldg(j.f + c) : 0;
+        }
+      }
       int widx = 0;
       for (int wstart = 2; wstart <= s + 1; wstart += win, ++widx) {
         const int wlen = min(win, s + 2 - wstart);
@@ -1374,7 +1386,15 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         pa.kind = gend == s + 1 ? kFinal : widx == 0 ? kSpill : kClose;
 #pragma unroll 1
         for (int o = 0; o < nout; o += 8) {
-          window_out<8, false>(W, o, pa, j, nullptr, nullptr);
+          long long s0c[8];
+          int fe[8];
+          const int fsrc = o < 32 ? fcol[0] : fcol[1];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            s0c[i] = widx >= 1 ? pa.S0[(size_t)(o + i) * BM] : 0ll;
+            fe[i] = __shfl_sync(0xffffffffu, fsrc, (o + i) & 31);
+          }
+          window_out<8, false, true>(W, o, pa, j, s0c, fe);
 #pragma unroll
           for (int c = 0; c < NOUT - 8; ++c) W[c] = W[c + 8];
         }
