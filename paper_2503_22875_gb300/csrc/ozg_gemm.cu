@@ -970,8 +970,8 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
 // one-group schedule this halves the shared-memory fill (L2 -> SM bytes) and the MMA
 // instructions per product.  The stage ring holds one A and one B sub-tile (64 k) per entry;
 // a B tile is used by its own stage and the next, so the commit after a stage frees the entry
-// of the stage before it.  Where the two B tiles straddle the end of the ring the MMA is issued
-// as two N = 128 halves.  A window with an odd number of groups starts with a lone group
+// of the stage before it.  Entry 0's B tile is also written to a mirror slot behind the last
+// entry, so the two B tiles of a stage are adjacent across the end of the ring too.  A window with an odd number of groups starts with a lone group
 // (one N = 128 MMA per plane pair, into columns 128 .. 255).
 //
 // The two 256-column accumulators fill TMEM, so the int64 windows live in the epilogue's
@@ -983,7 +983,9 @@ namespace stk {
 constexpr int NE = 6;                      // stage ring entries
 constexpr uint32_t SLOT = BM * BK * 2;     // one 128-row x 64-k fp16 sub-tile (16 KB, one TMA box)
 constexpr uint32_t A_OFF = 0, B_OFF = NE * SLOT;
-constexpr size_t SMEM = (size_t)2 * NE * SLOT + 1024;
+// B slots: one per entry and a mirror of entry 0's behind the last, so that the B tiles of
+// every two consecutive stages are adjacent (one N = 256 operand) also across the ring's end
+constexpr size_t SMEM = (size_t)(2 * NE + 1) * SLOT + 1024;
 constexpr uint32_t IDESC2 = umma_idesc_f16_f32(BM, 256), IDESC1 = umma_idesc_f16_f32(BM, 128);
 constexpr int CHAIN_STAGES = CHAIN_K / BK;  // 64-k MMA stages per accumulator column and chain
 constexpr int MAX_S = CHAIN_STAGES;          // a two-group sweep of g stages must fit one chain
@@ -1114,11 +1116,14 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                   if (!mbar_wait(&bar_empty[e], eph ^ 1, abort_p, status)) goto producer_done;
                   const bool last = i == ga;  // two groups only
                   const bool hasA = i >= 1, hasB = last ? kbi + 1 < KB : true;
-                  mbar_arrive_expect_tx(&bar_full[e], (hasA ? SLOT : 0u) + (hasB ? SLOT : 0u));
+                  const bool mirror = hasB && e == 0;
+                  mbar_arrive_expect_tx(&bar_full[e], (hasA ? SLOT : 0u) + (hasB ? SLOT : 0u) + (mirror ? SLOT : 0u));
                   if (hasA) tma_load_3d(j.tmA, &bar_full[e], smem + A_OFF + e * SLOT, kb * BK, arow, i - 1);
-                  if (hasB)
-                    tma_load_3d(j.tmB, &bar_full[e], smem + B_OFF + e * SLOT, (last ? kbn : kb) * BK, brow,
-                                last ? ga - 1 : ga - i - 1);
+                  if (hasB) {
+                    const int bk = (last ? kbn : kb) * BK, bz = last ? ga - 1 : ga - i - 1;
+                    tma_load_3d(j.tmB, &bar_full[e], smem + B_OFF + e * SLOT, bk, brow, bz);
+                    if (mirror) tma_load_3d(j.tmB, &bar_full[e], smem + B_OFF + NE * SLOT, bk, brow, bz);
+                  }
                   ++issued;
                   if (++e == NE) {
                     e = 0;
@@ -1219,15 +1224,9 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                   for (int i = 1; i < ga; ++i) {
                     if (!mbar_wait(&bar_full[e], eph, abort_p, status)) goto mma_done;
                     tc_fence_after();
-                    const uint64_t da = dA0 + e * DSLOT, dbp = dB0 + (uint32_t)eprev * DSLOT;
-                    if (e != 0) {
-                      // [B_{ga+1-i}; B_{ga-i}] are adjacent slots: one N = 256 operand
-                      stk_mma4(dt, da, dbp, IDESC2, fresh);
-                    } else {
-                      // the pair straddles the end of the ring: two N = 128 halves
-                      stk_mma4(dt, da, dbp, IDESC1, fresh);
-                      stk_mma4(dt + 128, da, dB0, IDESC1, fresh);
-                    }
+                    // [B_{ga+1-i}; B_{ga-i}] are adjacent slots (at the ring's end, the last slot
+                    // and entry 0's mirror): one N = 256 operand
+                    stk_mma4(dt, dA0 + e * DSLOT, dB0 + (uint32_t)eprev * DSLOT, IDESC2, fresh);
                     fresh = false;
                     umma_commit(&bar_empty[eprev]);  // the previous entry's B was last used here
                     eprev = (int)e;
