@@ -282,9 +282,10 @@ int ozg_set_fallback_slices(ozg_ctx* ctx, int slices);
  * variant) is seen, keeps the fastest,
  * and appends single-call choices to cache_path (may be NULL) as "bucket variant" lines that
  * later contexts read back.  Tuning runs only for calls with beta == 0 (C is then write-only);
- * other calls use the heuristic: the width that pads least; then for 128 x 256 tiles deferral
- * when k >= 2048 (for a grouped batch, the mean k weighted by m n s^2); for 128 x 128 tiles the
- * stacked group pairs (variant 5) in grouped calls whose slice counts allow them, else two k
+ * other calls use the heuristic: the stacked group pairs (variant 5) for single calls with at
+ * most 16 slices outside the exact epilogue; otherwise the width that pads least, then for
+ * 128 x 256 tiles deferral when k >= 2048 (for a grouped batch, the mean k weighted by m n s^2)
+ * and for 128 x 128 tiles variant 5 in grouped calls whose slice counts allow it, else two k
  * slices per stage (variant 1). */
 int ozg_set_autotune(ozg_ctx* ctx, int enable, const char* cache_path);
 

@@ -1014,6 +1014,16 @@ __device__ __forceinline__ void stk_pass(int wstart, int wlen, int q, int& ga, b
     ga = wstart + 2 * q;
   }
 }
+// Length of the first window.  With three or more windows every window but the last holds win
+// groups, as in the one-group kernels (their FP64 continuation rounds per window, so the split
+// must be the same for the same bits).  With two windows the exact sum is rounded once and any
+// split into windows of at most win groups gives the same bits: the first takes one group
+// less when that makes the second window's count even (a lone group of a later window pairs
+// far more planes than the lone group 2 of the first).
+__device__ __forceinline__ int stk_len0(int s, int win) {
+  if (s <= win || s > 2 * win) return min(s, win);
+  return (((win - s) & 1) && s - (win - 1) <= win) ? win - 1 : win;
+}
 // k sweeps per chain: a sweep adds ga (two groups) or ga - 1 (lone group) 64-k MMA stages to
 // the accumulator columns that collect the most
 __device__ __forceinline__ int stk_sweeps(int ga, bool two) { return stk::CHAIN_STAGES / (two ? ga : ga - 1); }
@@ -1100,8 +1110,8 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
           const int arow = j.tm * BM, brow = j.tn * 128;
           const int win = window_len(j.s, (int64_t)j.KB * 128, j.cplx);
           int pc = 0;
-          for (int wstart = 2; wstart <= j.s + 1; wstart += win) {
-            const int wlen = min(win, j.s + 2 - wstart);
+          for (int wstart = 2, wlen = stk_len0(j.s, win); wstart <= j.s + 1;
+               wstart += wlen, wlen = min(win, j.s + 2 - wstart)) {
             for (int q = 0; q < (wlen + 1) / 2; ++q, ++pc) {
               int ga;
               bool two;
@@ -1177,8 +1187,8 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
           if (j.skip) continue;
           const int KB = (j.KB - 1) * 2 + j.klast;
           const int win = window_len(j.s, (int64_t)j.KB * 128, j.cplx);
-          for (int wstart = 2; wstart <= j.s + 1; wstart += win) {
-            const int wlen = min(win, j.s + 2 - wstart);
+          for (int wstart = 2, wlen = stk_len0(j.s, win); wstart <= j.s + 1;
+               wstart += wlen, wlen = min(win, j.s + 2 - wstart)) {
             for (int q = 0; q < (wlen + 1) / 2; ++q) {
               int ga;
               bool two;
@@ -1323,8 +1333,8 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         }
       }
       int widx = 0;
-      for (int wstart = 2; wstart <= s + 1; wstart += win, ++widx) {
-        const int wlen = min(win, s + 2 - wstart);
+      for (int wstart = 2, wlen = stk_len0(s, win); wstart <= s + 1;
+           wstart += wlen, wlen = min(win, s + 2 - wstart), ++widx) {
         const int gend = wstart + wlen - 1;
         long long W[NOUT];
 #pragma unroll

@@ -150,6 +150,10 @@ int choose_variant(ozg_ctx* c, int64_t rows, int64_t cols, int64_t k, int s) {
   tune_load(c);
   auto it = c->tune.find(shape_bucket(rows, cols, k, s));
   if (it != c->tune.end()) return it->second;
+  // the stacked group pairs where they apply: on square DGEMMs of 1024 .. 8192 at s = 7 .. 10
+  // they measured 0.47 - 1.06x the time of the width heuristic's choice (faster except for
+  // 2048^3 and for 8192^3 at s = 10, by 6%)
+  if (s <= stacked_max_slices() && !c->exact) return kStackedVariant;
   return heuristic_variant(rows, cols, k, s);
 }
 
