@@ -598,7 +598,9 @@ def single_section(ozg, torch, size, steps, phis=SINGLE_PHIS, slice_list=tuple(r
             ph = ctx.phase_times()
             ctx.set_profiling(False)
             gemm_ms = ph["gemm"][0] / max(ph["gemm"][1], 1)
-            roof = tensor_roofline("slice_gemm_kernel", s * (s + 1) / 2 * flops, gemm_ms, f"slice_gemm_{n}_s{s}")
+            # single calls of at most 16 slices run the stacked group-pair kernel (variant 5)
+            kname = "slice_gemm_stacked_kernel" if s <= 16 else "slice_gemm_kernel"
+            roof = tensor_roofline(kname, s * (s + 1) / 2 * flops, gemm_ms, f"slice_gemm_{n}_s{s}", 5 if s <= 16 else None)
             roof["slices"] = s
             roof["algorithmic_bytes"] = 2.0 * s * 2 * n * n + 8.0 * n * n
             ms_nat = timed(torch, st, lambda: ctx.native_dgemm("N", "N", n, n, n, 1.0, dA, n, dB, n, 0.0, dC, n), 1,
