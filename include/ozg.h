@@ -212,7 +212,8 @@ int ozg_dgemm_grouped(ozg_ctx* ctx, int64_t count, const ozg_gemm_desc* descs, c
  * (CPU) pointers, everything else is as for ozg_dgemm_grouped (slices, reports, the selector, the
  * check and its escalation).  Synchronous: on return C holds the results and the reports are
  * final.  The library stages the matrices in device memory it owns (grown with cudaMalloc) and
- * cuts the batch into parts of about equal work (ozg_set_host_parts, default 16): a part's inputs
+ * cuts the batch into parts (ozg_set_host_parts, default 16) whose shares of the work rise and
+ * fall (1, 2, 3, .., 3, 2, 1: small first and last parts, whose copies cannot overlap): a part's inputs
  * are copied in while earlier parts compute and their results are copied out, each part on its
  * own internal stream and CUDA graph.  Matrices whose host regions touch or overlap move as one
  * copy; C is written back only where the calls write it (rows 0..m-1 of each column; C is read

@@ -139,13 +139,18 @@ extern "C" int ozg_dgemm_grouped_host(ozg_ctx* c, int64_t count, const ozg_gemm_
   int rc = ensure_parts(c, parts);
   if (rc) return rc;
 
-  // parts of about equal work (2 m n k), in call order
+  // parts in call order with work (2 m n k) shares rising and then falling (1, 2, 3, .., 3, 2, 1):
+  // the first part's copy-in and the last part's compute and copy-out are not overlapped, so
+  // they are kept small, while the middle parts are large enough to keep the per-part launches
+  // and the tail of each part's persistent launch small against its work
   std::vector<double> wsum(count + 1, 0.0);
   for (int64_t i = 0; i < count; ++i) wsum[i + 1] = wsum[i] + 2.0 * descs[i].m * descs[i].n * descs[i].k;
+  std::vector<double> share(parts + 1, 0.0);
+  for (int p = 0; p < parts; ++p) share[p + 1] = share[p] + (double)std::min(p + 1, parts - p);
   std::vector<int64_t> cut(parts + 1, 0);
   cut[parts] = count;
   for (int p = 1; p < parts; ++p) {
-    const double want = wsum[count] * p / parts;
+    const double want = wsum[count] * share[p] / share[parts];
     cut[p] = std::max(cut[p - 1], (int64_t)(std::lower_bound(wsum.begin(), wsum.end(), want) - wsum.begin()));
     cut[p] = std::min(cut[p], count);
   }
