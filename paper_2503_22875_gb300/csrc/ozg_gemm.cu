@@ -277,6 +277,16 @@ __device__ __forceinline__ void prefetch_close(const PushArgs& a, const TileJob&
   for (int i = 0; i < NCH; ++i) fe[i] = (a.kind == kFinal && c0 + i < climit) ? __ldg(j.f + c0 + i) : 0;
 }
 
+// RN(W 2^E) for one int64 window: one correctly rounded conversion, the power of two added to
+// the exponent field.  `ok` is false when the result is not a normal double (the caller then
+// takes final_val).  The same value as rn_windows(0, W, S, E) with fewer instructions.
+__device__ __forceinline__ double rn_single(long long W, int E, bool& ok) {
+  const long long bits = __double_as_longlong(__ll2double_rn(W));
+  const int ex = (int)((bits >> 52) & 0x7ff) + E;
+  ok = W == 0 || (ex >= 1 && ex <= 2046);
+  return W == 0 ? 0.0 : __longlong_as_double(bits + ((long long)E << 52));
+}
+
 template <int NCH, bool TMR, bool PRE = false>
 __device__ __forceinline__ void window_out(const long long* rw, int o0, const PushArgs& a, const TileJob& j,
                                            const long long* s0_pre, const int* fe_pre);
@@ -366,7 +376,21 @@ __device__ __forceinline__ void window_out(const long long* rw, int o0, const Pu
 #pragma unroll
   for (int i0 = 0; i0 < NCH; i0 += RB) {
     double tv[RB];
-    if (a.widx <= 1) {
+    if (a.widx == 0 && a.kind == kFinal) {
+      // a single window: one conversion per output
+      unsigned bad = 0;
+#pragma unroll
+      for (int i = 0; i < RB; ++i) {
+        bool ok;
+        tv[i] = rn_single(rw[i0 + i], a.ebase + fe[i0 + i], ok);
+        bad |= ok ? 0u : 1u << i;
+      }
+      if (bad != 0) {
+#pragma unroll
+        for (int i = 0; i < RB; ++i)
+          if ((bad >> i) & 1u) tv[i] = final_val(0, rw[i0 + i], 0, a.wlen, a.ebase + fe[i0 + i]);
+      }
+    } else if (a.widx <= 1) {
       const bool close = a.kind == kClose;
       unsigned bad = 0;
 #pragma unroll
@@ -1356,6 +1380,12 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
               tmem_ld16(ta + 128 + cc * 16, h1);  // group ga
               if (two) tmem_ld16(ta + cc * 16, h0);  // group ga + 1
               tmem_ld_wait();
+              if (cc == NOUT / 16 - 1) {
+                // the accumulator is read: the MMA lane may refill it while this chunk converts
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_acce[buf]);
+              }
               if (!j.cplx) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -1380,9 +1410,6 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                 }
               }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_acce[buf]);
             acc_par ^= 1u << buf;
             buf ^= 1;
           }
