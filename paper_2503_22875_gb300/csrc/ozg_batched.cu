@@ -368,16 +368,25 @@ __device__ __forceinline__ void digits_unit(const SplitArgs* jobs, int2 ur) {
     }
     if (sub + 1 < kDgK / 64 && l0 + 64 < J.k) load(l0 + 64);
     if (!row_ok || l0 + lg >= J.k) continue;
-    DigitSrc ds[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) ds[q] = digit_src(b[q], e);
     __half* out = J.D + row * J.Kp + l0 + lg;
-    store_digit_planes<kMaxPlanes>(ds, t_lo, t_hi, out, plane);
+    if (t_hi <= 9) {
+      // planes 1 .. 9 only need the first fixed-point word (fewer registers and instructions)
+      DigitSrc ds[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ds[q] = digit_src_first(b[q], e);
+      store_digit_planes<9>(ds, t_lo, t_hi, out, plane);
+    } else {
+      DigitSrc ds[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) ds[q] = digit_src(b[q], e);
+      store_digit_planes<kMaxPlanes>(ds, t_lo, t_hi, out, plane);
+    }
   }
 }
 
 // Grid-stride over the units; a gated pass (re-run completion) first reads one step-wide flag.
-__global__ void __launch_bounds__(256) digits_batched(const SplitArgs* jobs, const int2* units, int64_t nunits,
+// five CTAs per SM (48 registers): the planes 1 .. 9 path fits; the rare longer one spills a little
+__global__ void __launch_bounds__(256, 5) digits_batched(const SplitArgs* jobs, const int2* units, int64_t nunits,
                                                       const int* run) {
   if (run != nullptr && *run == 0) return;  // nothing to do in this pass
   for (int64_t unit = blockIdx.x; unit < nunits; unit += gridDim.x) {

@@ -48,6 +48,21 @@ __device__ __forceinline__ DigitSrc digit_src(uint64_t b, int e) {
   d.neg = (b >> 63) != 0 ? 0x8000u : 0u;
   return d;
 }
+// The same with only fa (digits 1 .. 9); fb is left 0.
+__device__ __forceinline__ DigitSrc digit_src_first(uint64_t b, int e) {
+  DigitSrc d;
+  const int eb = (int)((b >> 52) & 0x7FF);
+  uint64_t mant = b & 0xFFFFFFFFFFFFFull;
+  int ex = -1074;
+  if (eb != 0) {
+    mant |= 1ull << 52;
+    ex = eb - 1075;
+  }
+  d.fa = shift_signed(mant, ex - e + 63);
+  d.fb = 0;
+  d.neg = (b >> 63) != 0 ? 0x8000u : 0u;
+  return d;
+}
 // |digit t| in [0, 127]
 __device__ __forceinline__ uint32_t digit_mag(const DigitSrc& d, int t) {
   return t <= 9 ? (uint32_t)(d.fa >> (63 - 7 * t)) & 127u : (uint32_t)(d.fb >> (126 - 7 * t)) & 127u;
