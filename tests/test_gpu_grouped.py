@@ -253,7 +253,9 @@ def test_stacked_group_pairs_match_one_group_kernel(ozg, s):
     calls with alpha / beta and a grouped batch give the bits of the one-group 128-wide kernel
     (variant 1), and the oracle's where the exact sum needs at most two windows.  s = 17 is above
     the stacked kernel's limit and runs as variant 1."""
-    shapes = [(200, 130, 2100), (129, 257, 1000), (64, 64, 64), (130, 70, 129)]
+    # k mod 64 covers every count of valid 16-wide slices in the last k sub-tile (k16 = 4, 3, 4,
+    # 1, 2, 1), and k = 7 is one sub-tile that is both the first and the last of every sweep
+    shapes = [(200, 130, 2100), (129, 257, 1000), (64, 64, 64), (130, 70, 129), (97, 33, 85), (40, 150, 7)]
     res = {}
     for v in (1, 5):
         ctx = ozg.Context()
