@@ -995,8 +995,11 @@ __device__ __forceinline__ void gemm_body(const CUtensorMap* tmA0, const CUtenso
 // instructions per product.  The stage ring holds one A and one B sub-tile (64 k) per entry;
 // a B tile is used by its own stage and the next, so the commit after a stage frees the entry
 // of the stage before it.  Entry 0's B tile is also written to a mirror slot behind the last
-// entry, so the two B tiles of a stage are adjacent across the end of the ring too.  A window with an odd number of groups starts with a lone group
-// (one N = 128 MMA per plane pair, into columns 128 .. 255).
+// entry, so the two B tiles of a stage are adjacent across the end of the ring too.  A window
+// with an odd number of groups ends with its first group alone (one N = 128 MMA per plane pair,
+// into columns 128 .. 255): a tile then starts with a pass of two groups, whose chains are twice
+// as long as a lone group's, so the two accumulators keep the tensor pipe busy longer while the
+// epilogue rounds the previous tile.
 //
 // The two 256-column accumulators fill TMEM, so the int64 windows live in the epilogue's
 // registers, and every drained chain is added into them directly: the window is linear in the
@@ -1027,12 +1030,12 @@ __device__ __forceinline__ void stk_mma4(uint32_t dt, uint64_t da, uint64_t db, 
   for (int k16 = 1; k16 < BK / 16; ++k16) umma_f16(dt, da + (uint64_t)(2 * k16), db + (uint64_t)(2 * k16), idesc, 1u);
 }
 
-// Pass q of the window [wstart, wstart + wlen): the groups ga, ga + 1, or the lone group ga
-// (first pass of a window with an odd count).
+// Pass q of the window [wstart, wstart + wlen): the groups ga, ga + 1, or the lone group ga =
+// wstart (last pass of a window with an odd count).
 __device__ __forceinline__ void stk_pass(int wstart, int wlen, int q, int& ga, bool& two) {
   if (wlen & 1) {
-    two = q > 0;
-    ga = q == 0 ? wstart : wstart + 1 + 2 * (q - 1);
+    two = q < (wlen - 1) / 2;
+    ga = two ? wstart + 1 + 2 * q : wstart;
   } else {
     two = true;
     ga = wstart + 2 * q;
