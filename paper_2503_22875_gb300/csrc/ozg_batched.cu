@@ -110,9 +110,12 @@ __global__ void __launch_bounds__(256) rowmax_batched(const SplitArgs* jobs, con
 // selector's 10-bin histogram (bins of 4, the last holding gaps >= 36 and zeros) -- the same
 // counts as the two-pass form (row maxima, then a histogram pass over the operand again).
 // The gap needs e_i, known only once the whole row has been read.  So each element's exponent is
-// kept in shared memory as one byte, E(chunk max) - E(x) capped at 255, beside the exponent of
-// its 16-element chunk's maximum; then gap = (e_i - E(chunk max)) + byte, exactly while it is
-// below 36 and >= 36 whenever the byte was capped.
+// kept in shared memory as one byte, E(chunk max) - E(x) capped at 63 (plus 128 for a slot past
+// the row's end), beside the exponent of its 16-element chunk's maximum; then gap = (e_i -
+// E(chunk max)) + byte, exactly while it is below 36 and >= 36 whenever the byte was capped.
+// With e_i - E(chunk max) also capped at 63, four bytes add without carries in one 32-bit add,
+// and gap / 4 indexes a 64-entry table (bins 0 .. 8, bin 9 for 9 .. 31, nothing for the slots
+// past the row's end at 32 .. 63).
 // Only the high 32-bit word of each element is loaded: it holds the exponent field.  When the
 // chunk's maximum has a biased exponent >= 36, the biased exponents give every byte exactly
 // (a subnormal or zero element then gets a byte >= 36, its true gap being larger), and that
@@ -131,6 +134,12 @@ static_assert(kStatsK % (16 * kStatsChunk) == 0, "whole chunks");
 static_assert(kStatsK / 16 < 256 && 2 * kStatsBlockElems / 16 < 256, "per-thread bin counts fit 8-bit fields");
 
 extern __shared__ __align__(16) uint8_t stats_smem[];
+
+// 0x80 in the bytes of a four-byte word whose slots lie past the row's end (valid = slots of the
+// word before the end; <= 0: all four past it)
+__device__ __forceinline__ uint32_t past_end_bytes(int valid) {
+  return valid >= 4 ? 0u : (valid <= 0 ? 0x80808080u : 0x80808080u << (8 * valid));
+}
 
 // Exact path of one chunk (its maximum is subnormal, zero or below 2^-987): the full words, the
 // frexp exponents, and the chunk's bytes when hist is set.  Returns the chunk maximum's bits.
@@ -152,10 +161,10 @@ __device__ __noinline__ uint64_t stats_chunk_exact(const uint64_t* p, int64_t st
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const uint64_t x = v[4 * w4 + b];
-        const int d = x ? min(255, ecm - exponent_from_maxbits(x)) : 255;
+        const int d = x ? min(63, ecm - exponent_from_maxbits(x)) : 63;
         word |= (uint32_t)d << (8 * b);
       }
-      bytes[(4 * c + w4) * kStatsThreads + tid] = word;
+      bytes[(4 * c + w4) * kStatsThreads + tid] = word | past_end_bytes(n_t - i0 - 4 * w4);
     }
   }
   return cm;
@@ -165,16 +174,17 @@ template <bool HIST>
 __device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t unit) {
   __shared__ unsigned long long red[8][16];
   __shared__ unsigned int sh[10];
-  __shared__ uint4 onehot[11];  // bin b -> +1 in its 8-bit field of (bins 0-3, 4-7, 8-9); 10: nothing
+  __shared__ uint4 onehot[64];  // gap / 4 -> +1 in its bin's 8-bit field of (bins 0-3, 4-7, 8-9)
   short* cmx = reinterpret_cast<short*>(stats_smem);  // [chunk][tid]: frexp exponent of the chunk max
   uint32_t* bytes = reinterpret_cast<uint32_t*>(stats_smem + kStatsChunks * kStatsThreads * sizeof(short));  // [word][tid]
   const int tid = threadIdx.x;
   if (HIST && tid < 10) sh[tid] = 0;
-  if (HIST && tid < 11) {
+  if (HIST && tid < 64) {
+    const int bin = tid < 9 ? tid : (tid < 32 ? 9 : -1);  // -1: a slot past the row's end
     uint4 o = make_uint4(0, 0, 0, 0);
-    if (tid < 4) o.x = 1u << (8 * tid);
-    else if (tid < 8) o.y = 1u << (8 * (tid - 4));
-    else if (tid < 10) o.z = 1u << (8 * (tid - 8));
+    if (bin >= 0 && bin < 4) o.x = 1u << (8 * bin);
+    else if (bin >= 4 && bin < 8) o.y = 1u << (8 * (bin - 4));
+    else if (bin >= 8) o.z = 1u << (8 * (bin - 8));
     onehot[tid] = o;
   }
   const bool hist = HIST && J.hist != nullptr;
@@ -228,7 +238,8 @@ __device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t unit) {
           for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
             uint32_t word = 0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) word |= (uint32_t)min(255, ebm - (int)(h[4 * w4 + b] >> 20)) << (8 * b);
+            for (int b = 0; b < 4; ++b) word |= (uint32_t)min(63, ebm - (int)(h[4 * w4 + b] >> 20)) << (8 * b);
+            word |= past_end_bytes(nt - kStatsChunk * c - 4 * w4);
             bytes[(4 * c + w4) * kStatsThreads + tid] = word;
           }
         }
@@ -261,20 +272,17 @@ __device__ __forceinline__ void stats_unit(const SplitArgs& J, int64_t unit) {
       if (rmax >= kInfBits) atomicExch(J.nonfinite, 1);
     }
     if (hist) {
-      // per byte: bin = min(9, min(255, delta + byte) >> 2), four at a time with byte-SIMD ops;
-      // bytes past the row's end count in the empty bin 10
+      // per byte: table index (delta + byte) / 4 with delta capped at 63; four bytes per add
       const int e_row = exponent_from_maxbits(rmax);
       for (int c = 0; c < nc; ++c) {
-        const int delta = min(255, max(0, e_row - (int)cmx[c * kStatsThreads + tid]));
+        const int delta = min(63, max(0, e_row - (int)cmx[c * kStatsThreads + tid]));
         const uint32_t d4 = (uint32_t)delta * 0x01010101u;
 #pragma unroll
         for (int w4 = 0; w4 < kStatsChunk / 4; ++w4) {
-          const uint32_t g4 = __vaddus4(bytes[(4 * c + w4) * kStatsThreads + tid], d4);
-          const uint32_t b4 = __vminu4((g4 >> 2) & 0x3F3F3F3Fu, 0x09090909u);
+          const uint32_t q4 = ((bytes[(4 * c + w4) * kStatsThreads + tid] + d4) >> 2) & 0x3F3F3F3Fu;
 #pragma unroll
           for (int b = 0; b < 4; ++b) {
-            const int i = kStatsChunk * c + 4 * w4 + b;
-            const uint4 o = onehot[i < nt ? (int)((b4 >> (8 * b)) & 255u) : 10];
+            const uint4 o = onehot[(q4 >> (8 * b)) & 63u];
             c0 += o.x;
             c1 += o.y;
             c2 += o.z;
