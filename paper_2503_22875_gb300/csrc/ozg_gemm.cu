@@ -1011,8 +1011,10 @@ constexpr int NE = 6;                      // stage ring entries
 constexpr uint32_t SLOT = BM * BK * 2;     // one 128-row x 64-k fp16 sub-tile (16 KB, one TMA box)
 constexpr uint32_t A_OFF = 0, B_OFF = NE * SLOT;
 // B slots: one per entry and a mirror of entry 0's behind the last, so that the B tiles of
-// every two consecutive stages are adjacent (one N = 256 operand) also across the ring's end
-constexpr size_t SMEM = (size_t)(2 * NE + 1) * SLOT + 1024;
+// every two consecutive stages are adjacent (one N = 256 operand) also across the ring's end;
+// behind them the epilogue's staging of the spilled first-window words (8 per thread)
+constexpr uint32_t S0_OFF = (2 * NE + 1) * SLOT;
+constexpr size_t SMEM = (size_t)S0_OFF + 8 * EPI_WARPS * 32 * sizeof(long long) + 1024;
 constexpr uint32_t IDESC2 = umma_idesc_f16_f32(BM, 256), IDESC1 = umma_idesc_f16_f32(BM, 128);
 constexpr int CHAIN_STAGES = CHAIN_K / BK;  // 64-k MMA stages per accumulator column and chain
 constexpr int MAX_S = CHAIN_STAGES;          // a two-group sweep of g stages must fit one chain
@@ -1423,16 +1425,39 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         pa.widx = widx;
         pa.wlen = wlen;
         pa.kind = gend == s + 1 ? kFinal : widx == 0 ? kSpill : kClose;
+        // from the second window on, the spilled first-window words of the next chunk are
+        // copied into shared memory while this chunk is rounded (cp.async: no registers held)
+        long long* sbuf = reinterpret_cast<long long*>(smem + S0_OFF) + ew * 32 + lane;
+        if (widx >= 1) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) cp_async8(sbuf + i * EPI_WARPS * 32, pa.S0 + (size_t)i * BM);
+          cp_async_commit();
+        }
 #pragma unroll 1
         for (int o = 0; o < nout; o += 8) {
           long long s0c[8];
           int fe[8];
           const int fsrc = o < 32 ? fcol[0] : fcol[1];
+          if (widx >= 1) {
+            cp_async_wait_all();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            s0c[i] = widx >= 1 ? pa.S0[(size_t)(o + i) * BM] : 0ll;
-            fe[i] = __shfl_sync(0xffffffffu, fsrc, (o + i) & 31);
+            for (int i = 0; i < 8; ++i) s0c[i] = sbuf[i * EPI_WARPS * 32];
+            if (o + 8 < nout) {
+              // the next copies overwrite these slots: their addresses depend on the last word
+              // read, so they issue only once the reads have returned
+              uint32_t dep = (uint32_t)s0c[7];
+              asm volatile("and.b32 %0, %0, 0;" : "+r"(dep));
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                cp_async8(sbuf + dep + i * EPI_WARPS * 32, pa.S0 + (size_t)(o + 8 + i) * BM);
+              cp_async_commit();
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s0c[i] = 0ll;
           }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) fe[i] = __shfl_sync(0xffffffffu, fsrc, (o + i) & 31);
           window_out<8, false, true>(W, o, pa, j, s0c, fe);
 #pragma unroll
           for (int c = 0; c < NOUT - 8; ++c) W[c] = W[c + 8];
