@@ -1368,6 +1368,12 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         long long W[NOUT];
 #pragma unroll
         for (int c = 0; c < NOUT; ++c) W[c] = 0;
+        long long* sbuf = reinterpret_cast<long long*>(smem + S0_OFF) + ew * 32 + lane;
+        if (widx >= 1) {  // the first chunk's spilled words, staged while this window drains
+#pragma unroll
+          for (int i = 0; i < 8; ++i) cp_async8(sbuf + i * EPI_WARPS * 32, pa.S0 + (size_t)i * BM);
+          cp_async_commit();
+        }
         for (int q = 0; q < (wlen + 1) / 2; ++q) {
           int ga;
           bool two;
@@ -1426,13 +1432,8 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         pa.wlen = wlen;
         pa.kind = gend == s + 1 ? kFinal : widx == 0 ? kSpill : kClose;
         // from the second window on, the spilled first-window words of the next chunk are
-        // copied into shared memory while this chunk is rounded (cp.async: no registers held)
-        long long* sbuf = reinterpret_cast<long long*>(smem + S0_OFF) + ew * 32 + lane;
-        if (widx >= 1) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) cp_async8(sbuf + i * EPI_WARPS * 32, pa.S0 + (size_t)i * BM);
-          cp_async_commit();
-        }
+        // copied into shared memory while this chunk is rounded (cp.async: no registers held);
+        // the first chunk's copies were issued when the window started
 #pragma unroll 1
         for (int o = 0; o < nout; o += 8) {
           long long s0c[8];
@@ -1464,7 +1465,8 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         }
       }
     }
-  epi_done:;
+  epi_done:
+    cp_async_wait_all();  // no staging copy is left in flight (an aborted tile may leave one)
   }
 
   tc_fence_before();
