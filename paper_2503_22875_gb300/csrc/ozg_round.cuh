@@ -2,7 +2,7 @@
 // 2^E, rounded once to FP64 with ties to even (the result T of the emulated product, Sec. 2.2,
 // taken as one rounding of the exact sum).  N is a 128-bit integer (the exact epilogue's Horner
 // sum) or two int64 windows N = W0 2^S + W1 (the default epilogue).  Integer instructions and
-// one correctly rounded u64 -> f64 conversion; results outside the normal range (subnormal,
+// one correctly rounded 64-bit integer -> f64 conversion; results outside the normal range (subnormal,
 // zero or overflow) take round_edge, which rounds onto the grid of the smallest subnormal
 // directly, so that no second rounding follows the 53-bit one.  The functions use only integer
 // operations, conversion intrinsics and exact ldexp scalings, so the unit tests also compile
@@ -130,27 +130,24 @@ __device__ __forceinline__ double rn_i128_pow2(long long hi, unsigned long long 
 // RN(N 2^E) for N = W0 2^S + W1 (S = 7 wlen in [7, 56], |W0|, |W1| < 2^63 - 2^57, which the
 // windows of window_len satisfy; W0 = 0 for a single window) without data-dependent branches,
 // so the outputs of a chunk interleave.  With q = W0 + floor(W1 / 2^S) and r = W1 mod 2^S,
-// N = q 2^S + r (0 <= r < 2^S) and |N| = qm 2^S + rm with qm = q, rm = r for q >= 0 and
-// qm = -q - 1, rm = 2^S - r (r > 0) or qm = -q, rm = 0 (r = 0) for q < 0.  The top 63 bits of
-// |N| with a sticky bit below them are converted with one correctly rounded conversion and the
-// power of two goes into the exponent field.  `ok` is false when the result is not a normal
-// double (the caller then takes final_val, which rounds the 128-bit N).
+// N = q 2^S + r (0 <= r < 2^S).  Cut z low bits so that floor(N / 2^z) fits 63 bits past its
+// sign, and fold whether any cut bit was set into its lowest bit: that is N rounded to odd at
+// 2^z, with 63 significant bits whenever z > 0, so the correctly rounded signed int64 -> f64
+// conversion rounds it to nearest exactly as it would round N itself (an odd-rounded value with
+// at least two bits more than the target precision never creates or hides a tie).  The power of
+// two goes into the exponent field.  `ok` is false when the result is not a normal double (the
+// caller then takes final_val, which rounds the 128-bit N).
 __device__ __forceinline__ double rn_windows(long long W0, long long W1, int S, int E, bool& ok) {
   const long long q = W0 + (W1 >> S);
-  const unsigned long long mask = (1ull << S) - 1ull;
-  const unsigned long long r = (unsigned long long)W1 & mask;
-  const bool neg = q < 0;
-  const unsigned long long qm = neg ? (unsigned long long)(~q) + (r == 0 ? 1ull : 0ull) : (unsigned long long)q;
-  const unsigned long long rm = neg ? ((0ull - r) & mask) : r;
-  const int bl = 64 - __clzll((long long)qm);  // 0 .. 63
-  const int z = max(0, bl + S - 63);           // low bits of |N| below the 63-bit window (<= S)
-  const unsigned long long t =
-      (qm << (S - z)) | (rm >> z) | ((rm & ((1ull << z) - 1ull)) != 0 ? 1ull : 0ull);
-  const long long bits = __double_as_longlong(__ull2double_rn(t));
-  const int ex = (int)(bits >> 52) + z + E;  // biased exponent of the result
+  const unsigned long long r = (unsigned long long)W1 & ((1ull << S) - 1ull);
+  const int bl = 64 - __clzll(q ^ (q >> 63));  // bits of q past its sign: -2^bl <= q < 2^bl
+  const int z = max(0, bl + S - 63);           // <= S
+  const long long t = (long long)(((unsigned long long)q << (S - z)) | (r >> z) |
+                                  ((r & ((1ull << z) - 1ull)) != 0 ? 1ull : 0ull));
+  const long long bits = __double_as_longlong(__ll2double_rn(t));
+  const int ex = (int)((bits >> 52) & 0x7ff) + z + E;  // biased exponent of the result
   ok = t == 0 || (ex >= 1 && ex <= 2046);
-  const long long rb = bits + ((long long)(z + E) << 52);
-  return t == 0 ? 0.0 : __longlong_as_double(neg ? (rb | (long long)0x8000000000000000ull) : rb);
+  return t == 0 ? 0.0 : __longlong_as_double(bits + ((long long)(z + E) << 52));
 }
 
 }  // namespace ozg

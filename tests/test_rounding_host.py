@@ -27,6 +27,7 @@ HARNESS = r"""
 #define __forceinline__ inline
 static inline int __clzll(long long x) { return x == 0 ? 64 : __builtin_clzll((unsigned long long)x); }
 static inline double __ull2double_rn(unsigned long long x) { return (double)x; }
+static inline double __ll2double_rn(long long x) { return (double)x; }
 static inline long long __double_as_longlong(double d) { long long r; std::memcpy(&r, &d, 8); return r; }
 static inline double __longlong_as_double(long long x) { double r; std::memcpy(&r, &x, 8); return r; }
 using std::max;
