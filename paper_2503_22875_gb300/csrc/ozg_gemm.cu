@@ -1400,9 +1400,11 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
               if (!j.cplx) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                  const long long v1 = __float2int_rn(__uint_as_float(h1[i]));
-                  const long long v = two ? v1 * 128 + __float2int_rn(__uint_as_float(h0[i])) : v1;
-                  W[cc * 16 + i] += (long long)((unsigned long long)v << sh);
+                  // a chain sums at most 1024 products of digits |d| <= 127 (< 2^24), so
+                  // 128 c_ga + c_{ga+1} stays below 2^31 and combines in 32 bits
+                  const int v1 = __float2int_rn(__uint_as_float(h1[i]));
+                  const int v = two ? v1 * 128 + __float2int_rn(__uint_as_float(h0[i])) : v1;
+                  W[cc * 16 + i] += (long long)((unsigned long long)(long long)v << sh);
                 }
               } else {
                 // (Re, Im) of 8 outputs: even lanes Re = P_rr - P_ii, odd lanes Im = P_ir + P_ri
