@@ -1380,7 +1380,15 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
           stk_pass(wstart, wlen, q, ga, two);
           const int spc = stk_sweeps(ga, two);
           const int nch = (KB + spc - 1) / spc;
-          const int sh = 7 * (gend - ga - (two ? 1 : 0));
+          // real pair passes run in increasing ga and close the window (a lone group runs last),
+          // so they accumulate by Horner's rule: W <- 128^2 W before the pass, chains added
+          // unshifted; the lone group and complex data add their chains shifted to their weight
+          const bool horner = two && !j.cplx;
+          const int sh = horner ? 0 : 7 * (gend - ga - (two ? 1 : 0));
+          if (horner) {
+#pragma unroll
+            for (int c = 0; c < NOUT; ++c) W[c] = (long long)((unsigned long long)W[c] << 14);
+          }
           for (int ch = 0; ch < nch; ++ch) {
             if (!mbar_wait(&bar_accf[buf], (acc_par >> buf) & 1, abort_p, status)) goto epi_done;
             tc_fence_after();
@@ -1397,14 +1405,19 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_acce[buf]);
               }
-              if (!j.cplx) {
+              if (horner) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                   // a chain sums at most 1024 products of digits |d| <= 127 (< 2^24), so
                   // 128 c_ga + c_{ga+1} stays below 2^31 and combines in 32 bits
-                  const int v1 = __float2int_rn(__uint_as_float(h1[i]));
-                  const int v = two ? v1 * 128 + __float2int_rn(__uint_as_float(h0[i])) : v1;
-                  W[cc * 16 + i] += (long long)((unsigned long long)(long long)v << sh);
+                  const int v = __float2int_rn(__uint_as_float(h1[i])) * 128 + __float2int_rn(__uint_as_float(h0[i]));
+                  W[cc * 16 + i] += (long long)v;
+                }
+              } else if (!j.cplx) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const long long v = __float2int_rn(__uint_as_float(h1[i]));
+                  W[cc * 16 + i] += (long long)((unsigned long long)v << sh);
                 }
               } else {
                 // (Re, Im) of 8 outputs: even lanes Re = P_rr - P_ii, odd lanes Im = P_ir + P_ri
