@@ -1361,6 +1361,14 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
           fcol[h] = (c < climit && (h == 0 || !j.cplx)) ? __ldg(j.f + c) : 0;
         }
       }
+      // real tiles: the warp finishes only the 8-output chunks that reach into C, and none when
+      // its 32 rows all lie past C's last row (warp-uniform; the padding's sums are never written)
+      int nfin = nout;
+      if (!j.cplx) {
+        int nvalid = (int)max((int64_t)0, min((int64_t)NOUT, j.cols - pa.gcol0));
+        if ((int64_t)j.tm * BM + quad * 32 >= j.rows) nvalid = 0;
+        nfin = (nvalid + 7) & ~7;
+      }
       int widx = 0;
       for (int wstart = 2, wlen = stk_len0(s, win); wstart <= s + 1;
            wstart += wlen, wlen = min(win, s + 2 - wstart), ++widx) {
@@ -1369,7 +1377,7 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
 #pragma unroll
         for (int c = 0; c < NOUT; ++c) W[c] = 0;
         long long* sbuf = reinterpret_cast<long long*>(smem + S0_OFF) + ew * 32 + lane;
-        if (widx >= 1) {  // the first chunk's spilled words, staged while this window drains
+        if (widx >= 1 && nfin > 0) {  // the first chunk's spilled words, staged while this window drains
 #pragma unroll
           for (int i = 0; i < 8; ++i) cp_async8(sbuf + i * EPI_WARPS * 32, pa.S0 + (size_t)i * BM);
           cp_async_commit();
@@ -1450,7 +1458,7 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
         // copied into shared memory while this chunk is rounded (cp.async: no registers held);
         // the first chunk's copies were issued when the window started
 #pragma unroll 1
-        for (int o = 0; o < nout; o += 8) {
+        for (int o = 0; o < nfin; o += 8) {
           long long s0c[8];
           int fe[8];
           const int fsrc = o < 32 ? fcol[0] : fcol[1];
@@ -1458,7 +1466,7 @@ __device__ __forceinline__ void stacked_body(const CUtensorMap* tmA0, const CUte
             cp_async_wait_all();
 #pragma unroll
             for (int i = 0; i < 8; ++i) s0c[i] = sbuf[i * EPI_WARPS * 32];
-            if (o + 8 < nout) {
+            if (o + 8 < nfin) {
               // the next copies overwrite these slots: their addresses depend on the last word
               // read, so they issue only once the reads have returned
               uint32_t dep = (uint32_t)s0c[7];
