@@ -145,6 +145,29 @@ def test_two_window_rounding_equals_exact_rounding(harness):
     check(harness, cases, lambda c: f"w {c[2]} {c[3]} {c[4]} {c[1]}\n")
 
 
+def test_two_window_rounding_ties_and_near_ties_of_both_signs(harness):
+    """Exact ties and one-unit neighbours of ties at the 53-bit cut, for sums of 60 to 118 bits of
+    either sign (the sum then has bits both above and below the 63-bit window the two-window
+    form keeps, so the folded sticky bit decides), split into the two windows in every way the
+    epilogue can produce (the second window signed, its magnitude below 2^S or reaching past it)."""
+    g = random.Random(13)
+    wmax = 2 ** 69 // 127
+    raw = []
+    while len(raw) < 30000:
+        S = 7 * g.randint(1, 8)
+        L = g.randint(60, 118)
+        m = g.getrandbits(53) | (1 << 52)
+        N = m * 2 ** (L - 53) + 2 ** (L - 54) + g.choice([-1, 0, 0, 1])
+        N = -N if g.random() < 0.5 else N
+        W1 = N % 2 ** S - (2 ** S if g.random() < 0.5 else 0) + g.choice([0, 0, 1, -1]) * 2 ** S
+        W0 = (N - W1) // 2 ** S
+        if abs(W0) > wmax or abs(W1) > wmax:
+            continue
+        raw.append((W0, W1, S, pick_exponent(g, abs(N).bit_length())))
+    cases = [(W0 * 2 ** S + W1, E, W0, W1, S) for W0, W1, S, E in raw]
+    check(harness, cases, lambda c: f"w {c[2]} {c[3]} {c[4]} {c[1]}\n")
+
+
 def test_window_length_keeps_every_window_in_int64(harness):
     """window_len(s, kpad, cplx) is the closed form c = (62 - L) / 7 + 1 (L the bit length of
     gmax = s kpad 127^2, doubled for complex), and the worst-case window, gmax (128^c - 1) / 127,
