@@ -346,7 +346,20 @@ __device__ __forceinline__ void digits_unit(const SplitArgs* jobs, int2 ur) {
   const int rr = tid % 32;
   const bool rrok = r0 + rr < J.rows;
   uint64_t nx[8];
+  // contiguous rows whose elements sit on 16-byte boundaries in pairs (even ld, aligned base)
+  // take their eight elements as four 16-byte loads where all eight lie inside the row
+  const bool pairs = !J.strided && (J.ld & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   auto load = [&](int64_t l0) {
+    if (pairs && row_ok && l0 + lg + 8 <= J.k) {
+      const ulonglong2* p = reinterpret_cast<const ulonglong2*>(X + row * J.ld + l0 + lg);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const ulonglong2 v = __ldg(p + h);
+        nx[2 * h] = v.x;
+        nx[2 * h + 1] = v.y;
+      }
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       if (J.strided) {
